@@ -1,0 +1,146 @@
+"""FP64 CPU oracle for the SVDLUT transform -- TEST INFRASTRUCTURE.
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline leg may import this package.  The product (the CUDA library and
+its Python binding) never calls it, and it shares no code with it.
+
+``svdlut_oracle.c`` holds the arithmetic (Eq. 7 reconstruction, Supp.
+Eqs. 10-20 transform and slicing, and their adjoint); this module compiles
+it with gcc and marshals numpy arrays.  ``generator.py`` holds the FP64
+oracle of the learned factor generator (Supp. Tables 1-5).
+
+Parity status: forward and adjoint are pinned (tests/test_oracle_*.py);
+the generator's numeric outputs are "parity unpinned" beyond the paper's
+parameter count and finite differences: the paper prints no values.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "svdlut_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, f"liboracle_{platform.machine()}.so")
+_lock = threading.Lock()
+_lib = None
+
+PARAM_NAMES = ("U", "S", "V", "lut_w", "g_xy", "g_xc", "g_yc", "grid_w")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc -O2, no fast-math, OpenMP).  Returns the path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int)
+            i = ctypes.c_int
+            lib.oracle_forward.argtypes = [ip, i, i, i] + [dp] * 10 + [i]
+            lib.oracle_forward_separable.argtypes = [ip, i, i, i] + [dp] * 10
+            lib.oracle_backward.argtypes = [ip, i, i, i] + [dp] * 19
+            lib.oracle_lut_from_svd.argtypes = [i, i, dp, dp, dp, dp]
+            lib.oracle_quantize_u8.argtypes = [dp, ctypes.c_void_p, ctypes.c_size_t]
+            lib.oracle_u8_to_unit.argtypes = [ctypes.c_void_p, dp, ctypes.c_size_t]
+            _lib = lib
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    if a is None:
+        return ctypes.POINTER(ctypes.c_double)()
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _dims(d):
+    t = d.as_tuple() if hasattr(d, "as_tuple") else tuple(d)
+    return (ctypes.c_int * 6)(*t)
+
+
+def _batched(params, x):
+    """Accept unbatched ([3][H][W] + per-image params) or batched inputs."""
+    x = _d(x)
+    if x.ndim == 3:
+        x = x[None]
+        params = {k: _d(params[k])[None] for k in PARAM_NAMES}
+    else:
+        params = {k: _d(params[k]) for k in PARAM_NAMES}
+    return params, x
+
+
+def lut_from_svd(U, S, V):
+    """Eq. 7 for one table: U [D][R], S [R], V [D][R] -> T [D][D]."""
+    U, S, V = _d(U), _d(S), _d(V)
+    D, R = U.shape
+    T = np.empty((D, D))
+    _load().oracle_lut_from_svd(D, R, _ptr(U), _ptr(S), _ptr(V), _ptr(T))
+    return T
+
+
+def forward(dims, params, x, nthreads: int = 0, separable: bool = False):
+    """Y = transform(x) in FP64.  x: [3][H][W] or [B][3][H][W] in [0,1] scale."""
+    squeeze = np.asarray(x).ndim == 3
+    p, xb = _batched(params, x)
+    B, _, H, W = xb.shape
+    y = np.empty_like(xb)
+    args = [_ptr(p[k]) for k in PARAM_NAMES]
+    lib = _load()
+    if separable:
+        lib.oracle_forward_separable(_dims(dims), B, H, W, *args, _ptr(xb), _ptr(y))
+    else:
+        lib.oracle_forward(_dims(dims), B, H, W, *args, _ptr(xb), _ptr(y), int(nthreads))
+    return y[0] if squeeze else y
+
+
+def backward(dims, params, x, dy):
+    """Adjoint in FP64: returns dict with dx and d<param> for every parameter."""
+    squeeze = np.asarray(x).ndim == 3
+    p, xb = _batched(params, x)
+    dyb = _d(dy)
+    if dyb.ndim == 3:
+        dyb = dyb[None]
+    B, _, H, W = xb.shape
+    out = {"dx": np.empty_like(xb)}
+    for k in PARAM_NAMES:
+        out["d" + k] = np.empty_like(p[k])
+    _load().oracle_backward(_dims(dims), B, H, W, *[_ptr(p[k]) for k in PARAM_NAMES],
+                            _ptr(xb), _ptr(dyb), _ptr(out["dx"]),
+                            *[_ptr(out["d" + k]) for k in PARAM_NAMES])
+    if squeeze:
+        out = {k: v[0] for k, v in out.items()}
+    return out
+
+
+def u8_to_unit(v):
+    v = np.ascontiguousarray(v, dtype=np.uint8)
+    out = np.empty(v.shape, dtype=np.float64)
+    _load().oracle_u8_to_unit(v.ctypes.data, _ptr(out), v.size)
+    return out
+
+
+def quantize_u8(y):
+    y = _d(y)
+    out = np.empty(y.shape, dtype=np.uint8)
+    _load().oracle_quantize_u8(_ptr(y), out.ctypes.data, y.size)
+    return out
