@@ -1,0 +1,324 @@
+"""Benchmark of the SVDLUT fused apply on GB300.
+
+Default workload: one 3840x2160 RGB FP32 image per step through svdlut_apply
+(fused 2D slicing + 2D LUT transform, D_t=33, rank 8, K=8 spatial grids at
+1/8 resolution).  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference there is:
+the paper ships no code) on the same workload, on the host cores.
+Under torchrun (N > 1) each rank runs its own replica on its own GPU
+(weak scaling, no collective on the data path); value = all ranks' pixels /
+max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import svdlut_inputs as si  # noqa: E402
+
+H4K, W4K = 2160, 3840
+METRIC = "Mpix/s and % HBM peak, SVDLUT apply at 4K (plain vs batched/learned), 1 GB300"
+N_SETS = 4  # rotating input/output sets: 4 x 199 MB > 129 MB L2
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algo_bytes_apply(H, W, d: si.Dims, io_bytes: int) -> int:
+    """Algorithmic bytes of one fused apply: read x and write y (3 planes),
+    read the grid planes, grid weights and SVD factors once."""
+    px = H * W
+    grids = d.K * (d.Dsy * d.Dsx + d.Dsx * d.Dsc + d.Dsy * d.Dsc + 4) * 4
+    factors = (2 * 9 * d.D_t * d.rank + 9 * d.rank + 12) * 4
+    return px * 3 * io_bytes * 2 + grids + factors
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2508_16121_gb300 as svdlut
+    from paper_2508_16121_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    H, W = H4K, W4K
+    d = si.spatial_dims(H, W)
+    sets = []
+    for s in range(N_SETS):
+        x, p = si.make_batch(si.config_seed(1) + 1000 * rank + s, 1, H, W, d)
+        sets.append((torch.from_numpy(x).to(dev), svdlut.to_device(p, dev), torch.empty_like(torch.from_numpy(x), device=dev)))
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        xt, pt, yt = sets[i % N_SETS]
+        svdlut.apply(xt, pt, out=yt)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step(i)
+            ev[i][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    total_ms = max_over_ranks(world, t0.elapsed_time(t1))
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    clocks = clk.summary()
+
+    # ---- u8 variant (same frames quantised) ----
+    u8_sets = [(torch.from_numpy(si.to_u8(s[0].cpu().numpy())).to(dev), s[1]) for s in sets]
+    u8_out = torch.empty_like(u8_sets[0][0])
+    for i in range(3):
+        svdlut.apply(u8_sets[i % N_SETS][0], u8_sets[i % N_SETS][1], out=u8_out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for i in range(args.steps):
+        svdlut.apply(u8_sets[i % N_SETS][0], u8_sets[i % N_SETS][1], out=u8_out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    u8_ms = a.elapsed_time(b) / args.steps
+
+    # ---- end to end through the public API with pinned host buffers ----
+    xh = sets[0][0].cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xd, pd, yd = sets[0]
+    for _ in range(3):
+        xd.copy_(xh, non_blocking=True)
+        svdlut.apply(xd, pd, out=yd)
+        yh.copy_(yd, non_blocking=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        xd.copy_(xh, non_blocking=True)
+        svdlut.apply(xd, pd, out=yd)
+        yh.copy_(yd, non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(world, a.elapsed_time(b) / args.steps)
+
+    mpix = H * W / 1e6
+    ms_per_step = total_ms / args.steps
+    value = world * mpix / (ms_per_step / 1e3)
+    peak, peak_src = peaks()
+    bytes_launch = algo_bytes_apply(H, W, d, 4)
+    achieved = bytes_launch / (kern_ms / 1e3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "Mpix/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; 64x64 checkerboard of U(0,1) noise and smooth gradients)",
+        "config": {"workload": "plain svdlut_apply, 1x3840x2160 RGB FP32, D_t=33 rank 8, K=8 grids "
+                               "480x270x17 (1/8 res)", "global_batch": world, "image": "3840x2160",
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"rotating {N_SETS} input/output sets ({N_SETS * bytes_launch / 1e6:.0f} MB) > 129 MB L2"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "apply_kernel<float>", "bytes_per_launch": bytes_launch,
+                     "kernel_ms": round(kern_ms, 5), "peak_source": peak_src},
+        "e2e": {"value": round(world * mpix / (e2e_ms / 1e3), 1), "unit": "Mpix/s",
+                "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4)},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "variants": {"u8_plain_4k": {"value": round(mpix / (u8_ms / 1e3), 1), "unit": "Mpix/s",
+                                     "ms": round(u8_ms, 5),
+                                     "GB/s": round(algo_bytes_apply(H, W, d, 1) / (u8_ms / 1e3) / 1e9, 1)}},
+    }
+    return out, (xh.numpy(), {k: v.cpu().numpy() for k, v in pd.items()}, d)
+
+
+def cpu_baseline(x, p, d, reps=2):
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.forward(d, p, x[..., :64, :], nthreads=cores)  # warm
+    t = time.time()
+    for _ in range(reps):
+        oracle.forward(d, p, x, nthreads=cores)
+    dt = time.time() - t
+    px = reps * x.shape[-1] * x.shape[-2]
+    return {"value": round(px / dt / 1e6, 3), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} full 3840x2160 FP32 frames through the FP64 oracle, OpenMP over rows "
+                      f"({dt:.1f} s wall)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    H, W = H4K, W4K
+    d = si.spatial_dims(H, W)
+    x, p = si.make_batch(si.config_seed(1), 1, H, W, d)
+    x, p = x[0], {k: v[0] for k, v in p.items()}
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.forward(d, p, x[:, :64], nthreads=cores)
+    t = time.time()
+    for _ in range(args.steps):
+        oracle.forward(d, p, x, nthreads=cores)
+    dt = time.time() - t
+    ms = dt * 1e3 / args.steps
+    v = H * W / 1e6 / (ms / 1e3)
+    return {
+        "metric": METRIC, "value": round(v, 3), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
+        "config": {"workload": "plain svdlut_apply, 1x3840x2160 RGB FP32, D_t=33 rank 8, K=8 grids "
+                               "480x270x17 (1/8 res)", "global_batch": 1, "image": "3840x2160",
+                   "parallelism": "host cores"},
+        "cpu_baseline": {"value": round(v, 3), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full 3840x2160 frames through the FP64 CPU oracle"},
+        "e2e": {"value": round(v, 3), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world, rank, local = (1, 0, 0)
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        if args.impl == "reference":
+            rank = int(os.environ.get("RANK", "0"))
+            if rank != 0:
+                return
+            world = int(os.environ.get("WORLD_SIZE", "1"))
+        else:
+            world, rank, local = dist_init()
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out, sample = run_ours(args, world, rank, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            x, p, d = sample
+            out["cpu_baseline"] = cpu_baseline(x, p, d)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

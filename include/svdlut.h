@@ -1,0 +1,107 @@
+/*
+ * svdlut.h -- C ABI of the GB300 (sm_103a) SVDLUT library.
+ *
+ * SVDLUT (arXiv 2508.16121) enhances an image with an image-adaptive colour
+ * transform stored as nine 2D LUTs, each rebuilt from rank-R SVD factors, and
+ * adds 2D bilateral-grid slicing for spatial awareness; both are fused into one
+ * per-pixel pass (Sec. 3.2.3, Eq. 8; Supp. Sec. C, Eqs. 10-20).
+ *
+ * Conventions shared by every entry point
+ *  - All tensor pointers are DEVICE pointers unless stated otherwise; the
+ *    caller owns every buffer.  The library does not allocate on these paths.
+ *  - Calls are asynchronous on the given stream (a cudaStream_t, passed as
+ *    svdlut_stream_t; NULL = legacy default stream).  Errors found on the host
+ *    (bad arguments) are returned before anything is launched; a failed launch
+ *    returns SVDLUT_ERR_CUDA.  svdlut_last_error() gives a thread-local message.
+ *  - Images are planar (CHW) per image, batch-major: x[b][c][h][w], c = r,g,b.
+ *    FP32 values are read as they are and clamped to [0,1] before lookup;
+ *    8-bit values v are read as v/255.
+ *  - Cell rule on an axis with D vertices: u = p (D-1), i = min(floor(u), D-2),
+ *    delta = u - i  (Supp. Eq. 12 / Eq. 16 with the upper edge kept inside).
+ *  - Spatial coordinates x' = x/(W-1), y' = y/(H-1) (0 when W or H is 1), pixel
+ *    indices as in Supp. Eq. 15.
+ */
+#ifndef SVDLUT_H
+#define SVDLUT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *svdlut_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    SVDLUT_OK = 0,
+    SVDLUT_ERR_INVALID_ARG = 1, /* null pointer, bad size, misaligned pointer */
+    SVDLUT_ERR_UNSUPPORTED = 2, /* valid but beyond this build's limits      */
+    SVDLUT_ERR_CUDA = 3,        /* a CUDA call or launch failed              */
+    SVDLUT_ERR_WORKSPACE = 4,   /* workspace missing or too small            */
+    SVDLUT_ERR_TIMEOUT = 5      /* a bounded device-side wait ran out        */
+} svdlut_status;
+
+typedef enum {
+    SVDLUT_F32 = 0, /* float32 in and out                                    */
+    SVDLUT_U8 = 1   /* uint8 in and out; out = rint(clamp(Y,0,1)*255) in FP32 */
+} svdlut_dtype;
+
+/*
+ * Sizes of one transform.
+ *   D_t   LUT vertices per axis (paper: 33, Supp. Sec. A)        2 <= D_t <= 33
+ *   rank  SVD rank N_s (paper: 8, Eq. 7)                          1 <= rank <= D_t
+ *   K     number of 2D bilateral grids (paper: 6)                 0 <= K <= 48
+ *   Dsx, Dsy, Dsc  grid vertices along x, y and intensity (paper: 17 each);
+ *         Dsx, Dsy >= 2, 2 <= Dsc <= 64.
+ */
+typedef struct {
+    int32_t D_t, rank, K, Dsx, Dsy, Dsc;
+} svdlut_dims;
+
+/*
+ * Per-image transform parameters (Supp. Tables 3-5), FP32 device arrays with
+ * a leading batch axis B (one set per image):
+ *   U      [B][3 c][3 pair][D_t][rank]  pair order (rg, rb, gb); row i of U is
+ *                                       vertex i of the pair's first axis
+ *   S      [B][3][3][rank]              singular values (any sign)
+ *   V      [B][3][3][D_t][rank]         row j is vertex j of the second axis
+ *          so that t^c_p[i][j] = sum_r U[i][r] S[r] V[j][r]          (Eq. 7)
+ *   lut_w  [B][3 c][4]                  (w_rg, w_rb, w_gb, b)        (Eq. 4)
+ *   g_xy   [B][K][Dsy][Dsx]             plane over (y, x)
+ *   g_xc   [B][K][Dsx][Dsc]             plane over (x, intensity)
+ *   g_yc   [B][K][Dsy][Dsc]             plane over (y, intensity)
+ *   grid_w [B][K][4]                    (w_xy, w_xc, w_yc, b)        (Eq. 19)
+ * Grid k uses the intensity of channel k mod 3 and adds to output channel
+ * k mod 3 (Eq. 8 / Supp. Eq. 20).  g_* and grid_w may be NULL when K == 0.
+ */
+typedef struct {
+    const float *U, *S, *V, *lut_w, *g_xy, *g_xc, *g_yc, *grid_w;
+} svdlut_params;
+
+/*
+ * svdlut_apply -- the fused 2D slicing + 2D LUT transform (Eq. 8, Supp. Eq. 20):
+ *   Y_c = sum_p w^c_p I_bi(x, t^c_p) + b^c
+ *       + sum_{k = c mod 3} [ w_xy I_bi((x',y'), g_xy) + w_xc I_bi((x',x_c), g_xc)
+ *                             + w_yc I_bi((y',x_c), g_yc) + b_k ]
+ * for B images of H x W.  x and y: [B][3][H][W] of dtype (float or uint8),
+ * device, must not overlap.  Pointers must be 4-byte aligned for F32; 16-byte
+ * alignment and W % 4 == 0 enable the vectorised path (any other case is
+ * handled, more slowly).  Returns INVALID_ARG for null pointers, B, H or W < 1
+ * or dims out of range; UNSUPPORTED for dims beyond the limits above.
+ */
+svdlut_status svdlut_apply(const svdlut_dims *dims, const svdlut_params *params, int B, int H,
+                           int W, svdlut_dtype dtype, const void *x, void *y,
+                           svdlut_stream_t stream);
+
+/* Message of the last error raised on this thread ("" if none). */
+const char *svdlut_last_error(void);
+
+/* Library version, e.g. "svdlut 0.1.0 sm_103a". */
+const char *svdlut_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVDLUT_H */

@@ -1,0 +1,98 @@
+"""GB300-native SVDLUT: fused 2D-LUT transform + 2D bilateral-grid slicing
+(arXiv 2508.16121) as hand-written sm_103a CUDA behind a C ABI
+(include/svdlut.h).  This module only marshals torch tensors into that ABI;
+torch provides device memory and streams.
+
+    import paper_2508_16121_gb300 as svdlut
+    y = svdlut.apply(x, params)          # x: [B,3,H,W] or [3,H,W], float32 or uint8, CUDA
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import SvdlutError  # noqa: F401
+
+PARAM_NAMES = ("U", "S", "V", "lut_w", "g_xy", "g_xc", "g_yc", "grid_w")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def dims_of(params) -> _lib.Dims:
+    """Infer (D_t, rank, K, Dsx, Dsy, Dsc) from parameter tensor shapes
+    (per-image [3,3,D,R] or batched [B,3,3,D,R] U)."""
+    U, gxy, gxc = params["U"], params["g_xy"], params["g_xc"]
+    D, R = U.shape[-2], U.shape[-1]
+    K, Dsy, Dsx = gxy.shape[-3], gxy.shape[-2], gxy.shape[-1]
+    Dsc = gxc.shape[-1]
+    return _lib.Dims(D, R, K, Dsx, Dsy, Dsc)
+
+
+def _param_struct(params, B, d):
+    torch = _torch()
+    shapes = {"U": (3, 3, d.D_t, d.rank), "S": (3, 3, d.rank), "V": (3, 3, d.D_t, d.rank),
+              "lut_w": (3, 4), "g_xy": (d.K, d.Dsy, d.Dsx), "g_xc": (d.K, d.Dsx, d.Dsc),
+              "g_yc": (d.K, d.Dsy, d.Dsc), "grid_w": (d.K, 4)}
+    ptrs = {}
+    for n in PARAM_NAMES:
+        t = params[n]
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"param {n} must be a contiguous float32 CUDA tensor")
+        want = shapes[n]
+        if tuple(t.shape[-len(want):]) != want or t.numel() != B * _numel(want):
+            raise ValueError(f"param {n}: shape {tuple(t.shape)} does not match {want} x B={B}")
+        ptrs[n] = t.data_ptr() if t.numel() else None
+    return _lib.Params(**ptrs)
+
+
+def _numel(s):
+    n = 1
+    for v in s:
+        n *= v
+    return n
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def apply(x, params, out=None, stream=None):
+    """Fused SVDLUT apply (Eq. 8).  x: CUDA tensor [B,3,H,W] or [3,H,W],
+    float32 or uint8, contiguous.  params: dict of float32 CUDA tensors with
+    an optional leading batch axis (see include/svdlut.h).  Returns y with
+    x's shape and dtype."""
+    torch = _torch()
+    squeeze = x.dim() == 3
+    xb = x.unsqueeze(0) if squeeze else x
+    if xb.dim() != 4 or xb.shape[1] != 3:
+        raise ValueError("x must be [B,3,H,W] or [3,H,W]")
+    if not xb.is_cuda or not xb.is_contiguous():
+        raise ValueError("x must be a contiguous CUDA tensor")
+    if xb.dtype == torch.float32:
+        dt = _lib.F32
+    elif xb.dtype == torch.uint8:
+        dt = _lib.U8
+    else:
+        raise ValueError("x must be float32 or uint8")
+    B, _, H, W = xb.shape
+    d = dims_of(params)
+    p = _param_struct(params, B, d)
+    y = torch.empty_like(xb) if out is None else (out.unsqueeze(0) if squeeze else out)
+    if y.shape != xb.shape or y.dtype != xb.dtype or not y.is_contiguous():
+        raise ValueError("out must match x in shape and dtype")
+    lib = _lib.load()
+    _lib.check(lib.svdlut_apply(ctypes.byref(d), ctypes.byref(p), B, H, W, dt,
+                                ctypes.c_void_p(xb.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                _stream_ptr(stream)))
+    return y[0] if squeeze else y
+
+
+def to_device(params, device="cuda"):
+    """numpy / torch parameter dict -> contiguous float32 tensors on device."""
+    torch = _torch()
+    return {k: torch.as_tensor(v, dtype=torch.float32).contiguous().to(device) for k, v in params.items()}

@@ -1,0 +1,82 @@
+"""ctypes view of include/svdlut.h.  Argument marshalling only: every step of
+the transform runs in libsvdlut.so's CUDA kernels.  Loading fails loudly when
+the library has not been built (there is no CPU fallback)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT = range(6)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "WORKSPACE", 5: "TIMEOUT"}
+F32, U8 = 0, 1
+
+c_int, c_size_t, c_void_p, c_float_p = ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("D_t", "rank", "K", "Dsx", "Dsy", "Dsc")]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("U", "S", "V", "lut_w", "g_xy", "g_xc", "g_yc", "grid_w")]
+
+
+class SvdlutError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"svdlut: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libsvdlut.so.  Raises if it is missing (no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and (not os.path.exists(path) or _build.needs_build()):
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"libsvdlut.so is not built ({path}); run paper_2508_16121_gb300.build.build() "
+                "-- the CUDA library is required, there is no CPU fallback")
+        lib = ctypes.CDLL(path)
+        _declare(lib)
+        _lib = lib
+        return lib
+
+
+def _declare(lib):
+    P = ctypes.POINTER
+    lib.svdlut_last_error.restype = ctypes.c_char_p
+    lib.svdlut_version.restype = ctypes.c_char_p
+    lib.svdlut_apply.argtypes = [P(Dims), P(Params), c_int, c_int, c_int, c_int, c_void_p, c_void_p,
+                                 c_void_p]
+    lib.svdlut_apply.restype = c_int
+    for name, argtypes in _EXTRA.items():
+        if hasattr(lib, name):
+            f = getattr(lib, name)
+            f.argtypes = argtypes[0]
+            f.restype = argtypes[1]
+
+
+_EXTRA: dict = {}
+
+
+def check(status: int):
+    if status != OK:
+        raise SvdlutError(status, load().svdlut_last_error().decode())
+
+
+# names every build of the library exports (declared in include/svdlut.h)
+EXPORTED = ["svdlut_apply", "svdlut_last_error", "svdlut_version"]

@@ -1,0 +1,106 @@
+// svdlut_apply: host entry of the plain (same-size batch) fused apply.
+#include <algorithm>
+#include <cmath>
+
+#include "apply_kernel.cuh"
+#include "apply_launch.cuh"
+
+namespace svdlut {
+
+svdlut_status check_params(const svdlut_dims *d, const svdlut_params *p)
+{
+    if (!p) return fail(SVDLUT_ERR_INVALID_ARG, "params is NULL");
+    if (!p->U || !p->S || !p->V || !p->lut_w)
+        return fail(SVDLUT_ERR_INVALID_ARG, "params: U, S, V and lut_w are required");
+    if (d->K > 0 && (!p->g_xy || !p->g_xc || !p->g_yc || !p->grid_w))
+        return fail(SVDLUT_ERR_INVALID_ARG, "params: g_xy, g_xc, g_yc and grid_w are required when K > 0");
+    const void *ptrs[8] = {p->U, p->S, p->V, p->lut_w, p->g_xy, p->g_xc, p->g_yc, p->grid_w};
+    for (const void *q : ptrs)
+        if (q && !aligned(q, 4)) return fail(SVDLUT_ERR_INVALID_ARG, "params: pointers must be 4-byte aligned");
+    return SVDLUT_OK;
+}
+
+size_t param_stride(const svdlut_dims *d, int which)
+{
+    const size_t D = d->D_t, R = d->rank, K = d->K;
+    switch (which) {
+    case 0: return 9 * D * R;                              // U
+    case 1: return 9 * R;                                  // S
+    case 2: return 9 * D * R;                              // V
+    case 3: return 12;                                     // lut_w
+    case 4: return K * d->Dsy * d->Dsx;                    // g_xy
+    case 5: return K * d->Dsx * d->Dsc;                    // g_xc
+    case 6: return K * d->Dsy * d->Dsc;                    // g_yc
+    default: return K * 4;                                 // grid_w
+    }
+}
+
+ImgDesc make_desc(const svdlut_dims *d, const svdlut_params *p, int b, int H, int W, svdlut_dtype dt,
+                  const void *x, void *y)
+{
+    ImgDesc e{};
+    const size_t es = dt == SVDLUT_F32 ? 4 : 1;
+    const size_t img = static_cast<size_t>(3) * H * W * es;
+    e.x = static_cast<const char *>(x) + b * img;
+    e.y = static_cast<char *>(y) + b * img;
+    e.U = p->U + b * param_stride(d, 0);
+    e.S = p->S + b * param_stride(d, 1);
+    e.V = p->V + b * param_stride(d, 2);
+    e.lw = p->lut_w + b * param_stride(d, 3);
+    e.gxy = p->g_xy ? p->g_xy + b * param_stride(d, 4) : nullptr;
+    e.gxc = p->g_xc ? p->g_xc + b * param_stride(d, 5) : nullptr;
+    e.gyc = p->g_yc ? p->g_yc + b * param_stride(d, 6) : nullptr;
+    e.gw = p->grid_w ? p->grid_w + b * param_stride(d, 7) : nullptr;
+    e.H = H;
+    e.W = W;
+    e.D = d->D_t;
+    e.R = d->rank;
+    e.K = d->K;
+    e.Dsx = d->Dsx;
+    e.Dsy = d->Dsy;
+    e.Dsc = d->Dsc;
+    e.tiles_x = (W + kTileW - 1) / kTileW;
+    e.rW1 = W > 1 ? 1.0f / static_cast<float>(W - 1) : 0.f;
+    e.rH1 = H > 1 ? 1.0f / static_cast<float>(H - 1) : 0.f;
+    const size_t va = dt == SVDLUT_F32 ? 16 : 4;
+    e.vec = (W % 4 == 0) && aligned(e.x, va) && aligned(e.y, va);
+    return e;
+}
+
+}  // namespace svdlut
+
+using namespace svdlut;
+
+extern "C" svdlut_status svdlut_apply(const svdlut_dims *dims, const svdlut_params *params, int B, int H,
+                                      int W, svdlut_dtype dtype, const void *x, void *y,
+                                      svdlut_stream_t stream)
+{
+    clear_error();
+    svdlut_status st = check_dims(dims);
+    if (st != SVDLUT_OK) return st;
+    if ((st = check_params(dims, params)) != SVDLUT_OK) return st;
+    if (B < 1 || H < 1 || W < 1) return fail(SVDLUT_ERR_INVALID_ARG, "B=%d H=%d W=%d must be >= 1", B, H, W);
+    if (dtype != SVDLUT_F32 && dtype != SVDLUT_U8) return fail(SVDLUT_ERR_INVALID_ARG, "unknown dtype %d", dtype);
+    if (!x || !y) return fail(SVDLUT_ERR_INVALID_ARG, "x and y are required");
+    const size_t es = dtype == SVDLUT_F32 ? 4 : 1;
+    if (dtype == SVDLUT_F32 && (!aligned(x, 4) || !aligned(y, 4)))
+        return fail(SVDLUT_ERR_INVALID_ARG, "float images must be 4-byte aligned");
+    const size_t bytes = static_cast<size_t>(B) * 3 * H * W * es;
+    const char *xs = static_cast<const char *>(x), *ys = static_cast<const char *>(y);
+    if (xs < ys + bytes && ys < xs + bytes) return fail(SVDLUT_ERR_INVALID_ARG, "x and y overlap");
+
+    const int tiles_img = ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH);
+    for (int b0 = 0; b0 < B; b0 += kPlainChunk) {
+        LaunchArgs<kPlainChunk> a{};
+        a.n = std::min(kPlainChunk, B - b0);
+        for (int i = 0; i < a.n; ++i) {
+            a.img[i] = make_desc(dims, params, b0 + i, H, W, dtype, x, y);
+            a.img[i].tile_begin = i * tiles_img;
+        }
+        a.total_tiles = a.n * tiles_img;
+        a.nvx_max = span_bound(kTileW, W, dims->Dsx);
+        a.nvy_max = span_bound(kTileH, H, dims->Dsy);
+        if ((st = launch_apply(a, dtype, reinterpret_cast<cudaStream_t>(stream), 0)) != SVDLUT_OK) return st;
+    }
+    return SVDLUT_OK;
+}

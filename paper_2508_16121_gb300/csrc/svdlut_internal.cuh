@@ -1,0 +1,58 @@
+// Internal helpers shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+
+#include "svdlut.h"
+
+namespace svdlut {
+
+// ---- error reporting (thread-local message behind svdlut_last_error) ----
+void set_error(const char *fmt, ...);
+void clear_error();
+
+inline svdlut_status fail(svdlut_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    set_error("%s", buf);
+    return s;
+}
+
+inline svdlut_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(SVDLUT_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define SVDLUT_CUDA_TRY(expr)                                          \
+    do {                                                               \
+        cudaError_t _e = (expr);                                       \
+        if (_e != cudaSuccess) return ::svdlut::cuda_fail(_e, #expr);  \
+    } while (0)
+
+// ---- limits of this build ----
+constexpr int kMaxDt = 33;
+constexpr int kMaxK = 48;
+constexpr int kMaxDsc = 64;
+
+// Validate dims against the documented ranges.
+svdlut_status check_dims(const svdlut_dims *d);
+
+// Device properties of the current device, cached per device.
+struct DeviceInfo {
+    int device;
+    int sm_count;
+    int max_smem_optin;
+};
+svdlut_status device_info(DeviceInfo *out);
+
+inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace svdlut

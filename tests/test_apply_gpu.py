@@ -1,0 +1,148 @@
+"""GPU parity of svdlut_apply (through the C ABI) against the FP64 oracle.
+
+Bar: max-abs <= 2e-5 on FP32 outputs; <= 1 LSB on 8-bit outputs.  Sizes
+span several 128x32 tiles with ragged tails, plus the degenerate shapes
+(W = 1, H = 1, 1x1), W not a multiple of 4, misaligned views, clamped
+inputs, every K regime, D_t in {2, 17, 33} and the full rank.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import svdlut_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def sv():
+    import torch
+    import paper_2508_16121_gb300 as svdlut
+    from paper_2508_16121_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return svdlut
+
+
+def run(sv, x, p, dtype="f32"):
+    import torch
+    xt = torch.from_numpy(x).cuda()
+    y = sv.apply(xt, sv.to_device(p))
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def check_f32(sv, d, x, p, tol=TOL):
+    y = run(sv, x, p).astype(np.float64)
+    ref = oracle.forward(d, p, x)
+    err = np.abs(y - ref).max()
+    assert err <= tol, err
+    return err
+
+
+@pytest.mark.parametrize("HW", [(256, 256), (1, 1), (1, 37), (29, 1), (33, 130), (67, 257), (130, 515)])
+def test_f32_spatial_dims(sv, HW):
+    H, W = HW
+    d = si.spatial_dims(H, W)
+    x, p = si.make_batch(si.config_seed(0) + H * 7 + W, 1, H, W, d)
+    check_f32(sv, d, x, p)
+
+
+@pytest.mark.parametrize("d", [si.paper_dims(), si.Dims(2, 1, 3, 2, 2, 2), si.Dims(17, 8, 8, 9, 5, 33),
+                               si.Dims(33, 33, 0, 2, 2, 2), si.Dims(5, 3, 1, 3, 4, 2), si.Dims(33, 8, 48, 17, 17, 33)])
+def test_f32_dims_variants(sv, d):
+    x, p = si.make_batch(77, 1, 70, 260, d)
+    check_f32(sv, d, x, p)
+
+
+def test_batch_of_three(sv):
+    d = si.spatial_dims(48, 200)
+    x, p = si.make_batch(5, 3, 48, 200, d)
+    check_f32(sv, d, x, p)
+
+
+def test_batch_larger_than_one_launch_chunk(sv):
+    d = si.Dims(9, 2, 3, 4, 4, 5)
+    x, p = si.make_batch(6, 19, 9, 20, d)
+    check_f32(sv, d, x, p)
+
+
+def test_identity_reproduces_input(sv):
+    d = si.spatial_dims(40, 300)
+    x = si.make_image(np.random.default_rng(3), 40, 300)
+    p = {k: v.astype(np.float32) for k, v in si.identity_params(d).items()}
+    y = run(sv, x, p)
+    assert np.abs(y - x).max() <= 1e-6
+
+
+def test_clamped_inputs(sv):
+    d = si.spatial_dims(20, 44)
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-0.5, 1.5, size=(3, 20, 44)).astype(np.float32)
+    p = si.make_params(rng, d)
+    check_f32(sv, d, x, p)
+
+
+def test_misaligned_views_use_scalar_path(sv):
+    import torch
+    d = si.spatial_dims(16, 64)
+    x, p = si.make_batch(8, 1, 16, 64, d)
+    buf = torch.zeros(x.size + 1, dtype=torch.float32, device="cuda")
+    xv = buf[1:].view(x.shape)
+    xv.copy_(torch.from_numpy(x))
+    out = torch.zeros(x.size + 1, dtype=torch.float32, device="cuda")
+    yv = out[1:].view(x.shape)
+    sv.apply(xv, sv.to_device(p), out=yv)
+    torch.cuda.synchronize()
+    ref = oracle.forward(d, p, x)
+    assert np.abs(yv.cpu().numpy() - ref).max() <= TOL
+
+
+@pytest.mark.parametrize("HW", [(256, 256), (35, 129), (1, 5)])
+def test_u8_within_one_lsb(sv, HW):
+    import torch
+    H, W = HW
+    d = si.spatial_dims(H, W)
+    x, p = si.make_batch(9 + H, 1, H, W, d)
+    x8 = si.to_u8(x)
+    y8 = sv.apply(torch.from_numpy(x8).cuda(), sv.to_device(p))
+    torch.cuda.synchronize()
+    ref = oracle.quantize_u8(oracle.forward(d, p, oracle.u8_to_unit(x8)))
+    diff = np.abs(y8.cpu().numpy().astype(int) - ref.astype(int))
+    assert diff.max() <= 1
+    assert (diff > 0).mean() < 1e-3
+
+
+def test_deterministic(sv):
+    d = si.spatial_dims(64, 256)
+    x, p = si.make_batch(10, 2, 64, 256, d)
+    a = run(sv, x, p)
+    b = run(sv, x, p)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", ["mix"])
+def test_4k_full_size(sv, mode):
+    """The 3840x2160 bench workload, FP32, in the launch configuration the
+    benchmark times, against the full oracle (OpenMP)."""
+    H, W = 2160, 3840
+    d = si.spatial_dims(H, W)
+    x, p = si.make_batch(si.config_seed(1), 1, H, W, d, mode=mode)
+    y = run(sv, x, p).astype(np.float64)
+    ref = oracle.forward(d, p, x)
+    assert np.abs(y - ref).max() <= TOL
+
+
+def test_4k_u8_sampled_rows(sv):
+    import torch
+    H, W = 2160, 3840
+    d = si.spatial_dims(H, W)
+    x, p = si.make_batch(si.config_seed(1), 1, H, W, d)
+    x8 = si.to_u8(x)
+    y8 = sv.apply(torch.from_numpy(x8).cuda(), sv.to_device(p)).cpu().numpy()
+    ref = oracle.quantize_u8(oracle.forward(d, p, oracle.u8_to_unit(x8)))
+    diff = np.abs(y8.astype(int) - ref.astype(int))
+    assert diff.max() <= 1
