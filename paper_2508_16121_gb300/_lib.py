@@ -43,7 +43,7 @@ def load(build_if_missing: bool = False):
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
+        path = os.environ.get("SVDLUT_LIB") or _build.LIB
         if build_if_missing and (not os.path.exists(path) or _build.needs_build()):
             _build.build()
         if not os.path.exists(path):

@@ -1,31 +1,44 @@
 // Fused 2D slicing + 2D LUT transform kernel (Eq. 8, Supp. Eq. 20) for sm_103a.
 //
-// One persistent CTA per SM walks a contiguous range of 128 x 32 pixel tiles.
+// One persistent CTA per SM walks a contiguous range of 128 x kTileH pixel
+// tiles; each warp owns kRowsPerWarp consecutive rows of a tile, a lane owns 4
+// consecutive pixels of a row (one 16-byte load/store per plane).
 //  - Prologue, once per image a CTA meets: the nine 2D LUTs are rebuilt from
 //    their SVD factors (Eq. 7) in shared memory, multiplied by their LUT
 //    weights (Eq. 4) and turned into per-cell bilinear coefficients
-//    (a, b, c, d: phi = a + b da + c db + d da db, Supp. Eq. 13) for the three
-//    output channels, 3 float4 per cell and pair.
-//  - Per tile: the grid planes of the tile's spatial footprint are read from
-//    L2, summed over the grids that feed each output channel (grid k feeds
-//    channel k mod 3, Supp. Eq. 20) with their weights (Eq. 19), and
-//    pre-interpolated along y per tile row (planes xy and yc) so the per-pixel
-//    slicing needs two float4 and three float2 shared-memory reads.
-//  - Per pixel: 3 x 16-byte coalesced loads (one per plane, 4 pixels per
-//    thread), 9 LDS.128 for the three LUT pairs, grid reads, 3 x 16-byte
-//    streaming stores.  The next tile's pixels are loaded before the current
-//    tile's setup so HBM traffic overlaps compute.
+//    (phi = a + b da + c db + d da db, Supp. Eq. 13) for the three output
+//    channels: 3 float4 per cell and pair.
+//  - Per tile: the raw grid slices of the tile's footprint are staged in
+//    shared memory with cp.async during the previous tile, then summed over
+//    the grids that feed each output channel (grid k feeds channel k mod 3,
+//    Supp. Eq. 20) with their weights (Eq. 19).  The xc plane is packed as
+//    (x, x+1) x (j, j+1) corners.
+//  - Per row: a warp interpolates the xy and yc slices along y for its row.
+//  - Per pixel: 9 LDS.128 for the three LUT pairs, 2 LDS.128 (xy), 3 LDS.128
+//    (xc) and 3 LDS.64 (yc).  Row data is loaded one row ahead, across tile
+//    boundaries.
 #pragma once
 
 #include "svdlut_internal.cuh"
 
 namespace svdlut {
 
-constexpr int kThreads = 512;
-constexpr int kWarps = kThreads / 32;
+#ifndef SVDLUT_WARPS
+#define SVDLUT_WARPS 16
+#endif
+#ifndef SVDLUT_ROWS_PER_WARP
+#define SVDLUT_ROWS_PER_WARP 4
+#endif
+#ifndef SVDLUT_STAGE
+#define SVDLUT_STAGE 0
+#endif
+constexpr int kWarps = SVDLUT_WARPS;
+constexpr int kThreads = kWarps * 32;
+constexpr int kRowsPerWarp = SVDLUT_ROWS_PER_WARP;
 constexpr int kTileW = 128;  // 32 lanes x 4 pixels
-constexpr int kTileH = 32;
-constexpr int kRowsPerWarp = kTileH / kWarps;
+constexpr int kTileH = kWarps * kRowsPerWarp;
+constexpr bool kStage = SVDLUT_STAGE != 0;
+static_assert(kTileW + kTileH <= kThreads, "row/column tables need one thread each");
 
 struct ImgDesc {
     const void *x;
@@ -43,20 +56,14 @@ struct LaunchArgs {
     int n;            // images in img[]
     int total_tiles;  // sum of tiles over images
     int nvx_max, nvy_max;
-    int lcell_floats;  // floats reserved for the cell table
-    int scratch_floats;
+    int lcell_floats;    // floats reserved for the cell table
+    int stage_floats;    // floats of the grid-slice staging area (0: read grids from global)
+    int scratch_floats;  // floats of the tile buffers / prologue temporaries
     ImgDesc img[N];
 };
 
-// ---- host/device shared small helpers ----
-__host__ __device__ inline int cell_index(float u, int D)
-{
-    int i = static_cast<int>(u);  // u >= 0
-    return i < D - 2 ? i : D - 2;
-}
-
 // Spatial cell of pixel index x on an axis of n pixels and Ds vertices
-// (x' = x/(n-1), u = x' (Ds-1), Supp. Eq. 15-16), computed exactly in
+// (x' = x/(n-1), u = x' (Ds-1), Supp. Eqs. 15-16), computed exactly in
 // integers: i = floor(x (Ds-1) / (n-1)) clamped to Ds-2, delta = remainder
 // / (n-1).  A float product x * (Ds-1)/(n-1) would lose up to half an ulp of
 // u (1.5e-5 at u ~ 479), too much for the grid term at 4K.
@@ -84,25 +91,9 @@ inline int span_bound(int extent, int n, int Ds)
     return v < Ds ? v : Ds;
 }
 
-// Shared-memory floats needed by the tile buffers (see build_tile).
-__host__ __device__ inline int tile_floats(int nvx, int nvy, int Dsc)
-{
-    int fxy = 3 * nvy * nvx, fxc = 3 * nvx * Dsc, fyc = 3 * nvy * Dsc;
-    int a = (fxy + fxc + fyc + 3) & ~3;
-    int rxy = kTileH * nvx * 4;
-    int pxc = 3 * nvx * (Dsc - 1) * 2;
-    int ryc = kTileH * 3 * (Dsc - 1) * 2;
-    return a + rxy + pxc + ryc;
-}
-
-// Shared-memory floats needed by the LUT prologue temporaries (one pair at a time).
-__host__ __device__ inline int prologue_floats(int D, int R)
-{
-    int fac = ((2 * 3 * D * R) + 3) & ~3;
-    return fac + D * D * 4;
-}
-
-__host__ __device__ inline int lcell_floats(int D) { return 3 * (D - 1) * (D - 1) * 12; }
+// Cell table: per pair (D-1) rows of cells with a row stride of D cells (one
+// cell of padding) so that the bank of a cell depends on both of its indices.
+__host__ __device__ inline int lcell_floats(int D) { return 3 * (D - 1) * D * 12; }
 
 constexpr int kMiscFloats = kMaxK * 4 + 4;
 
@@ -137,45 +128,50 @@ struct PixIO<float> {
     }
 };
 
-__device__ __forceinline__ unsigned char quant_u8(float y)
+// Round-half-even of clamp(y,0,1)*255 on the FMA pipe: after adding 1.5*2^23
+// the low byte of the bit pattern is the rounded integer (0..255).
+__device__ __forceinline__ unsigned int quant_u8_bits(float y)
 {
     y = fminf(fmaxf(y, 0.f), 1.f);
-    return static_cast<unsigned char>(__float2int_rn(y * 255.f));
+    return static_cast<unsigned int>(__float_as_int(fmaf(y, 255.f, 12582912.0f)));
 }
 
 template <>
 struct PixIO<uint8_t> {
-    using Raw = uchar4;
+    // four pixels packed in one 32-bit word, byte k = pixel k
+    using Raw = unsigned int;
     static __device__ __forceinline__ Raw load(const uint8_t *p, int n, bool vec)
     {
-        if (vec && n == 4) {
-            unsigned int w = __ldcs(reinterpret_cast<const unsigned int *>(p));
-            return make_uchar4(w & 0xff, (w >> 8) & 0xff, (w >> 16) & 0xff, w >> 24);
-        }
-        Raw v = make_uchar4(0, 0, 0, 0);
-        if (n > 0) v.x = p[0];
-        if (n > 1) v.y = p[1];
-        if (n > 2) v.z = p[2];
-        if (n > 3) v.w = p[3];
-        return v;
+        if (vec && n == 4) return __ldcs(reinterpret_cast<const unsigned int *>(p));
+        unsigned int w = 0;
+        if (n > 0) w |= static_cast<unsigned int>(p[0]);
+        if (n > 1) w |= static_cast<unsigned int>(p[1]) << 8;
+        if (n > 2) w |= static_cast<unsigned int>(p[2]) << 16;
+        if (n > 3) w |= static_cast<unsigned int>(p[3]) << 24;
+        return w;
     }
-    static __device__ __forceinline__ float4 to_float(Raw v)
+    // v/255 with the integer placed in the mantissa of 2^23 (no I2F)
+    static __device__ __forceinline__ float4 to_float(Raw w)
     {
-        const float k = 1.0f / 255.0f;
-        return make_float4(v.x * k, v.y * k, v.z * k, v.w * k);
+        const float k = 1.0f / 255.0f, m = 8388608.0f;
+        const float a = __int_as_float(__byte_perm(w, 0x4B000000u, 0x7440)) - m;
+        const float b = __int_as_float(__byte_perm(w, 0x4B000000u, 0x7441)) - m;
+        const float c = __int_as_float(__byte_perm(w, 0x4B000000u, 0x7442)) - m;
+        const float d = __int_as_float(__byte_perm(w, 0x4B000000u, 0x7443)) - m;
+        return make_float4(a * k, b * k, c * k, d * k);
     }
     static __device__ __forceinline__ void store(uint8_t *p, float4 v, int n, bool vec)
     {
-        uchar4 q = make_uchar4(quant_u8(v.x), quant_u8(v.y), quant_u8(v.z), quant_u8(v.w));
+        const unsigned int w = __byte_perm(__byte_perm(quant_u8_bits(v.x), quant_u8_bits(v.y), 0x0040),
+                                           __byte_perm(quant_u8_bits(v.z), quant_u8_bits(v.w), 0x0040), 0x5410);
         if (vec && n == 4) {
-            unsigned int w = q.x | (q.y << 8) | (q.z << 16) | (static_cast<unsigned int>(q.w) << 24);
             __stcs(reinterpret_cast<unsigned int *>(p), w);
             return;
         }
-        if (n > 0) p[0] = q.x;
-        if (n > 1) p[1] = q.y;
-        if (n > 2) p[2] = q.z;
-        if (n > 3) p[3] = q.w;
+        if (n > 0) p[0] = w & 0xff;
+        if (n > 1) p[1] = (w >> 8) & 0xff;
+        if (n > 2) p[2] = (w >> 16) & 0xff;
+        if (n > 3) p[3] = w >> 24;
     }
 };
 
@@ -184,14 +180,42 @@ __device__ __forceinline__ float get(const float4 &v, int k)
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
-// ---- LUT prologue: Eq. 7 reconstruction, Eq. 4 weight fold, cell coefficients ----
-__device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, float *misc)
+// Cell of p in [0,1] on an axis with D vertices (fDm1 = D-1, fDm2 = D-2), on
+// the FMA pipe: i = round-to-nearest(min(p (D-1) - 1/2, D-2)) via the
+// 1.5 * 2^23 magic constant, frac = p (D-1) - i in [0, 1].  This is the
+// Supp. Eq. 12 cell except exactly on a vertex, where the cell below may be
+// chosen with frac = 1; bilinear interpolation is continuous there, so the
+// value is the same.
+__device__ __forceinline__ int cell_of(float p, float fDm1, float fDm2, float &frac)
 {
-    const int tid = threadIdx.x;
-    const int D = d.D, R = d.R, DR = D * R, Dm1 = D - 1;
-    float *sU = tmp;                                   // [3 c][D][R] = U * S * w
-    float *sV = tmp + 3 * DR;                          // [3 c][D][R]
-    float4 *vt = reinterpret_cast<float4 *>(tmp + ((2 * 3 * DR + 3) & ~3));  // [D][D]
+    const float t = fminf(fmaf(p, fDm1, -0.5f), fDm2);
+    const float m = t + 12582912.0f;
+    frac = fmaf(p, fDm1, -(m - 12582912.0f));
+    return __float_as_int(m) - 0x4B400000;
+}
+
+// ---- LUT prologue: Eq. 7 reconstruction, Eq. 4 weight fold, cell coefficients ----
+// Factor rows are padded to an odd stride so that lanes reading different
+// rows hit different banks.
+__host__ __device__ inline int padded_rank(int R) { return R | 1; }
+
+// Shared-memory floats of the prologue temporaries: factors of all nine
+// tables at once (pairs = 3) or of one pair at a time (pairs = 1).
+__host__ __device__ inline int prologue_floats_n(int D, int R, int pairs)
+{
+    return (((2 * 3 * pairs * D * (R | 1)) + 3) & ~3) + D * D * 4;
+}
+
+__device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, float *misc, int tmp_floats)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int D = d.D, R = d.R, Rp = padded_rank(R), DR = D * R, DRp = D * Rp, Dm1 = D - 1;
+    // all nine tables' factors at once when they fit (one global round trip)
+    const int pairs_at_once = prologue_floats_n(D, R, 3) <= tmp_floats ? 3 : 1;
+    const int nf = 3 * pairs_at_once;  // (c, p) tables held
+    float *sU = tmp;                   // [nf][D][Rp] = U * S * w
+    float *sV = tmp + nf * DRp;        // [nf][D][Rp]
+    float4 *vt = reinterpret_cast<float4 *>(tmp + ((2 * nf * DRp + 3) & ~3));  // [D][D]
 
     // grid weights and summed biases
     for (int e = tid; e < d.K * 4; e += kThreads) misc[e] = __ldg(d.gw + e);
@@ -200,41 +224,49 @@ __device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, f
         for (int k = tid; k < d.K; k += 3) b += __ldg(d.gw + k * 4 + 3);
         misc[kMaxK * 4 + tid] = b;
     }
+    const int nc = Dm1 * D;  // padded cells per pair
     for (int p = 0; p < 3; ++p) {
-        for (int e = tid; e < 3 * DR; e += kThreads) {
-            int c = e / DR, ir = e - c * DR, r = ir % R;
-            int cp = c * 3 + p;
-            sU[e] = __ldg(d.U + cp * DR + ir) * __ldg(d.S + cp * R + r) * __ldg(d.lw + c * 4 + p);
-            sV[e] = __ldg(d.V + cp * DR + ir);
-        }
-        __syncthreads();
-        for (int e = tid; e < D * D; e += kThreads) {
-            int i = e / D, j = e - i * D;
-            float acc[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float *u = sU + c * DR + i * R;
-                const float *v = sV + c * DR + j * R;
-                float a = 0.f;
-                for (int r = 0; r < R; ++r) a = fmaf(u[r], v[r], a);
-                acc[c] = a;
+        if (pairs_at_once == 1 || p == 0) {
+            // slot <-> (c, p): slot = c * 3 + p when all pairs are held, else c
+            for (int e = tid; e < nf * DR; e += kThreads) {
+                const int slot = e / DR, ir = e - slot * DR, i = ir / R, r = ir - i * R;
+                const int c = slot / pairs_at_once, pp = pairs_at_once == 3 ? slot - c * 3 : p;
+                const int cp = c * 3 + pp;
+                sU[slot * DRp + i * Rp + r] =
+                    __ldg(d.U + cp * DR + ir) * __ldg(d.S + cp * R + r) * __ldg(d.lw + c * 4 + pp);
+                sV[slot * DRp + i * Rp + r] = __ldg(d.V + cp * DR + ir);
             }
-            vt[e] = make_float4(acc[0], acc[1], acc[2], 0.f);
+            __syncthreads();
+        }
+        for (int i = warp; i < D; i += kWarps) {
+            for (int j = lane; j < D; j += 32) {
+                float acc[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int slot = pairs_at_once == 3 ? c * 3 + p : c;
+                    const float *u = sU + slot * DRp + i * Rp;
+                    const float *v = sV + slot * DRp + j * Rp;
+                    float a = 0.f;
+                    for (int r = 0; r < R; ++r) a = fmaf(u[r], v[r], a);
+                    acc[c] = a;
+                }
+                vt[i * D + j] = make_float4(acc[0], acc[1], acc[2], 0.f);
+            }
         }
         __syncthreads();
-        const int nc = Dm1 * Dm1;
-        for (int e = tid; e < nc; e += kThreads) {
-            int i = e / Dm1, j = e - i * Dm1;
-            float4 v00 = vt[i * D + j], v10 = vt[(i + 1) * D + j];
-            float4 v01 = vt[i * D + j + 1], v11 = vt[(i + 1) * D + j + 1];
-            float4 b = make_float4(v10.x - v00.x, v10.y - v00.y, v10.z - v00.z, 0.f);
-            float4 c = make_float4(v01.x - v00.x, v01.y - v00.y, v01.z - v00.z, 0.f);
-            float4 dd = make_float4(v11.x - v10.x - v01.x + v00.x, v11.y - v10.y - v01.y + v00.y,
-                                    v11.z - v10.z - v01.z + v00.z, 0.f);
-            float4 *q = lcell + (p * nc + e) * 3;
-            q[0] = make_float4(v00.x, v00.y, v00.z, b.x);
-            q[1] = make_float4(b.y, b.z, c.x, c.y);
-            q[2] = make_float4(c.z, dd.x, dd.y, dd.z);
+        for (int i = warp; i < Dm1; i += kWarps) {
+            for (int j = lane; j < Dm1; j += 32) {
+                const float4 v00 = vt[i * D + j], v10 = vt[(i + 1) * D + j];
+                const float4 v01 = vt[i * D + j + 1], v11 = vt[(i + 1) * D + j + 1];
+                const float bx = v10.x - v00.x, by = v10.y - v00.y, bz = v10.z - v00.z;
+                const float cx = v01.x - v00.x, cy = v01.y - v00.y, cz = v01.z - v00.z;
+                const float dx = v11.x - v10.x - v01.x + v00.x, dy = v11.y - v10.y - v01.y + v00.y,
+                            dz = v11.z - v10.z - v01.z + v00.z;
+                float4 *q = lcell + (p * nc + i * D + j) * 3;
+                q[0] = make_float4(v00.x, v00.y, v00.z, bx);
+                q[1] = make_float4(by, bz, cx, cy);
+                q[2] = make_float4(cz, dx, dy, dz);
+            }
         }
         __syncthreads();
     }
@@ -264,101 +296,198 @@ __device__ __forceinline__ TileGeom tile_geom(const ImgDesc &d, int lt, int nvx_
     return g;
 }
 
+// Tile buffers (floats, in this order):
+//   fxy [3][nvy][nvx], fxc [3][nvx][Dsc], fyc [3][nvy][Dsc]   folded grid slices
+//   rowi [kTileH] int, rowd [kTileH], coli [kTileW] int, cold [kTileW]
+//   pxc [3][nvx-1][Dsc] float4   xc corners (x, x+1) x (j, j+1); row stride Dsc
+//                                (one padding entry) to spread banks
+//   per warp: rxy [nvx] float4 (xy interpolated along y for the warp's row),
+//             ryc [3][Dsc-1] float2 (yc interpolated along y, (j, j+1))
 struct TileBufs {
     float *fxy, *fxc, *fyc;
-    float4 *rxy;
-    float2 *pxc, *ryc;
+    int *rowi, *coli;
+    float *rowd, *cold;
+    float4 *pxc, *rxy;
+    float2 *ryc;
 };
+
+// rounded to 4 floats so every warp's float4 table stays 16-byte aligned
+__host__ __device__ inline int warp_row_floats(int nvx, int Dsc) { return (nvx * 4 + 3 * (Dsc - 1) * 2 + 3) & ~3; }
+
+__host__ __device__ inline int tile_floats(int nvx, int nvy, int Dsc)
+{
+    int a = (3 * nvy * nvx + 3 * nvx * Dsc + 3 * nvy * Dsc + 3) & ~3;
+    int tabs = 2 * kTileH + 2 * kTileW;
+    int pxc = 3 * (nvx - 1) * Dsc * 4;
+    int rows = kWarps * warp_row_floats(nvx, Dsc);
+    return a + tabs + pxc + rows;
+}
 
 __device__ __forceinline__ TileBufs tile_bufs(float *scratch, int nvx, int nvy, int Dsc)
 {
     TileBufs b;
+    const int warp = threadIdx.x >> 5;
     b.fxy = scratch;
     b.fxc = b.fxy + 3 * nvy * nvx;
     b.fyc = b.fxc + 3 * nvx * Dsc;
-    float *after = scratch + ((3 * nvy * nvx + 3 * nvx * Dsc + 3 * nvy * Dsc + 3) & ~3);
-    b.rxy = reinterpret_cast<float4 *>(after);
-    b.pxc = reinterpret_cast<float2 *>(after + kTileH * nvx * 4);
-    b.ryc = b.pxc + 3 * nvx * (Dsc - 1);
+    float *t = scratch + ((3 * nvy * nvx + 3 * nvx * Dsc + 3 * nvy * Dsc + 3) & ~3);
+    b.rowi = reinterpret_cast<int *>(t);
+    b.rowd = t + kTileH;
+    b.coli = reinterpret_cast<int *>(t + 2 * kTileH);
+    b.cold = t + 2 * kTileH + kTileW;
+    b.pxc = reinterpret_cast<float4 *>(t + 2 * kTileH + 2 * kTileW);
+    float *w = reinterpret_cast<float *>(b.pxc + 3 * (nvx - 1) * Dsc) + warp * warp_row_floats(nvx, Dsc);
+    b.rxy = reinterpret_cast<float4 *>(w);
+    b.ryc = reinterpret_cast<float2 *>(w + nvx * 4);
     return b;
 }
 
-// Phase A (grid planes of the tile footprint, folded per output channel) and
-// phase B (y-interpolated rows, (j, j+1) pairs).  Ends with a barrier.
-__device__ inline void build_tile(const ImgDesc &d, const TileGeom &g, const TileBufs &b,
-                                  const float *misc)
+// ---- asynchronous staging of a tile's raw grid slices (cp.async, 4 bytes) ----
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
 {
-    const int tid = threadIdx.x;
+    const unsigned int sa = static_cast<unsigned int>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Raw slices of tile g: xy [K][nvy][nvx], xc [K][nvx][Dsc], yc [K][nvy][Dsc].
+__host__ __device__ inline int stage_floats(int K, int nvx, int nvy, int Dsc)
+{
+    return K * (nvy * nvx + nvx * Dsc + nvy * Dsc);
+}
+
+__device__ inline void issue_stage(const ImgDesc &d, const TileGeom &g, float *stage)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int K = d.K, nvx = g.nvx, nvy = g.nvy, Dsc = d.Dsc;
+    float *sxy = stage, *sxc = sxy + K * nvy * nvx, *syc = sxc + K * nvx * Dsc;
+    for (int r = warp; r < K * nvy; r += kWarps) {  // r = k * nvy + iyl
+        const int k = r / nvy, iyl = r - k * nvy;
+        const float *src = d.gxy + (static_cast<size_t>(k) * d.Dsy + g.iylo + iyl) * d.Dsx + g.ixlo;
+        for (int ixl = lane; ixl < nvx; ixl += 32) cp_async4(sxy + r * nvx + ixl, src + ixl);
+    }
+    for (int r = warp; r < K * nvx; r += kWarps) {  // r = k * nvx + ixl
+        const int k = r / nvx, ixl = r - k * nvx;
+        const float *src = d.gxc + (static_cast<size_t>(k) * d.Dsx + g.ixlo + ixl) * Dsc;
+        for (int j = lane; j < Dsc; j += 32) cp_async4(sxc + r * Dsc + j, src + j);
+    }
+    for (int r = warp; r < K * nvy; r += kWarps) {  // r = k * nvy + iyl
+        const int k = r / nvy, iyl = r - k * nvy;
+        const float *src = d.gyc + (static_cast<size_t>(k) * d.Dsy + g.iylo + iyl) * Dsc;
+        for (int j = lane; j < Dsc; j += 32) cp_async4(syc + r * Dsc + j, src + j);
+    }
+    cp_async_commit();
+}
+
+// Phase A: grid slices of the tile footprint folded per output channel
+// (sum over grids k = c mod 3 with their weights), read from the staging area
+// when present, else from global memory; row and column cell tables.
+__device__ inline void tile_phase_a(const ImgDesc &d, const TileGeom &g, const TileBufs &b,
+                                    const float *misc, const float *stage)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nvx = g.nvx, nvy = g.nvy, Dsc = d.Dsc, K = d.K;
-    // phase A
-    for (int e = tid; e < 3 * nvy * nvx; e += kThreads) {
-        int c = e / (nvy * nvx), r = e - c * nvy * nvx, iyl = r / nvx, ixl = r - iyl * nvx;
-        float s = 0.f;
-        for (int k = c; k < K; k += 3)
-            s = fmaf(misc[k * 4 + 0],
-                     __ldg(d.gxy + (static_cast<size_t>(k) * d.Dsy + g.iylo + iyl) * d.Dsx + g.ixlo + ixl), s);
-        b.fxy[e] = s;
+    const float *sxy = stage, *sxc = stage + K * nvy * nvx, *syc = sxc + K * nvx * Dsc;
+    for (int r = warp; r < 3 * nvy; r += kWarps) {
+        const int c = r / nvy, iyl = r - c * nvy;
+        for (int ixl = lane; ixl < nvx; ixl += 32) {
+            float s = 0.f;
+            for (int k = c; k < K; k += 3) {
+                const float v = stage ? sxy[(k * nvy + iyl) * nvx + ixl]
+                                      : __ldg(d.gxy + (static_cast<size_t>(k) * d.Dsy + g.iylo + iyl) * d.Dsx + g.ixlo + ixl);
+                s = fmaf(misc[k * 4 + 0], v, s);
+            }
+            b.fxy[r * nvx + ixl] = s;
+        }
     }
-    for (int e = tid; e < 3 * nvx * Dsc; e += kThreads) {
-        int c = e / (nvx * Dsc), r = e - c * nvx * Dsc, ixl = r / Dsc, j = r - ixl * Dsc;
-        float s = 0.f;
-        for (int k = c; k < K; k += 3)
-            s = fmaf(misc[k * 4 + 1],
-                     __ldg(d.gxc + (static_cast<size_t>(k) * d.Dsx + g.ixlo + ixl) * Dsc + j), s);
-        b.fxc[e] = s;
+    for (int r = warp; r < 3 * nvx; r += kWarps) {
+        const int c = r / nvx, ixl = r - c * nvx;
+        for (int j = lane; j < Dsc; j += 32) {
+            float s = 0.f;
+            for (int k = c; k < K; k += 3) {
+                const float v = stage ? sxc[(k * nvx + ixl) * Dsc + j]
+                                      : __ldg(d.gxc + (static_cast<size_t>(k) * d.Dsx + g.ixlo + ixl) * Dsc + j);
+                s = fmaf(misc[k * 4 + 1], v, s);
+            }
+            b.fxc[r * Dsc + j] = s;
+        }
     }
-    for (int e = tid; e < 3 * nvy * Dsc; e += kThreads) {
-        int c = e / (nvy * Dsc), r = e - c * nvy * Dsc, iyl = r / Dsc, j = r - iyl * Dsc;
-        float s = 0.f;
-        for (int k = c; k < K; k += 3)
-            s = fmaf(misc[k * 4 + 2],
-                     __ldg(d.gyc + (static_cast<size_t>(k) * d.Dsy + g.iylo + iyl) * Dsc + j), s);
-        b.fyc[e] = s;
+    for (int r = warp; r < 3 * nvy; r += kWarps) {
+        const int c = r / nvy, iyl = r - c * nvy;
+        for (int j = lane; j < Dsc; j += 32) {
+            float s = 0.f;
+            for (int k = c; k < K; k += 3) {
+                const float v = stage ? syc[(k * nvy + iyl) * Dsc + j]
+                                      : __ldg(d.gyc + (static_cast<size_t>(k) * d.Dsy + g.iylo + iyl) * Dsc + j);
+                s = fmaf(misc[k * 4 + 2], v, s);
+            }
+            b.fyc[r * Dsc + j] = s;
+        }
     }
-    __syncthreads();
-    // phase B
-    for (int e = tid; e < kTileH * nvx; e += kThreads) {
-        int row = e / nvx, ixl = e - row * nvx;
-        int y = min(g.y0 + row, d.H - 1);
+    if (tid < kTileW) {
+        int ix;
+        float dx;
+        spatial_cell(min(g.x0 + tid, d.W - 1), d.W, d.Dsx, d.rW1, ix, dx);
+        b.coli[tid] = max(0, min(ix - g.ixlo, nvx - 2));
+        b.cold[tid] = dx;
+    } else if (tid < kTileW + kTileH) {
+        const int row = tid - kTileW;
         int iy;
         float dy;
-        spatial_cell(y, d.H, d.Dsy, d.rH1, iy, dy);
-        int iyl = min(iy - g.iylo, nvy - 2);
+        spatial_cell(min(g.y0 + row, d.H - 1), d.H, d.Dsy, d.rH1, iy, dy);
+        b.rowi[row] = max(0, min(iy - g.iylo, nvy - 2));
+        b.rowd[row] = dy;
+    }
+}
+
+// Phase B: corner packs of the folded xc slice.
+__device__ inline void tile_phase_b(const ImgDesc &d, const TileGeom &g, const TileBufs &b)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nvx = g.nvx, Dsc = d.Dsc, Dc1 = Dsc - 1;
+    for (int r = warp; r < 3 * (nvx - 1); r += kWarps) {
+        const int c = r / (nvx - 1), ixl = r - c * (nvx - 1);
+        const float *f0 = b.fxc + (c * nvx + ixl) * Dsc;
+        const float *f1 = f0 + Dsc;
+        for (int j = lane; j < Dc1; j += 32) b.pxc[r * Dsc + j] = make_float4(f0[j], f0[j + 1], f1[j], f1[j + 1]);
+    }
+}
+
+// Per-warp tables of one tile row: xy and yc slices interpolated along y.
+__device__ __forceinline__ void warp_row_tables(const TileGeom &g, const TileBufs &b, int Dsc, int row)
+{
+    const int lane = threadIdx.x & 31;
+    const int nvx = g.nvx, nvy = g.nvy, Dc1 = Dsc - 1;
+    const int iyl = b.rowi[row];
+    const float dy = b.rowd[row];
+    for (int ixl = lane; ixl < nvx; ixl += 32) {
         float v[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float a0 = b.fxy[(c * nvy + iyl) * nvx + ixl], a1 = b.fxy[(c * nvy + iyl + 1) * nvx + ixl];
+            const float a0 = b.fxy[(c * nvy + iyl) * nvx + ixl];
+            const float a1 = b.fxy[(c * nvy + iyl + 1) * nvx + ixl];
             v[c] = fmaf(a1 - a0, dy, a0);
         }
-        b.rxy[e] = make_float4(v[0], v[1], v[2], 0.f);
+        b.rxy[ixl] = make_float4(v[0], v[1], v[2], 0.f);
     }
-    const int Dc1 = Dsc - 1;
-    for (int e = tid; e < 3 * nvx * Dc1; e += kThreads) {
-        int cx = e / Dc1, j = e - cx * Dc1;  // cx = c * nvx + ixl
-        b.pxc[e] = make_float2(b.fxc[cx * Dsc + j], b.fxc[cx * Dsc + j + 1]);
-    }
-    for (int e = tid; e < kTileH * 3 * Dc1; e += kThreads) {
-        int rc = e / Dc1, j = e - rc * Dc1, row = rc / 3, c = rc - row * 3;
-        int y = min(g.y0 + row, d.H - 1);
-        int iy;
-        float dy;
-        spatial_cell(y, d.H, d.Dsy, d.rH1, iy, dy);
-        int iyl = min(iy - g.iylo, nvy - 2);
-        const float *r0 = b.fyc + (c * nvy + iyl) * Dsc + j;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float *r0 = b.fyc + (c * nvy + iyl) * Dsc;
         const float *r1 = r0 + Dsc;
-        b.ryc[e] = make_float2(fmaf(r1[0] - r0[0], dy, r0[0]), fmaf(r1[1] - r0[1], dy, r0[1]));
+        for (int j = lane; j < Dc1; j += 32)
+            b.ryc[c * Dc1 + j] = make_float2(fmaf(r1[j] - r0[j], dy, r0[j]), fmaf(r1[j + 1] - r0[j + 1], dy, r0[j + 1]));
     }
-    __syncthreads();
 }
 
 // One LUT pair: add the folded, weighted bilinear value of the three output
-// channels (coefficient form of Supp. Eq. 13).
-__device__ __forceinline__ void lut_pair(const float4 *__restrict__ lc, int cell, float da, float db,
-                                         float &y0, float &y1, float &y2)
+// channels (coefficient form of Supp. Eq. 13).  q points at the cell's 3 float4.
+__device__ __forceinline__ void lut_pair(const float4 *__restrict__ q, float da, float db, float &y0, float &y1,
+                                         float &y2)
 {
-    const float4 q0 = lc[cell * 3 + 0];
-    const float4 q1 = lc[cell * 3 + 1];
-    const float4 q2 = lc[cell * 3 + 2];
+    const float4 q0 = q[0];
+    const float4 q1 = q[1];
+    const float4 q2 = q[2];
     y0 += fmaf(fmaf(q2.y, da, q1.z), db, fmaf(q0.w, da, q0.x));
     y1 += fmaf(fmaf(q2.z, da, q1.w), db, fmaf(q1.x, da, q0.y));
     y2 += fmaf(fmaf(q2.w, da, q2.x), db, fmaf(q1.y, da, q0.z));
@@ -370,7 +499,8 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
     extern __shared__ __align__(16) float smem[];
     float4 *lcell = reinterpret_cast<float4 *>(smem);
     float *misc = smem + a.lcell_floats;
-    float *scratch = misc + kMiscFloats;
+    float *stage = a.stage_floats > 0 ? misc + kMiscFloats : nullptr;
+    float *scratch = misc + kMiscFloats + a.stage_floats;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int G = gridDim.x, gi = blockIdx.x;
@@ -379,124 +509,122 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
     if (t_begin >= t_end) return;
 
     using Raw = typename PixIO<T>::Raw;
-    Raw cur[kRowsPerWarp][3], nxt[kRowsPerWarp][3];
 
     auto find_image = [&](int t) {
         int im = 0;
         while (im + 1 < a.n && a.img[im + 1].tile_begin <= t) ++im;
         return im;
     };
-    auto load_tile = [&](int t, Raw (&dst)[kRowsPerWarp][3]) {
-        const int im = find_image(t);
-        const ImgDesc &d = a.img[im];
+    // loads this lane's 4 pixels of row rr (of this warp) of tile t
+    auto load_row = [&](int t, int rr, Raw (&dst)[3]) {
+        const ImgDesc &d = a.img[find_image(t)];
         const int lt = t - d.tile_begin;
         const int ty = lt / d.tiles_x, tx = lt - ty * d.tiles_x;
         const int x = tx * kTileW + lane * 4;
         const int n = min(4, d.W - x);
+        const int y = ty * kTileH + warp * kRowsPerWarp + rr;
         const size_t plane = static_cast<size_t>(d.H) * d.W;
-        const T *src = static_cast<const T *>(d.x);
+        const T *src = static_cast<const T *>(d.x) + static_cast<size_t>(y) * d.W + x;
 #pragma unroll
-        for (int rr = 0; rr < kRowsPerWarp; ++rr) {
-            const int y = ty * kTileH + warp * kRowsPerWarp + rr;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (y < d.H && n > 0)
-                    dst[rr][c] = PixIO<T>::load(src + c * plane + static_cast<size_t>(y) * d.W + x, n, d.vec);
-                else
-                    dst[rr][c] = Raw{};
-            }
-        }
+        for (int c = 0; c < 3; ++c) dst[c] = (y < d.H && n > 0) ? PixIO<T>::load(src + c * plane, n, d.vec) : Raw();
+    };
+    auto stage_tile = [&](int t) {
+        const ImgDesc &d = a.img[find_image(t)];
+        if (d.K > 0) issue_stage(d, tile_geom(d, t - d.tile_begin, a.nvx_max, a.nvy_max), stage);
     };
 
+    Raw cur[3], nxt[3];
     int cur_im = -1;
-    load_tile(t_begin, cur);
+    load_row(t_begin, 0, cur);
+    if (stage) stage_tile(t_begin);
     for (int t = t_begin; t < t_end; ++t) {
-        if (t + 1 < t_end) load_tile(t + 1, nxt);
         const int im = find_image(t);
         const ImgDesc &d = a.img[im];
         if (im != cur_im) {
             __syncthreads();
-            build_luts(d, lcell, scratch, misc);
+            build_luts(d, lcell, scratch, misc, a.scratch_floats);
             cur_im = im;
         }
         const TileGeom g = tile_geom(d, t - d.tile_begin, a.nvx_max, a.nvy_max);
         const TileBufs b = tile_bufs(scratch, g.nvx, g.nvy, d.Dsc);
-        build_tile(d, g, b, misc);
+        if (stage) cp_async_wait_all();
+        __syncthreads();  // staged slices visible; previous tile's rows done
+        tile_phase_a(d, g, b, misc, stage);
+        __syncthreads();
+        if (stage && t + 1 < t_end) stage_tile(t + 1);  // lands during this tile's rows
+        tile_phase_b(d, g, b);
+        __syncthreads();
 
-        // ---- phase C: pixels ----
-        const int D = d.D, Dm1 = D - 1, Dsc = d.Dsc, Dc1 = Dsc - 1, nc = Dm1 * Dm1;
-        const float fD = static_cast<float>(Dm1), fDs = static_cast<float>(Dc1);
-        const float4 *lc0 = lcell, *lc1 = lcell + nc * 3, *lc2 = lcell + 2 * nc * 3;
+        // ---- rows of this warp ----
+        const int D = d.D, Dsc = d.Dsc, Dc1 = Dsc - 1;
+        const int nc3 = (D - 1) * D * 3;  // float4 per pair table
+        const int D3 = D * 3;             // float4 per cell row
+        const float fD1 = static_cast<float>(D - 1), fD2 = static_cast<float>(D - 2);
+        const float fS1 = static_cast<float>(Dc1), fS2 = static_cast<float>(Dsc - 2);
         const float bias0 = misc[kMaxK * 4 + 0], bias1 = misc[kMaxK * 4 + 1], bias2 = misc[kMaxK * 4 + 2];
         const int xbase = g.x0 + lane * 4;
         const int n = min(4, d.W - xbase);
-        int ixl[4];
-        float dxk[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            int ix;
-            spatial_cell(min(xbase + k, d.W - 1), d.W, d.Dsx, d.rW1, ix, dxk[k]);
-            ixl[k] = max(0, min(ix - g.ixlo, g.nvx - 2));
-        }
+        const int4 ixl4 = reinterpret_cast<const int4 *>(b.coli)[lane];
+        const float4 dx4 = reinterpret_cast<const float4 *>(b.cold)[lane];
+        const int ixl[4] = {ixl4.x, ixl4.y, ixl4.z, ixl4.w};
+        const float dxk[4] = {dx4.x, dx4.y, dx4.z, dx4.w};
+        const int xcs = (g.nvx - 1) * Dsc;  // float4 per channel of pxc
         const size_t plane = static_cast<size_t>(d.H) * d.W;
         T *dst = static_cast<T *>(d.y);
-#pragma unroll
+#pragma unroll 1
         for (int rr = 0; rr < kRowsPerWarp; ++rr) {
+            // next row of this warp, possibly in the next tile
+            if (rr + 1 < kRowsPerWarp) load_row(t, rr + 1, nxt);
+            else if (t + 1 < t_end) load_row(t + 1, 0, nxt);
             const int row = warp * kRowsPerWarp + rr;
             const int y = g.y0 + row;
-            if (y >= d.H || n <= 0) continue;
-            const float4 pr = PixIO<T>::to_float(cur[rr][0]);
-            const float4 pg = PixIO<T>::to_float(cur[rr][1]);
-            const float4 pb = PixIO<T>::to_float(cur[rr][2]);
-            const float4 *rxy = b.rxy + row * g.nvx;
-            const float2 *ryc = b.ryc + row * 3 * Dc1;
-            float out[3][4];
+            warp_row_tables(g, b, Dsc, row);
+            __syncwarp();
+            if (y < d.H && n > 0) {
+                const float4 pr = PixIO<T>::to_float(cur[0]);
+                const float4 pg = PixIO<T>::to_float(cur[1]);
+                const float4 pb = PixIO<T>::to_float(cur[2]);
+                float out[3][4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float p[3] = {get(pr, k), get(pg, k), get(pb, k)};
-                int ic[3], jc[3];
-                float dc[3], ec[3];
+                for (int k = 0; k < 4; ++k) {
+                    float p[3] = {get(pr, k), get(pg, k), get(pb, k)};
+                    int ic[3], jc[3];
+                    float dc[3], ec[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    p[c] = fminf(fmaxf(p[c], 0.f), 1.f);
-                    float u = p[c] * fD;
-                    ic[c] = cell_index(u, D);
-                    dc[c] = u - static_cast<float>(ic[c]);
-                    float v = p[c] * fDs;
-                    jc[c] = cell_index(v, Dsc);
-                    ec[c] = v - static_cast<float>(jc[c]);
+                    for (int c = 0; c < 3; ++c) {
+                        p[c] = fminf(fmaxf(p[c], 0.f), 1.f);
+                        ic[c] = cell_of(p[c], fD1, fD2, dc[c]);
+                        jc[c] = cell_of(p[c], fS1, fS2, ec[c]);
+                    }
+                    float y0 = bias0, y1 = bias1, y2 = bias2;
+                    lut_pair(lcell + ic[0] * D3 + ic[1] * 3, dc[0], dc[1], y0, y1, y2);
+                    lut_pair(lcell + nc3 + ic[0] * D3 + ic[2] * 3, dc[0], dc[2], y0, y1, y2);
+                    lut_pair(lcell + 2 * nc3 + ic[1] * D3 + ic[2] * 3, dc[1], dc[2], y0, y1, y2);
+                    // xy slicing: row-interpolated vertices, lerp along x
+                    const float4 r0 = b.rxy[ixl[k]], r1 = b.rxy[ixl[k] + 1];
+                    const float dx = dxk[k];
+                    y0 += fmaf(r1.x - r0.x, dx, r0.x);
+                    y1 += fmaf(r1.y - r0.y, dx, r0.y);
+                    y2 += fmaf(r1.z - r0.z, dx, r0.z);
+                    float yy[3] = {y0, y1, y2};
+                    // xc + yc slicing share the intensity cell of channel c
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float4 q = b.pxc[c * xcs + ixl[k] * Dsc + jc[c]];
+                        const float2 qy = b.ryc[c * Dc1 + jc[c]];
+                        const float s0 = fmaf(q.z - q.x, dx, q.x) + qy.x;
+                        const float s1 = fmaf(q.w - q.y, dx, q.y) + qy.y;
+                        out[c][k] = yy[c] + fmaf(s1 - s0, ec[c], s0);
+                    }
                 }
-                float y0 = bias0, y1 = bias1, y2 = bias2;
-                lut_pair(lc0, ic[0] * Dm1 + ic[1], dc[0], dc[1], y0, y1, y2);
-                lut_pair(lc1, ic[0] * Dm1 + ic[2], dc[0], dc[2], y0, y1, y2);
-                lut_pair(lc2, ic[1] * Dm1 + ic[2], dc[1], dc[2], y0, y1, y2);
-                // xy slicing: row-interpolated vertices, lerp along x
-                const float4 r0 = rxy[ixl[k]], r1 = rxy[ixl[k] + 1];
-                const float dx = dxk[k];
-                y0 += fmaf(r1.x - r0.x, dx, r0.x);
-                y1 += fmaf(r1.y - r0.y, dx, r0.y);
-                y2 += fmaf(r1.z - r0.z, dx, r0.z);
-                float yy[3] = {y0, y1, y2};
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float2 *px = b.pxc + (c * g.nvx + ixl[k]) * Dc1 + jc[c];
-                    const float2 q0 = px[0], q1 = px[Dc1], qy = ryc[c * Dc1 + jc[c]];
-                    const float s0 = fmaf(q1.x - q0.x, dx, q0.x) + qy.x;
-                    const float s1 = fmaf(q1.y - q0.y, dx, q0.y) + qy.y;
-                    yy[c] += fmaf(s1 - s0, ec[c], s0);
-                    out[c][k] = yy[c];
-                }
+                for (int c = 0; c < 3; ++c)
+                    PixIO<T>::store(dst + c * plane + static_cast<size_t>(y) * d.W + xbase,
+                                    make_float4(out[c][0], out[c][1], out[c][2], out[c][3]), n, d.vec);
             }
+            __syncwarp();  // row tables are rewritten for the next row
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                PixIO<T>::store(dst + c * plane + static_cast<size_t>(y) * d.W + xbase,
-                                make_float4(out[c][0], out[c][1], out[c][2], out[c][3]), n, d.vec);
-        }
-        if (t + 1 < t_end) {
-#pragma unroll
-            for (int rr = 0; rr < kRowsPerWarp; ++rr)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) cur[rr][c] = nxt[rr][c];
+            for (int c = 0; c < 3; ++c) cur[c] = nxt[c];
         }
     }
 }

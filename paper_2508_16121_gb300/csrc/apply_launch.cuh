@@ -16,21 +16,30 @@ size_t param_stride(const svdlut_dims *d, int which);
 ImgDesc make_desc(const svdlut_dims *d, const svdlut_params *p, int b, int H, int W, svdlut_dtype dt,
                   const void *x, void *y);
 
-// Dynamic shared memory (bytes) needed for args a; sets a.lcell_floats and
-// a.scratch_floats.
+// Dynamic shared memory (bytes) for args a, given the per-block limit; sets
+// a.lcell_floats, a.stage_floats and a.scratch_floats.  The grid-slice
+// staging area and the all-tables-at-once prologue are used when they fit.
 template <int N>
-size_t apply_smem_bytes(LaunchArgs<N> &a)
+size_t apply_smem_bytes(LaunchArgs<N> &a, size_t limit)
 {
-    int Dmax = 2, pro = 0, til = 0;
+    int Dmax = 2, pro1 = 0, pro3 = 0, til = 0, stg = 0;
     for (int i = 0; i < a.n; ++i) {
         const ImgDesc &e = a.img[i];
         Dmax = std::max(Dmax, e.D);
-        pro = std::max(pro, prologue_floats(e.D, e.R));
+        pro1 = std::max(pro1, prologue_floats_n(e.D, e.R, 1));
+        pro3 = std::max(pro3, prologue_floats_n(e.D, e.R, 3));
         til = std::max(til, tile_floats(a.nvx_max, a.nvy_max, e.Dsc));
+        stg = std::max(stg, stage_floats(e.K, a.nvx_max, a.nvy_max, e.Dsc));
     }
+    stg = (stg + 3) & ~3;
     a.lcell_floats = lcell_floats(Dmax);
-    a.scratch_floats = std::max(pro, til);
-    return sizeof(float) * (static_cast<size_t>(a.lcell_floats) + kMiscFloats + a.scratch_floats);
+    auto bytes = [&](int stage, int scratch) {
+        return sizeof(float) * (static_cast<size_t>(a.lcell_floats) + kMiscFloats + stage + scratch);
+    };
+    const int base = std::max(til, pro1);
+    a.stage_floats = kStage && bytes(stg, base) <= limit ? stg : 0;
+    a.scratch_floats = bytes(a.stage_floats, std::max(base, pro3)) <= limit ? std::max(base, pro3) : base;
+    return bytes(a.stage_floats, a.scratch_floats);
 }
 
 template <typename T, int N>
@@ -39,7 +48,7 @@ svdlut_status launch_apply_t(LaunchArgs<N> &a, cudaStream_t s, int grid)
     DeviceInfo di;
     svdlut_status st = device_info(&di);
     if (st != SVDLUT_OK) return st;
-    const size_t smem = apply_smem_bytes(a);
+    const size_t smem = apply_smem_bytes(a, static_cast<size_t>(di.max_smem_optin));
     if (smem > static_cast<size_t>(di.max_smem_optin))
         return fail(SVDLUT_ERR_UNSUPPORTED,
                     "transform needs %zu bytes of shared memory per block (limit %d): grid vertices "
