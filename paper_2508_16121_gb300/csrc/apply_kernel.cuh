@@ -1,21 +1,22 @@
 // Fused 2D slicing + 2D LUT transform kernel (Eq. 8, Supp. Eq. 20) for sm_103a.
 //
-// One persistent CTA per SM walks a contiguous range of 128 x kTileH pixel
-// tiles; each warp owns kRowsPerWarp consecutive rows of a tile, a lane owns 4
-// consecutive pixels of a row (one 16-byte load/store per plane).
+// One persistent CTA per SM walks a contiguous range of pixel blocks; a block
+// is a 128-pixel-wide column strip of one image, BH rows tall (BH is planned
+// on the host so that the blocks cover the SMs evenly).  A lane owns 4
+// consecutive pixels of a row (one 16-byte load/store per plane); warp w owns
+// rows w, w + kWarps, ... of the block.
 //  - Prologue, once per image a CTA meets: the nine 2D LUTs are rebuilt from
 //    their SVD factors (Eq. 7) in shared memory, multiplied by their LUT
 //    weights (Eq. 4) and turned into per-cell bilinear coefficients
 //    (phi = a + b da + c db + d da db, Supp. Eq. 13) for the three output
 //    channels: 3 float4 per cell and pair.
-//  - Per tile: the raw grid slices of the tile's footprint are staged in
-//    shared memory with cp.async during the previous tile, then summed over
-//    the grids that feed each output channel (grid k feeds channel k mod 3,
-//    Supp. Eq. 20) with their weights (Eq. 19).  The xc plane is packed as
+//  - Per block: the grid slices of the block's footprint are summed over the
+//    grids that feed each output channel (grid k feeds channel k mod 3, Supp.
+//    Eq. 20) with their weights (Eq. 19); the xc slice is packed as
 //    (x, x+1) x (j, j+1) corners.
 //  - Per row: a warp interpolates the xy and yc slices along y for its row.
 //  - Per pixel: 9 LDS.128 for the three LUT pairs, 2 LDS.128 (xy), 3 LDS.128
-//    (xc) and 3 LDS.64 (yc).  Row data is loaded one row ahead, across tile
+//    (xc) and 3 LDS.64 (yc).  Row data is loaded one row ahead, across block
 //    boundaries.
 #pragma once
 
@@ -26,19 +27,11 @@ namespace svdlut {
 #ifndef SVDLUT_WARPS
 #define SVDLUT_WARPS 16
 #endif
-#ifndef SVDLUT_ROWS_PER_WARP
-#define SVDLUT_ROWS_PER_WARP 4
-#endif
-#ifndef SVDLUT_STAGE
-#define SVDLUT_STAGE 0
-#endif
 constexpr int kWarps = SVDLUT_WARPS;
 constexpr int kThreads = kWarps * 32;
-constexpr int kRowsPerWarp = SVDLUT_ROWS_PER_WARP;
 constexpr int kTileW = 128;  // 32 lanes x 4 pixels
-constexpr int kTileH = kWarps * kRowsPerWarp;
-constexpr bool kStage = SVDLUT_STAGE != 0;
-static_assert(kTileW + kTileH <= kThreads, "row/column tables need one thread each");
+constexpr int kMinBlockH = 16;
+static_assert(kTileW <= kThreads, "column tables need one thread each");
 
 struct ImgDesc {
     const void *x;
@@ -46,19 +39,20 @@ struct ImgDesc {
     const float *U, *S, *V, *lw, *gxy, *gxc, *gyc, *gw;
     int H, W;
     int D, R, K, Dsx, Dsy, Dsc;
-    int tiles_x, tile_begin;
-    float rW1, rH1;  // 1/(W-1), 1/(H-1); 0 when W or H is 1
+    int strips;       // column strips of kTileW pixels
+    int BH;           // block height (rows)
+    int block_begin;  // first global block index of this image
+    float rW1, rH1;   // 1/(W-1), 1/(H-1); 0 when W or H is 1
     int vec;         // 16-byte (f32) / 4-byte (u8) vector I/O allowed
 };
 
 template <int N>
 struct LaunchArgs {
-    int n;            // images in img[]
-    int total_tiles;  // sum of tiles over images
-    int nvx_max, nvy_max;
+    int n;             // images in img[]
+    int total_blocks;  // sum of blocks over images
+    int nvx_max, nvy_max, bh_max;
     int lcell_floats;    // floats reserved for the cell table
-    int stage_floats;    // floats of the grid-slice staging area (0: read grids from global)
-    int scratch_floats;  // floats of the tile buffers / prologue temporaries
+    int scratch_floats;  // floats of the block buffers / prologue temporaries
     ImgDesc img[N];
 };
 
@@ -238,24 +232,29 @@ __device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, f
             }
             __syncthreads();
         }
-        for (int i = warp; i < D; i += kWarps) {
-            for (int j = lane; j < D; j += 32) {
-                float acc[3];
+        for (int e = tid; e < D * D; e += kThreads) {
+            const int i = e / D, j = e - i * D;
+            float acc[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const int slot = pairs_at_once == 3 ? c * 3 + p : c;
-                    const float *u = sU + slot * DRp + i * Rp;
-                    const float *v = sV + slot * DRp + j * Rp;
-                    float a = 0.f;
+            for (int c = 0; c < 3; ++c) {
+                const int slot = pairs_at_once == 3 ? c * 3 + p : c;
+                const float *u = sU + slot * DRp + i * Rp;
+                const float *v = sV + slot * DRp + j * Rp;
+                float a = 0.f;
+                if (R == 8) {
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) a = fmaf(u[r], v[r], a);
+                } else {
                     for (int r = 0; r < R; ++r) a = fmaf(u[r], v[r], a);
-                    acc[c] = a;
                 }
-                vt[i * D + j] = make_float4(acc[0], acc[1], acc[2], 0.f);
+                acc[c] = a;
             }
+            vt[e] = make_float4(acc[0], acc[1], acc[2], 0.f);
         }
         __syncthreads();
-        for (int i = warp; i < Dm1; i += kWarps) {
-            for (int j = lane; j < Dm1; j += 32) {
+        for (int e = tid; e < Dm1 * Dm1; e += kThreads) {
+            const int i = e / Dm1, j = e - i * Dm1;
+            {
                 const float4 v00 = vt[i * D + j], v10 = vt[(i + 1) * D + j];
                 const float4 v01 = vt[i * D + j + 1], v11 = vt[(i + 1) * D + j + 1];
                 const float bx = v10.x - v00.x, by = v10.y - v00.y, bz = v10.z - v00.z;
@@ -272,17 +271,18 @@ __device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, f
     }
 }
 
-struct TileGeom {
-    int x0, y0, ixlo, iylo, nvx, nvy;
+struct BlockGeom {
+    int x0, y0, rows, ixlo, iylo, nvx, nvy;
 };
 
-__device__ __forceinline__ TileGeom tile_geom(const ImgDesc &d, int lt, int nvx_max, int nvy_max)
+__device__ __forceinline__ BlockGeom block_geom(const ImgDesc &d, int lb, int nvx_max, int nvy_max)
 {
-    TileGeom g;
-    int ty = lt / d.tiles_x, tx = lt - ty * d.tiles_x;
-    g.x0 = tx * kTileW;
-    g.y0 = ty * kTileH;
-    int x1 = min(g.x0 + kTileW - 1, d.W - 1), y1 = min(g.y0 + kTileH - 1, d.H - 1);
+    BlockGeom g;
+    const int band = lb / d.strips, strip = lb - band * d.strips;
+    g.x0 = strip * kTileW;
+    g.y0 = band * d.BH;
+    g.rows = min(d.BH, d.H - g.y0);
+    const int x1 = min(g.x0 + kTileW - 1, d.W - 1), y1 = g.y0 + g.rows - 1;
     int ixhi, iyhi;
     float unused;
     spatial_cell(g.x0, d.W, d.Dsx, d.rW1, g.ixlo, unused);
@@ -296,17 +296,18 @@ __device__ __forceinline__ TileGeom tile_geom(const ImgDesc &d, int lt, int nvx_
     return g;
 }
 
-// Tile buffers (floats, in this order):
+// Block buffers (floats, in this order):
 //   fxy [3][nvy][nvx], fxc [3][nvx][Dsc], fyc [3][nvy][Dsc]   folded grid slices
-//   rowi [kTileH] int, rowd [kTileH], coli [kTileW] int, cold [kTileW]
+//   coli [kTileW] int, cold [kTileW]                           column cells
+//   rowi [bh] int, rowd [bh]                                    row cells
 //   pxc [3][nvx-1][Dsc] float4   xc corners (x, x+1) x (j, j+1); row stride Dsc
 //                                (one padding entry) to spread banks
 //   per warp: rxy [nvx] float4 (xy interpolated along y for the warp's row),
 //             ryc [3][Dsc-1] float2 (yc interpolated along y, (j, j+1))
-struct TileBufs {
+struct BlockBufs {
     float *fxy, *fxc, *fyc;
-    int *rowi, *coli;
-    float *rowd, *cold;
+    int *coli, *rowi;
+    float *cold, *rowd;
     float4 *pxc, *rxy;
     float2 *ryc;
 };
@@ -314,114 +315,69 @@ struct TileBufs {
 // rounded to 4 floats so every warp's float4 table stays 16-byte aligned
 __host__ __device__ inline int warp_row_floats(int nvx, int Dsc) { return (nvx * 4 + 3 * (Dsc - 1) * 2 + 3) & ~3; }
 
-__host__ __device__ inline int tile_floats(int nvx, int nvy, int Dsc)
+__host__ __device__ inline int fold_floats(int nvx, int nvy, int Dsc)
 {
-    int a = (3 * nvy * nvx + 3 * nvx * Dsc + 3 * nvy * Dsc + 3) & ~3;
-    int tabs = 2 * kTileH + 2 * kTileW;
-    int pxc = 3 * (nvx - 1) * Dsc * 4;
-    int rows = kWarps * warp_row_floats(nvx, Dsc);
-    return a + tabs + pxc + rows;
+    return (3 * nvy * nvx + 3 * nvx * Dsc + 3 * nvy * Dsc + 3) & ~3;
 }
 
-__device__ __forceinline__ TileBufs tile_bufs(float *scratch, int nvx, int nvy, int Dsc)
+__host__ __device__ inline int block_floats(int nvx, int nvy, int Dsc, int bh)
 {
-    TileBufs b;
+    return fold_floats(nvx, nvy, Dsc) + 2 * kTileW + ((2 * bh + 3) & ~3) + 3 * (nvx - 1) * Dsc * 4 +
+           kWarps * warp_row_floats(nvx, Dsc);
+}
+
+__device__ __forceinline__ BlockBufs block_bufs(float *scratch, int nvx, int nvy, int Dsc, int bh_max)
+{
+    BlockBufs b;
     const int warp = threadIdx.x >> 5;
     b.fxy = scratch;
     b.fxc = b.fxy + 3 * nvy * nvx;
     b.fyc = b.fxc + 3 * nvx * Dsc;
-    float *t = scratch + ((3 * nvy * nvx + 3 * nvx * Dsc + 3 * nvy * Dsc + 3) & ~3);
-    b.rowi = reinterpret_cast<int *>(t);
-    b.rowd = t + kTileH;
-    b.coli = reinterpret_cast<int *>(t + 2 * kTileH);
-    b.cold = t + 2 * kTileH + kTileW;
-    b.pxc = reinterpret_cast<float4 *>(t + 2 * kTileH + 2 * kTileW);
+    float *t = scratch + fold_floats(nvx, nvy, Dsc);
+    b.coli = reinterpret_cast<int *>(t);
+    b.cold = t + kTileW;
+    b.rowi = reinterpret_cast<int *>(t + 2 * kTileW);
+    b.rowd = t + 2 * kTileW + bh_max;
+    b.pxc = reinterpret_cast<float4 *>(t + 2 * kTileW + ((2 * bh_max + 3) & ~3));
     float *w = reinterpret_cast<float *>(b.pxc + 3 * (nvx - 1) * Dsc) + warp * warp_row_floats(nvx, Dsc);
     b.rxy = reinterpret_cast<float4 *>(w);
     b.ryc = reinterpret_cast<float2 *>(w + nvx * 4);
     return b;
 }
 
-// ---- asynchronous staging of a tile's raw grid slices (cp.async, 4 bytes) ----
-__device__ __forceinline__ void cp_async4(float *dst, const float *src)
-{
-    const unsigned int sa = static_cast<unsigned int>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// Raw slices of tile g: xy [K][nvy][nvx], xc [K][nvx][Dsc], yc [K][nvy][Dsc].
-__host__ __device__ inline int stage_floats(int K, int nvx, int nvy, int Dsc)
-{
-    return K * (nvy * nvx + nvx * Dsc + nvy * Dsc);
-}
-
-__device__ inline void issue_stage(const ImgDesc &d, const TileGeom &g, float *stage)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int K = d.K, nvx = g.nvx, nvy = g.nvy, Dsc = d.Dsc;
-    float *sxy = stage, *sxc = sxy + K * nvy * nvx, *syc = sxc + K * nvx * Dsc;
-    for (int r = warp; r < K * nvy; r += kWarps) {  // r = k * nvy + iyl
-        const int k = r / nvy, iyl = r - k * nvy;
-        const float *src = d.gxy + (static_cast<size_t>(k) * d.Dsy + g.iylo + iyl) * d.Dsx + g.ixlo;
-        for (int ixl = lane; ixl < nvx; ixl += 32) cp_async4(sxy + r * nvx + ixl, src + ixl);
-    }
-    for (int r = warp; r < K * nvx; r += kWarps) {  // r = k * nvx + ixl
-        const int k = r / nvx, ixl = r - k * nvx;
-        const float *src = d.gxc + (static_cast<size_t>(k) * d.Dsx + g.ixlo + ixl) * Dsc;
-        for (int j = lane; j < Dsc; j += 32) cp_async4(sxc + r * Dsc + j, src + j);
-    }
-    for (int r = warp; r < K * nvy; r += kWarps) {  // r = k * nvy + iyl
-        const int k = r / nvy, iyl = r - k * nvy;
-        const float *src = d.gyc + (static_cast<size_t>(k) * d.Dsy + g.iylo + iyl) * Dsc;
-        for (int j = lane; j < Dsc; j += 32) cp_async4(syc + r * Dsc + j, src + j);
-    }
-    cp_async_commit();
-}
-
-// Phase A: grid slices of the tile footprint folded per output channel
-// (sum over grids k = c mod 3 with their weights), read from the staging area
-// when present, else from global memory; row and column cell tables.
-__device__ inline void tile_phase_a(const ImgDesc &d, const TileGeom &g, const TileBufs &b,
-                                    const float *misc, const float *stage)
+// Block setup, phase A: grid slices of the block footprint folded per output
+// channel (sum over grids k = c mod 3 with their weights); column and row
+// cell tables.
+__device__ inline void block_phase_a(const ImgDesc &d, const BlockGeom &g, const BlockBufs &b, const float *misc)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nvx = g.nvx, nvy = g.nvy, Dsc = d.Dsc, K = d.K;
-    const float *sxy = stage, *sxc = stage + K * nvy * nvx, *syc = sxc + K * nvx * Dsc;
+    const size_t kxy = static_cast<size_t>(d.Dsy) * d.Dsx, kxc = static_cast<size_t>(d.Dsx) * Dsc,
+                 kyc = static_cast<size_t>(d.Dsy) * Dsc;
     for (int r = warp; r < 3 * nvy; r += kWarps) {
         const int c = r / nvy, iyl = r - c * nvy;
+        const float *src = d.gxy + static_cast<size_t>(g.iylo + iyl) * d.Dsx + g.ixlo;
         for (int ixl = lane; ixl < nvx; ixl += 32) {
             float s = 0.f;
-            for (int k = c; k < K; k += 3) {
-                const float v = stage ? sxy[(k * nvy + iyl) * nvx + ixl]
-                                      : __ldg(d.gxy + (static_cast<size_t>(k) * d.Dsy + g.iylo + iyl) * d.Dsx + g.ixlo + ixl);
-                s = fmaf(misc[k * 4 + 0], v, s);
-            }
+            for (int k = c; k < K; k += 3) s = fmaf(misc[k * 4 + 0], __ldg(src + k * kxy + ixl), s);
             b.fxy[r * nvx + ixl] = s;
         }
     }
     for (int r = warp; r < 3 * nvx; r += kWarps) {
         const int c = r / nvx, ixl = r - c * nvx;
+        const float *src = d.gxc + static_cast<size_t>(g.ixlo + ixl) * Dsc;
         for (int j = lane; j < Dsc; j += 32) {
             float s = 0.f;
-            for (int k = c; k < K; k += 3) {
-                const float v = stage ? sxc[(k * nvx + ixl) * Dsc + j]
-                                      : __ldg(d.gxc + (static_cast<size_t>(k) * d.Dsx + g.ixlo + ixl) * Dsc + j);
-                s = fmaf(misc[k * 4 + 1], v, s);
-            }
+            for (int k = c; k < K; k += 3) s = fmaf(misc[k * 4 + 1], __ldg(src + k * kxc + j), s);
             b.fxc[r * Dsc + j] = s;
         }
     }
     for (int r = warp; r < 3 * nvy; r += kWarps) {
         const int c = r / nvy, iyl = r - c * nvy;
+        const float *src = d.gyc + static_cast<size_t>(g.iylo + iyl) * Dsc;
         for (int j = lane; j < Dsc; j += 32) {
             float s = 0.f;
-            for (int k = c; k < K; k += 3) {
-                const float v = stage ? syc[(k * nvy + iyl) * Dsc + j]
-                                      : __ldg(d.gyc + (static_cast<size_t>(k) * d.Dsy + g.iylo + iyl) * Dsc + j);
-                s = fmaf(misc[k * 4 + 2], v, s);
-            }
+            for (int k = c; k < K; k += 3) s = fmaf(misc[k * 4 + 2], __ldg(src + k * kyc + j), s);
             b.fyc[r * Dsc + j] = s;
         }
     }
@@ -431,18 +387,18 @@ __device__ inline void tile_phase_a(const ImgDesc &d, const TileGeom &g, const T
         spatial_cell(min(g.x0 + tid, d.W - 1), d.W, d.Dsx, d.rW1, ix, dx);
         b.coli[tid] = max(0, min(ix - g.ixlo, nvx - 2));
         b.cold[tid] = dx;
-    } else if (tid < kTileW + kTileH) {
-        const int row = tid - kTileW;
+    }
+    for (int row = tid; row < g.rows; row += kThreads) {
         int iy;
         float dy;
-        spatial_cell(min(g.y0 + row, d.H - 1), d.H, d.Dsy, d.rH1, iy, dy);
+        spatial_cell(g.y0 + row, d.H, d.Dsy, d.rH1, iy, dy);
         b.rowi[row] = max(0, min(iy - g.iylo, nvy - 2));
         b.rowd[row] = dy;
     }
 }
 
-// Phase B: corner packs of the folded xc slice.
-__device__ inline void tile_phase_b(const ImgDesc &d, const TileGeom &g, const TileBufs &b)
+// Block setup, phase B: corner packs of the folded xc slice.
+__device__ inline void block_phase_b(const ImgDesc &d, const BlockGeom &g, const BlockBufs &b)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nvx = g.nvx, Dsc = d.Dsc, Dc1 = Dsc - 1;
@@ -454,8 +410,8 @@ __device__ inline void tile_phase_b(const ImgDesc &d, const TileGeom &g, const T
     }
 }
 
-// Per-warp tables of one tile row: xy and yc slices interpolated along y.
-__device__ __forceinline__ void warp_row_tables(const TileGeom &g, const TileBufs &b, int Dsc, int row)
+// Per-warp tables of one block row: xy and yc slices interpolated along y.
+__device__ __forceinline__ void warp_row_tables(const BlockGeom &g, const BlockBufs &b, int Dsc, int row)
 {
     const int lane = threadIdx.x & 31;
     const int nvx = g.nvx, nvy = g.nvy, Dc1 = Dsc - 1;
@@ -471,12 +427,11 @@ __device__ __forceinline__ void warp_row_tables(const TileGeom &g, const TileBuf
         }
         b.rxy[ixl] = make_float4(v[0], v[1], v[2], 0.f);
     }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float *r0 = b.fyc + (c * nvy + iyl) * Dsc;
+    for (int e = lane; e < 3 * Dc1; e += 32) {
+        const int c = e >= Dc1 ? (e >= 2 * Dc1 ? 2 : 1) : 0, j = e - c * Dc1;
+        const float *r0 = b.fyc + (c * nvy + iyl) * Dsc + j;
         const float *r1 = r0 + Dsc;
-        for (int j = lane; j < Dc1; j += 32)
-            b.ryc[c * Dc1 + j] = make_float2(fmaf(r1[j] - r0[j], dy, r0[j]), fmaf(r1[j + 1] - r0[j + 1], dy, r0[j + 1]));
+        b.ryc[e] = make_float2(fmaf(r1[0] - r0[0], dy, r0[0]), fmaf(r1[1] - r0[1], dy, r0[1]));
     }
 }
 
@@ -499,60 +454,53 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
     extern __shared__ __align__(16) float smem[];
     float4 *lcell = reinterpret_cast<float4 *>(smem);
     float *misc = smem + a.lcell_floats;
-    float *stage = a.stage_floats > 0 ? misc + kMiscFloats : nullptr;
-    float *scratch = misc + kMiscFloats + a.stage_floats;
+    float *scratch = misc + kMiscFloats;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int G = gridDim.x, gi = blockIdx.x;
-    const int t_begin = static_cast<int>((static_cast<long long>(a.total_tiles) * gi) / G);
-    const int t_end = static_cast<int>((static_cast<long long>(a.total_tiles) * (gi + 1)) / G);
-    if (t_begin >= t_end) return;
+    const int b_begin = static_cast<int>((static_cast<long long>(a.total_blocks) * gi) / G);
+    const int b_end = static_cast<int>((static_cast<long long>(a.total_blocks) * (gi + 1)) / G);
+    if (b_begin >= b_end) return;
 
     using Raw = typename PixIO<T>::Raw;
 
-    auto find_image = [&](int t) {
+    auto find_image = [&](int blk) {
         int im = 0;
-        while (im + 1 < a.n && a.img[im + 1].tile_begin <= t) ++im;
+        while (im + 1 < a.n && a.img[im + 1].block_begin <= blk) ++im;
         return im;
     };
-    // loads this lane's 4 pixels of row rr (of this warp) of tile t
-    auto load_row = [&](int t, int rr, Raw (&dst)[3]) {
-        const ImgDesc &d = a.img[find_image(t)];
-        const int lt = t - d.tile_begin;
-        const int ty = lt / d.tiles_x, tx = lt - ty * d.tiles_x;
-        const int x = tx * kTileW + lane * 4;
+    // loads this lane's 4 pixels of row `row` (block-relative) of block blk
+    auto load_row = [&](int blk, int row, Raw (&dst)[3]) {
+        const ImgDesc &d = a.img[find_image(blk)];
+        const int lb = blk - d.block_begin;
+        const int band = lb / d.strips, strip = lb - band * d.strips;
+        const int x = strip * kTileW + lane * 4;
         const int n = min(4, d.W - x);
-        const int y = ty * kTileH + warp * kRowsPerWarp + rr;
+        const int y = band * d.BH + row;
         const size_t plane = static_cast<size_t>(d.H) * d.W;
         const T *src = static_cast<const T *>(d.x) + static_cast<size_t>(y) * d.W + x;
+        const bool ok = row < d.BH && y < d.H && n > 0;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) dst[c] = (y < d.H && n > 0) ? PixIO<T>::load(src + c * plane, n, d.vec) : Raw();
-    };
-    auto stage_tile = [&](int t) {
-        const ImgDesc &d = a.img[find_image(t)];
-        if (d.K > 0) issue_stage(d, tile_geom(d, t - d.tile_begin, a.nvx_max, a.nvy_max), stage);
+        for (int c = 0; c < 3; ++c) dst[c] = ok ? PixIO<T>::load(src + c * plane, n, d.vec) : Raw();
     };
 
     Raw cur[3], nxt[3];
     int cur_im = -1;
-    load_row(t_begin, 0, cur);
-    if (stage) stage_tile(t_begin);
-    for (int t = t_begin; t < t_end; ++t) {
-        const int im = find_image(t);
+    load_row(b_begin, warp, cur);
+    for (int blk = b_begin; blk < b_end; ++blk) {
+        const int im = find_image(blk);
         const ImgDesc &d = a.img[im];
         if (im != cur_im) {
             __syncthreads();
             build_luts(d, lcell, scratch, misc, a.scratch_floats);
             cur_im = im;
         }
-        const TileGeom g = tile_geom(d, t - d.tile_begin, a.nvx_max, a.nvy_max);
-        const TileBufs b = tile_bufs(scratch, g.nvx, g.nvy, d.Dsc);
-        if (stage) cp_async_wait_all();
-        __syncthreads();  // staged slices visible; previous tile's rows done
-        tile_phase_a(d, g, b, misc, stage);
+        const BlockGeom g = block_geom(d, blk - d.block_begin, a.nvx_max, a.nvy_max);
+        const BlockBufs b = block_bufs(scratch, g.nvx, g.nvy, d.Dsc, a.bh_max);
+        __syncthreads();  // previous block's rows done with the buffers
+        block_phase_a(d, g, b, misc);
         __syncthreads();
-        if (stage && t + 1 < t_end) stage_tile(t + 1);  // lands during this tile's rows
-        tile_phase_b(d, g, b);
+        block_phase_b(d, g, b);
         __syncthreads();
 
         // ---- rows of this warp ----
@@ -572,15 +520,14 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         const size_t plane = static_cast<size_t>(d.H) * d.W;
         T *dst = static_cast<T *>(d.y);
 #pragma unroll 1
-        for (int rr = 0; rr < kRowsPerWarp; ++rr) {
-            // next row of this warp, possibly in the next tile
-            if (rr + 1 < kRowsPerWarp) load_row(t, rr + 1, nxt);
-            else if (t + 1 < t_end) load_row(t + 1, 0, nxt);
-            const int row = warp * kRowsPerWarp + rr;
+        for (int row = warp; row < g.rows; row += kWarps) {
+            // next row of this warp, possibly in the next block
+            if (row + kWarps < g.rows) load_row(blk, row + kWarps, nxt);
+            else if (blk + 1 < b_end) load_row(blk + 1, warp, nxt);
             const int y = g.y0 + row;
             warp_row_tables(g, b, Dsc, row);
             __syncwarp();
-            if (y < d.H && n > 0) {
+            if (n > 0) {
                 const float4 pr = PixIO<T>::to_float(cur[0]);
                 const float4 pg = PixIO<T>::to_float(cur[1]);
                 const float4 pb = PixIO<T>::to_float(cur[2]);
@@ -626,6 +573,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
 #pragma unroll
             for (int c = 0; c < 3; ++c) cur[c] = nxt[c];
         }
+        if (warp >= g.rows && blk + 1 < b_end) load_row(blk + 1, warp, cur);  // no row here
     }
 }
 

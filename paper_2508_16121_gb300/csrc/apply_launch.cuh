@@ -16,66 +16,108 @@ size_t param_stride(const svdlut_dims *d, int which);
 ImgDesc make_desc(const svdlut_dims *d, const svdlut_params *p, int b, int H, int W, svdlut_dtype dt,
                   const void *x, void *y);
 
-// Dynamic shared memory (bytes) for args a, given the per-block limit; sets
-// a.lcell_floats, a.stage_floats and a.scratch_floats.  The grid-slice
-// staging area and the all-tables-at-once prologue are used when they fit.
+// Shared-memory bytes of args a for block heights up to bh_max; the
+// all-nine-tables prologue is enabled when it fits.  Sets lcell/scratch sizes.
 template <int N>
 size_t apply_smem_bytes(LaunchArgs<N> &a, size_t limit)
 {
-    int Dmax = 2, pro1 = 0, pro3 = 0, til = 0, stg = 0;
+    int Dmax = 2, pro1 = 0, pro3 = 0, blk = 0;
     for (int i = 0; i < a.n; ++i) {
         const ImgDesc &e = a.img[i];
         Dmax = std::max(Dmax, e.D);
         pro1 = std::max(pro1, prologue_floats_n(e.D, e.R, 1));
         pro3 = std::max(pro3, prologue_floats_n(e.D, e.R, 3));
-        til = std::max(til, tile_floats(a.nvx_max, a.nvy_max, e.Dsc));
-        stg = std::max(stg, stage_floats(e.K, a.nvx_max, a.nvy_max, e.Dsc));
+        blk = std::max(blk, block_floats(a.nvx_max, a.nvy_max, e.Dsc, a.bh_max));
     }
-    stg = (stg + 3) & ~3;
     a.lcell_floats = lcell_floats(Dmax);
-    auto bytes = [&](int stage, int scratch) {
-        return sizeof(float) * (static_cast<size_t>(a.lcell_floats) + kMiscFloats + stage + scratch);
+    auto bytes = [&](int scratch) {
+        return sizeof(float) * (static_cast<size_t>(a.lcell_floats) + kMiscFloats + scratch);
     };
-    const int base = std::max(til, pro1);
-    a.stage_floats = kStage && bytes(stg, base) <= limit ? stg : 0;
-    a.scratch_floats = bytes(a.stage_floats, std::max(base, pro3)) <= limit ? std::max(base, pro3) : base;
-    return bytes(a.stage_floats, a.scratch_floats);
+    const int base = std::max(blk, pro1);
+    a.scratch_floats = bytes(std::max(base, pro3)) <= limit ? std::max(base, pro3) : base;
+    return bytes(a.scratch_floats);
+}
+
+// Plans the block split of B same-size images: each image is cut into
+// `strips` column strips of kTileW pixels and `bands` row bands; bands is
+// chosen to maximise the share of SM time used (blocks / (waves x SMs)),
+// preferring fewer waves, while the block buffers fit in shared memory.  Fills strips/BH/block_begin, total_blocks, nvx_max, nvy_max,
+// bh_max and the shared-memory size.
+template <int N>
+svdlut_status plan_uniform(LaunchArgs<N> &a, int sm_count, size_t smem_limit, size_t *smem_out)
+{
+    const ImgDesc &e0 = a.img[0];
+    const int H = e0.H, W = e0.W, strips = (W + kTileW - 1) / kTileW;
+    const int max_bands = std::max(1, (H + kMinBlockH - 1) / kMinBlockH);
+    int best = -1;
+    double best_score = -1e30;
+    const int nvx = span_bound(kTileW, W, e0.Dsx);
+    const int fixed = lcell_floats(e0.D) + kMiscFloats;
+    const int pro = prologue_floats_n(e0.D, e0.R, 1);  // required; all-pairs-at-once is optional
+    for (int bands = 1; bands <= max_bands; ++bands) {
+        const int BH = (H + bands - 1) / bands;
+        const int need = fixed + std::max(pro, block_floats(nvx, span_bound(BH, H, e0.Dsy), e0.Dsc, BH));
+        if (sizeof(float) * static_cast<size_t>(need) > smem_limit) continue;
+        const long long T = static_cast<long long>(a.n) * strips * bands;
+        const double waves = std::ceil(static_cast<double>(T) / sm_count - 1e-9);
+        const double eff = static_cast<double>(T) / (waves * sm_count);  // share of SM time used
+        const double score = eff - 0.002 * waves;                        // prefer fewer, larger blocks
+        if (score > best_score + 1e-12) {
+            best_score = score;
+            best = bands;
+        }
+        if (bands >= 4 * sm_count) break;
+    }
+    if (best < 0)
+        return fail(SVDLUT_ERR_UNSUPPORTED,
+                    "grid slices of a %dx%d block do not fit in shared memory (%zu bytes): grid vertices too "
+                    "dense or D_t/rank too large", kTileW, kMinBlockH, smem_limit);
+    const int BH = (H + best - 1) / best;
+    const int bands = (H + BH - 1) / BH;
+    for (int i = 0; i < a.n; ++i) {
+        a.img[i].strips = strips;
+        a.img[i].BH = BH;
+        a.img[i].block_begin = i * strips * bands;
+    }
+    a.total_blocks = a.n * strips * bands;
+    a.nvx_max = span_bound(kTileW, W, e0.Dsx);
+    a.nvy_max = span_bound(BH, H, e0.Dsy);
+    a.bh_max = BH;
+    *smem_out = apply_smem_bytes(a, smem_limit);
+    return SVDLUT_OK;
 }
 
 template <typename T, int N>
-svdlut_status launch_apply_t(LaunchArgs<N> &a, cudaStream_t s, int grid)
+svdlut_status launch_apply_t(LaunchArgs<N> &a, size_t smem, int sm_count, int max_smem, int device,
+                             cudaStream_t s, int grid)
 {
-    DeviceInfo di;
-    svdlut_status st = device_info(&di);
-    if (st != SVDLUT_OK) return st;
-    const size_t smem = apply_smem_bytes(a, static_cast<size_t>(di.max_smem_optin));
-    if (smem > static_cast<size_t>(di.max_smem_optin))
-        return fail(SVDLUT_ERR_UNSUPPORTED,
-                    "transform needs %zu bytes of shared memory per block (limit %d): grid vertices "
-                    "too dense for a %dx%d tile or D_t/rank too large",
-                    smem, di.max_smem_optin, kTileW, kTileH);
     static std::mutex mu;
     static bool attr_set[64] = {};
     {
         std::lock_guard<std::mutex> g(mu);
-        if (!attr_set[di.device]) {
-            SVDLUT_CUDA_TRY(cudaFuncSetAttribute(apply_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 di.max_smem_optin));
-            attr_set[di.device] = true;
+        if (!attr_set[device]) {
+            SVDLUT_CUDA_TRY(
+                cudaFuncSetAttribute(apply_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+            attr_set[device] = true;
         }
     }
-    if (grid <= 0) grid = std::min(a.total_tiles, di.sm_count);
-    grid = std::max(1, std::min(grid, a.total_tiles));
+    if (grid <= 0) grid = std::min(a.total_blocks, sm_count);
+    grid = std::max(1, std::min(grid, a.total_blocks));
     apply_kernel<T, N><<<grid, kThreads, smem, s>>>(a);
     SVDLUT_CUDA_TRY(cudaGetLastError());
     return SVDLUT_OK;
 }
 
+// Launches apply_kernel for args whose blocks are already planned.
 template <int N>
-svdlut_status launch_apply(LaunchArgs<N> &a, svdlut_dtype dt, cudaStream_t s, int grid)
+svdlut_status launch_apply(LaunchArgs<N> &a, size_t smem, svdlut_dtype dt, cudaStream_t s, int grid)
 {
-    if (a.total_tiles <= 0) return SVDLUT_OK;
-    return dt == SVDLUT_F32 ? launch_apply_t<float, N>(a, s, grid) : launch_apply_t<uint8_t, N>(a, s, grid);
+    if (a.total_blocks <= 0) return SVDLUT_OK;
+    DeviceInfo di;
+    svdlut_status st = device_info(&di);
+    if (st != SVDLUT_OK) return st;
+    return dt == SVDLUT_F32 ? launch_apply_t<float, N>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid)
+                            : launch_apply_t<uint8_t, N>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid);
 }
 
 }  // namespace svdlut

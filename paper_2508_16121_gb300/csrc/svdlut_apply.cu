@@ -59,7 +59,6 @@ ImgDesc make_desc(const svdlut_dims *d, const svdlut_params *p, int b, int H, in
     e.Dsx = d->Dsx;
     e.Dsy = d->Dsy;
     e.Dsc = d->Dsc;
-    e.tiles_x = (W + kTileW - 1) / kTileW;
     e.rW1 = W > 1 ? 1.0f / static_cast<float>(W - 1) : 0.f;
     e.rH1 = H > 1 ? 1.0f / static_cast<float>(H - 1) : 0.f;
     const size_t va = dt == SVDLUT_F32 ? 16 : 4;
@@ -89,18 +88,16 @@ extern "C" svdlut_status svdlut_apply(const svdlut_dims *dims, const svdlut_para
     const char *xs = static_cast<const char *>(x), *ys = static_cast<const char *>(y);
     if (xs < ys + bytes && ys < xs + bytes) return fail(SVDLUT_ERR_INVALID_ARG, "x and y overlap");
 
-    const int tiles_img = ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH);
+    DeviceInfo di;
+    if ((st = device_info(&di)) != SVDLUT_OK) return st;
     for (int b0 = 0; b0 < B; b0 += kPlainChunk) {
         LaunchArgs<kPlainChunk> a{};
         a.n = std::min(kPlainChunk, B - b0);
-        for (int i = 0; i < a.n; ++i) {
-            a.img[i] = make_desc(dims, params, b0 + i, H, W, dtype, x, y);
-            a.img[i].tile_begin = i * tiles_img;
-        }
-        a.total_tiles = a.n * tiles_img;
-        a.nvx_max = span_bound(kTileW, W, dims->Dsx);
-        a.nvy_max = span_bound(kTileH, H, dims->Dsy);
-        if ((st = launch_apply(a, dtype, reinterpret_cast<cudaStream_t>(stream), 0)) != SVDLUT_OK) return st;
+        for (int i = 0; i < a.n; ++i) a.img[i] = make_desc(dims, params, b0 + i, H, W, dtype, x, y);
+        size_t smem = 0;
+        if ((st = plan_uniform(a, di.sm_count, static_cast<size_t>(di.max_smem_optin), &smem)) != SVDLUT_OK)
+            return st;
+        if ((st = launch_apply(a, smem, dtype, reinterpret_cast<cudaStream_t>(stream), 0)) != SVDLUT_OK) return st;
     }
     return SVDLUT_OK;
 }
