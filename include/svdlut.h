@@ -94,6 +94,41 @@ svdlut_status svdlut_apply(const svdlut_dims *dims, const svdlut_params *params,
                            int W, svdlut_dtype dtype, const void *x, void *y,
                            svdlut_stream_t stream);
 
+/*
+ * Gradient outputs of svdlut_backward: device FP32 arrays with the layouts of
+ * the matching svdlut_params fields (leading batch axis B).  Any pointer may
+ * be NULL (that gradient is not computed).  Wanted outputs are overwritten.
+ */
+typedef struct {
+    float *dU, *dS, *dV, *dlut_w, *dg_xy, *dg_xc, *dg_yc, *dgrid_w;
+} svdlut_grads;
+
+/*
+ * svdlut_backward -- adjoint of svdlut_apply for FP32 images.
+ * The paper trains end to end through the fused transform (Sec. 4.2) without
+ * printing its derivative; this is the exact derivative of the map above:
+ *   G^c_p = sum_px dy_c * (bilinear weights of (x_a, x_b))   per LUT vertex
+ *   dT^c_p = w^c_p G^c_p;  dU = dT V diag(S),  dV = dT^T U diag(S),
+ *   dS_r = sum_ij dT_ij U_ir V_jr;  dw^c_p = <G^c_p, T^c_p>;  db^c = sum dy_c
+ *   grids likewise (dg^k = w^k * scatter of dy_{k mod 3}, dw^k = <scatter, g^k>);
+ *   dx_a = [0 <= x_a <= 1] * (sum of dy-weighted slopes of every bilinear
+ *          term that reads x_a).
+ * x, dy: [B][3][H][W] FP32 device (x is the forward input).  dx: same shape,
+ * may be NULL.  Parameter gradients are deterministic: no atomics, every sum
+ * is taken in a fixed order, so repeated calls give identical bits.
+ * Workspace: device memory of at least svdlut_backward_workspace_size(...)
+ * bytes, 256-byte aligned, owned by the caller; contents on entry are
+ * ignored.  Returns SVDLUT_ERR_WORKSPACE if ws is NULL or too small while
+ * a parameter gradient is requested (dx alone needs no workspace).
+ */
+svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_params *params, int B, int H,
+                              int W, const float *x, const float *dy, float *dx,
+                              const svdlut_grads *grads, void *ws, size_t ws_bytes,
+                              svdlut_stream_t stream);
+
+/* Bytes of workspace svdlut_backward needs for these sizes (0 on bad args). */
+size_t svdlut_backward_workspace_size(const svdlut_dims *dims, int B, int H, int W);
+
 /* Message of the last error raised on this thread ("" if none). */
 const char *svdlut_last_error(void);
 

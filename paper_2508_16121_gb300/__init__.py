@@ -96,3 +96,81 @@ def to_device(params, device="cuda"):
     """numpy / torch parameter dict -> contiguous float32 tensors on device."""
     torch = _torch()
     return {k: torch.as_tensor(v, dtype=torch.float32).contiguous().to(device) for k, v in params.items()}
+
+
+def backward(x, params, dy, want=("dx",) + tuple("d" + n for n in PARAM_NAMES), workspace=None, stream=None):
+    """Adjoint of apply for float32 images (svdlut_backward).  Returns a dict
+    with the requested gradients ('dx', 'dU', 'dS', 'dV', 'dlut_w', 'dg_xy',
+    'dg_xc', 'dg_yc', 'dgrid_w'), each shaped like its input.  Deterministic:
+    identical inputs give identical bits."""
+    torch = _torch()
+    squeeze = x.dim() == 3
+    xb = x.unsqueeze(0) if squeeze else x
+    gb = dy.unsqueeze(0) if squeeze else dy
+    if xb.dtype != torch.float32 or gb.dtype != torch.float32:
+        raise ValueError("backward needs float32 x and dy")
+    if gb.shape != xb.shape or not xb.is_contiguous() or not gb.is_contiguous():
+        raise ValueError("dy must be contiguous and shaped like x")
+    B, _, H, W = xb.shape
+    d = dims_of(params)
+    p = _param_struct(params, B, d)
+    out = {}
+    ptrs = {}
+    for n in PARAM_NAMES:
+        if "d" + n in want:
+            t = torch.empty_like(params[n])
+            out["d" + n] = t
+            ptrs["d" + n] = t.data_ptr() if t.numel() else None
+    g = _lib.Grads(**ptrs)
+    dx = torch.empty_like(xb) if "dx" in want else None
+    lib = _lib.load()
+    need = lib.svdlut_backward_workspace_size(ctypes.byref(d), B, H, W)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=xb.device)
+    _lib.check(lib.svdlut_backward(ctypes.byref(d), ctypes.byref(p), B, H, W, ctypes.c_void_p(xb.data_ptr()),
+                                   ctypes.c_void_p(gb.data_ptr()),
+                                   ctypes.c_void_p(dx.data_ptr()) if dx is not None else None,
+                                   ctypes.byref(g), ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                   _stream_ptr(stream)))
+    if dx is not None:
+        out["dx"] = dx[0] if squeeze else dx
+    return out
+
+
+class _ApplyFn:
+    """torch.autograd.Function around svdlut_apply / svdlut_backward."""
+    _cls = None
+
+    @classmethod
+    def get(cls):
+        if cls._cls is None:
+            torch = _torch()
+
+            class Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, x, *tensors):
+                    params = dict(zip(PARAM_NAMES, tensors))
+                    ctx.save_for_backward(x, *tensors)
+                    return apply(x, params)
+
+                @staticmethod
+                def backward(ctx, gy):
+                    x, *tensors = ctx.saved_tensors
+                    params = dict(zip(PARAM_NAMES, tensors))
+                    want = []
+                    if ctx.needs_input_grad[0]:
+                        want.append("dx")
+                    for i, n in enumerate(PARAM_NAMES):
+                        if ctx.needs_input_grad[1 + i]:
+                            want.append("d" + n)
+                    g = backward(x, params, gy.contiguous(), want=tuple(want))
+                    return (g.get("dx"),) + tuple(g.get("d" + n) for n in PARAM_NAMES)
+
+            cls._cls = Fn
+        return cls._cls
+
+
+def apply_autograd(x, params):
+    """Differentiable apply (float32): gradients flow to x and every
+    parameter tensor through svdlut_backward."""
+    return _ApplyFn.get().apply(x, *[params[n] for n in PARAM_NAMES])

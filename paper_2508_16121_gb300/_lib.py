@@ -27,6 +27,10 @@ class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("U", "S", "V", "lut_w", "g_xy", "g_xc", "g_yc", "grid_w")]
 
 
+class Grads(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("dU", "dS", "dV", "dlut_w", "dg_xy", "dg_xc", "dg_yc", "dgrid_w")]
+
+
 class SvdlutError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"svdlut: {STATUS_NAMES.get(status, status)}: {msg}")
@@ -63,6 +67,11 @@ def _declare(lib):
     lib.svdlut_apply.argtypes = [P(Dims), P(Params), c_int, c_int, c_int, c_int, c_void_p, c_void_p,
                                  c_void_p]
     lib.svdlut_apply.restype = c_int
+    lib.svdlut_backward.argtypes = [P(Dims), P(Params), c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                    P(Grads), c_void_p, c_size_t, c_void_p]
+    lib.svdlut_backward.restype = c_int
+    lib.svdlut_backward_workspace_size.argtypes = [P(Dims), c_int, c_int, c_int]
+    lib.svdlut_backward_workspace_size.restype = c_size_t
     for name, argtypes in _EXTRA.items():
         if hasattr(lib, name):
             f = getattr(lib, name)
@@ -79,4 +88,5 @@ def check(status: int):
 
 
 # names every build of the library exports (declared in include/svdlut.h)
-EXPORTED = ["svdlut_apply", "svdlut_last_error", "svdlut_version"]
+EXPORTED = ["svdlut_apply", "svdlut_backward", "svdlut_backward_workspace_size", "svdlut_last_error",
+            "svdlut_version"]

@@ -35,7 +35,8 @@ static_assert(kTileW <= kThreads, "column tables need one thread each");
 
 struct ImgDesc {
     const void *x;
-    void *y;
+    void *y;          // forward: output image; adjoint: dx
+    const float *dy;  // adjoint only: upstream gradient
     const float *U, *S, *V, *lw, *gxy, *gxc, *gyc, *gw;
     int H, W;
     int D, R, K, Dsx, Dsy, Dsc;
@@ -222,6 +223,7 @@ __device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, f
     for (int p = 0; p < 3; ++p) {
         if (pairs_at_once == 1 || p == 0) {
             // slot <-> (c, p): slot = c * 3 + p when all pairs are held, else c
+#pragma unroll 4
             for (int e = tid; e < nf * DR; e += kThreads) {
                 const int slot = e / DR, ir = e - slot * DR, i = ir / R, r = ir - i * R;
                 const int c = slot / pairs_at_once, pp = pairs_at_once == 3 ? slot - c * 3 : p;
@@ -345,6 +347,28 @@ __device__ __forceinline__ BlockBufs block_bufs(float *scratch, int nvx, int nvy
     return b;
 }
 
+// sum_{k = c, c+3, ... < K} w_k[which] * src[k * kstride]: the grids feeding one
+// output channel (Supp. Eq. 20), weighted (Eq. 19).  Terms are taken four at a
+// time with all four loads issued before their FMAs.
+__device__ __forceinline__ float fold_k(const float *src, size_t kstride, int c, int K, const float *misc, int which)
+{
+    float s = 0.f;
+    for (int k0 = c; k0 < K; k0 += 12) {
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 + 3 * q;
+            v[q] = k < K ? __ldg(src + k * kstride) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 + 3 * q;
+            if (k < K) s = fmaf(misc[k * 4 + which], v[q], s);
+        }
+    }
+    return s;
+}
+
 // Block setup, phase A: grid slices of the block footprint folded per output
 // channel (sum over grids k = c mod 3 with their weights); column and row
 // cell tables.
@@ -357,29 +381,17 @@ __device__ inline void block_phase_a(const ImgDesc &d, const BlockGeom &g, const
     for (int r = warp; r < 3 * nvy; r += kWarps) {
         const int c = r / nvy, iyl = r - c * nvy;
         const float *src = d.gxy + static_cast<size_t>(g.iylo + iyl) * d.Dsx + g.ixlo;
-        for (int ixl = lane; ixl < nvx; ixl += 32) {
-            float s = 0.f;
-            for (int k = c; k < K; k += 3) s = fmaf(misc[k * 4 + 0], __ldg(src + k * kxy + ixl), s);
-            b.fxy[r * nvx + ixl] = s;
-        }
+        for (int ixl = lane; ixl < nvx; ixl += 32) b.fxy[r * nvx + ixl] = fold_k(src + ixl, kxy, c, K, misc, 0);
     }
     for (int r = warp; r < 3 * nvx; r += kWarps) {
         const int c = r / nvx, ixl = r - c * nvx;
         const float *src = d.gxc + static_cast<size_t>(g.ixlo + ixl) * Dsc;
-        for (int j = lane; j < Dsc; j += 32) {
-            float s = 0.f;
-            for (int k = c; k < K; k += 3) s = fmaf(misc[k * 4 + 1], __ldg(src + k * kxc + j), s);
-            b.fxc[r * Dsc + j] = s;
-        }
+        for (int j = lane; j < Dsc; j += 32) b.fxc[r * Dsc + j] = fold_k(src + j, kxc, c, K, misc, 1);
     }
     for (int r = warp; r < 3 * nvy; r += kWarps) {
         const int c = r / nvy, iyl = r - c * nvy;
         const float *src = d.gyc + static_cast<size_t>(g.iylo + iyl) * Dsc;
-        for (int j = lane; j < Dsc; j += 32) {
-            float s = 0.f;
-            for (int k = c; k < K; k += 3) s = fmaf(misc[k * 4 + 2], __ldg(src + k * kyc + j), s);
-            b.fyc[r * Dsc + j] = s;
-        }
+        for (int j = lane; j < Dsc; j += 32) b.fyc[r * Dsc + j] = fold_k(src + j, kyc, c, K, misc, 2);
     }
     if (tid < kTileW) {
         int ix;
@@ -448,7 +460,14 @@ __device__ __forceinline__ void lut_pair(const float4 *__restrict__ q, float da,
     y2 += fmaf(fmaf(q2.w, da, q2.x), db, fmaf(q1.y, da, q0.z));
 }
 
-template <typename T, int N>
+// DX = false: the forward transform, y = f(x).
+// DX = true (T = float): the pixel part of the adjoint, dx = (df/dx)^T dy,
+// from the slopes of the same cell coefficients: for a pair (alpha, beta),
+// d phi / d p_alpha = (D-1) (b + d delta_beta), d phi / d p_beta = (D-1) (c +
+// d delta_alpha) per output channel (weights already folded in); the xc / yc
+// terms add (Dsc-1) (s1 - s0) for their channel; zero where the input was
+// clamped (outside [0,1]).
+template <typename T, int N, bool DX>
 __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constant__ LaunchArgs<N> a)
 {
     extern __shared__ __align__(16) float smem[];
@@ -469,8 +488,9 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         while (im + 1 < a.n && a.img[im + 1].block_begin <= blk) ++im;
         return im;
     };
+    constexpr int NP = DX ? 6 : 3;  // planes loaded per row: x (and dy)
     // loads this lane's 4 pixels of row `row` (block-relative) of block blk
-    auto load_row = [&](int blk, int row, Raw (&dst)[3]) {
+    auto load_row = [&](int blk, int row, Raw (&dst)[NP]) {
         const ImgDesc &d = a.img[find_image(blk)];
         const int lb = blk - d.block_begin;
         const int band = lb / d.strips, strip = lb - band * d.strips;
@@ -482,9 +502,14 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         const bool ok = row < d.BH && y < d.H && n > 0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) dst[c] = ok ? PixIO<T>::load(src + c * plane, n, d.vec) : Raw();
+        if constexpr (DX) {
+            const float *g = d.dy + static_cast<size_t>(y) * d.W + x;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dst[3 + c] = ok ? PixIO<float>::load(g + c * plane, n, d.vec) : Raw();
+        }
     };
 
-    Raw cur[3], nxt[3];
+    Raw cur[NP], nxt[NP];
     int cur_im = -1;
     load_row(b_begin, warp, cur);
     for (int blk = b_begin; blk < b_end; ++blk) {
@@ -527,7 +552,15 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
             const int y = g.y0 + row;
             warp_row_tables(g, b, Dsc, row);
             __syncwarp();
-            if (n > 0) {
+            if (n > 0 && !DX) {
+                // the lane's 4 pixels usually span at most two x-cells: 3 vertices
+                const bool xy_fast = ixl[3] - ixl[0] <= 1;
+                float4 xa, xb, xc;
+                if (xy_fast) {
+                    xa = b.rxy[ixl[0]];
+                    xb = b.rxy[ixl[0] + 1];
+                    xc = b.rxy[min(ixl[0] + 2, g.nvx - 1)];
+                }
                 const float4 pr = PixIO<T>::to_float(cur[0]);
                 const float4 pg = PixIO<T>::to_float(cur[1]);
                 const float4 pb = PixIO<T>::to_float(cur[2]);
@@ -548,7 +581,8 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                     lut_pair(lcell + nc3 + ic[0] * D3 + ic[2] * 3, dc[0], dc[2], y0, y1, y2);
                     lut_pair(lcell + 2 * nc3 + ic[1] * D3 + ic[2] * 3, dc[1], dc[2], y0, y1, y2);
                     // xy slicing: row-interpolated vertices, lerp along x
-                    const float4 r0 = b.rxy[ixl[k]], r1 = b.rxy[ixl[k] + 1];
+                    const float4 r0 = xy_fast ? (ixl[k] == ixl[0] ? xa : xb) : b.rxy[ixl[k]];
+                    const float4 r1 = xy_fast ? (ixl[k] == ixl[0] ? xb : xc) : b.rxy[ixl[k] + 1];
                     const float dx = dxk[k];
                     y0 += fmaf(r1.x - r0.x, dx, r0.x);
                     y1 += fmaf(r1.y - r0.y, dx, r0.y);
@@ -569,9 +603,56 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                     PixIO<T>::store(dst + c * plane + static_cast<size_t>(y) * d.W + xbase,
                                     make_float4(out[c][0], out[c][1], out[c][2], out[c][3]), n, d.vec);
             }
+            if (n > 0 && DX) {
+                float outd[3][4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float xv[3] = {get(PixIO<T>::to_float(cur[0]), k), get(PixIO<T>::to_float(cur[1]), k),
+                                   get(PixIO<T>::to_float(cur[2]), k)};
+                    const float gy[3] = {get(PixIO<T>::to_float(cur[3]), k), get(PixIO<T>::to_float(cur[4]), k),
+                                         get(PixIO<T>::to_float(cur[5]), k)};
+                    float p[3], dc[3], ec[3], gp[3] = {0.f, 0.f, 0.f};
+                    int ic[3], jc[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        p[c] = fminf(fmaxf(xv[c], 0.f), 1.f);
+                        ic[c] = cell_of(p[c], fD1, fD2, dc[c]);
+                        jc[c] = cell_of(p[c], fS1, fS2, ec[c]);
+                    }
+                    // LUT pairs (rg, rb, gb): slopes along both axes
+#pragma unroll
+                    for (int pr = 0; pr < 3; ++pr) {
+                        const int A = pr == 2 ? 1 : 0, Bx = pr == 0 ? 1 : 2;
+                        const float4 *q = lcell + pr * nc3 + ic[A] * D3 + ic[Bx] * 3;
+                        const float4 q0 = q[0], q1 = q[1], q2 = q[2];
+                        // b = (q0.w, q1.x, q1.y), c = (q1.z, q1.w, q2.x), d = (q2.y, q2.z, q2.w)
+                        const float da = dc[A], db = dc[Bx];
+                        const float sa = gy[0] * fmaf(q2.y, db, q0.w) + gy[1] * fmaf(q2.z, db, q1.x) +
+                                         gy[2] * fmaf(q2.w, db, q1.y);
+                        const float sb = gy[0] * fmaf(q2.y, da, q1.z) + gy[1] * fmaf(q2.z, da, q1.w) +
+                                         gy[2] * fmaf(q2.w, da, q2.x);
+                        gp[A] = fmaf(fD1, sa, gp[A]);
+                        gp[Bx] = fmaf(fD1, sb, gp[Bx]);
+                    }
+                    const float dx = dxk[k];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float4 q = b.pxc[c * xcs + ixl[k] * Dsc + jc[c]];
+                        const float2 qy = b.ryc[c * Dc1 + jc[c]];
+                        const float s0 = fmaf(q.z - q.x, dx, q.x) + qy.x;
+                        const float s1 = fmaf(q.w - q.y, dx, q.y) + qy.y;
+                        gp[c] = fmaf(gy[c] * fS1, s1 - s0, gp[c]);
+                        outd[c][k] = (xv[c] >= 0.f && xv[c] <= 1.f) ? gp[c] : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    PixIO<float>::store(reinterpret_cast<float *>(d.y) + c * plane + static_cast<size_t>(y) * d.W + xbase,
+                                        make_float4(outd[c][0], outd[c][1], outd[c][2], outd[c][3]), n, d.vec);
+            }
             __syncwarp();  // row tables are rewritten for the next row
 #pragma unroll
-            for (int c = 0; c < 3; ++c) cur[c] = nxt[c];
+            for (int c = 0; c < NP; ++c) cur[c] = nxt[c];
         }
         if (warp >= g.rows && blk + 1 < b_end) load_row(blk + 1, warp, cur);  // no row here
     }

@@ -87,7 +87,7 @@ svdlut_status plan_uniform(LaunchArgs<N> &a, int sm_count, size_t smem_limit, si
     return SVDLUT_OK;
 }
 
-template <typename T, int N>
+template <typename T, int N, bool DX>
 svdlut_status launch_apply_t(LaunchArgs<N> &a, size_t smem, int sm_count, int max_smem, int device,
                              cudaStream_t s, int grid)
 {
@@ -97,27 +97,31 @@ svdlut_status launch_apply_t(LaunchArgs<N> &a, size_t smem, int sm_count, int ma
         std::lock_guard<std::mutex> g(mu);
         if (!attr_set[device]) {
             SVDLUT_CUDA_TRY(
-                cudaFuncSetAttribute(apply_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+                cudaFuncSetAttribute(apply_kernel<T, N, DX>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
             attr_set[device] = true;
         }
     }
     if (grid <= 0) grid = std::min(a.total_blocks, sm_count);
     grid = std::max(1, std::min(grid, a.total_blocks));
-    apply_kernel<T, N><<<grid, kThreads, smem, s>>>(a);
+    apply_kernel<T, N, DX><<<grid, kThreads, smem, s>>>(a);
     SVDLUT_CUDA_TRY(cudaGetLastError());
     return SVDLUT_OK;
 }
 
-// Launches apply_kernel for args whose blocks are already planned.
+// Launches apply_kernel for args whose blocks are already planned.  dx_mode
+// runs the pixel part of the adjoint (float images only).
 template <int N>
-svdlut_status launch_apply(LaunchArgs<N> &a, size_t smem, svdlut_dtype dt, cudaStream_t s, int grid)
+svdlut_status launch_apply(LaunchArgs<N> &a, size_t smem, svdlut_dtype dt, cudaStream_t s, int grid,
+                           bool dx_mode = false)
 {
     if (a.total_blocks <= 0) return SVDLUT_OK;
     DeviceInfo di;
     svdlut_status st = device_info(&di);
     if (st != SVDLUT_OK) return st;
-    return dt == SVDLUT_F32 ? launch_apply_t<float, N>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid)
-                            : launch_apply_t<uint8_t, N>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid);
+    if (dx_mode) return launch_apply_t<float, N, true>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid);
+    return dt == SVDLUT_F32
+               ? launch_apply_t<float, N, false>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid)
+               : launch_apply_t<uint8_t, N, false>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid);
 }
 
 }  // namespace svdlut

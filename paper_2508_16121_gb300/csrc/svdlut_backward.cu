@@ -1,0 +1,792 @@
+// svdlut_backward: adjoint of the fused transform (FP32 images).
+//
+// The paper trains end to end through its slicing + LUT transform (Sec. 4.2)
+// and prints no derivative; everything here is the exact derivative of the
+// forward map of Eq. 8 / Supp. Eqs. 10-20.  Passes (all on the caller's
+// stream, no atomics, every sum in a fixed order -> bitwise repeatable):
+//   1. dx      : apply_kernel<float, N, true> (slopes of the same cells).
+//   2. lut     : lut_grad_kernel scatters dy_c * bilinear weights into
+//                warp-private tables G^c_p (one channel per warp), then sums
+//                the warps of a CTA into a per-CTA partial.
+//   3. grid    : grid_grad_kernel does the same for the folded grid planes
+//                (xy, xc, yc per output channel) over 128-px column blocks.
+//   4. reduce  : lut_finalize_kernel sums the CTA partials and contracts
+//                through T = U diag(S) V^T (Eq. 7) to dU, dS, dV, dlut_w;
+//                grid_reduce_kernel + grid_finalize_kernel give dg_* and dgrid_w.
+#include <algorithm>
+#include <cmath>
+
+#include "apply_kernel.cuh"
+#include "apply_launch.cuh"
+
+namespace svdlut {
+
+// ---------------------------------------------------------------------------
+// deterministic warp scatter
+// ---------------------------------------------------------------------------
+
+// Position of the n-th (0-based) set bit of m (m has more than n set bits).
+__device__ __forceinline__ int nth_set_bit(unsigned int m, int n)
+{
+    int p = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const unsigned int lo = p + w >= 32 ? 0xffffffffu : ((1u << (p + w)) - 1u);
+        if (__popc(m & lo) <= n) p += w;
+    }
+    return p;
+}
+
+// Adds v[corner][ch] to tab[key + off(corner) + ch], corner offsets
+// (0, ld, cs, ld + cs) for the (00, 10, 01, 11) corners of a bilinear cell.
+// Lanes with equal keys are first summed by a shuffle tree over their ranks
+// in the group (fixed order); the lowest lane of each group then writes, one
+// corner at a time with a warp barrier between corners, so two groups never
+// update one address in the same step.  key < 0 marks an inactive lane.
+// Every lane of the warp must call this.
+template <int NC>
+__device__ __forceinline__ void warp_scatter(float *tab, int key, int ld, int cs, float (&v)[4][NC])
+{
+    const unsigned int full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned int me = 1u << lane;
+    const int k = key >= 0 ? key : -1 - lane;
+    const unsigned int grp = __match_any_sync(full, k);
+    if (!__all_sync(full, grp == me)) {
+        if (__all_sync(full, grp == full)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) v[q][c] += __shfl_xor_sync(full, v[q][c], o);
+        } else {
+            const int rank = __popc(grp & (me - 1));
+            const int size = __popc(grp);
+            const int maxsize = static_cast<int>(__reduce_max_sync(full, static_cast<unsigned int>(size)));
+            for (int s = 1; s < maxsize; s <<= 1) {
+                const int src_rank = rank + s;
+                const bool take = (rank & (2 * s - 1)) == 0 && src_rank < size;
+                const int src = take ? nth_set_bit(grp, src_rank) : lane;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        const float o = __shfl_sync(full, v[q][c], src);
+                        if (take) v[q][c] += o;
+                    }
+            }
+        }
+    }
+    const bool leader = key >= 0 && (grp & (me - 1)) == 0;
+    const int off[4] = {0, ld, cs, ld + cs};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (leader) {
+            float *t = tab + key + off[q];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) t[c] += v[q][c];
+        }
+        __syncwarp();
+    }
+}
+
+// Fixed-order warp sum (butterfly); every lane gets the total.
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+constexpr int kLutWarps = 12;  // 4 groups x 3 output channels
+constexpr int kLutThreads = kLutWarps * 32;
+
+struct BwdArgs {
+    const float *x, *dy;
+    int B, H, W;
+    int D, K, Dsx, Dsy, Dsc;
+    float rW1, rH1;
+    int strips;
+    int vec;  // 16-byte loads allowed
+};
+
+// ---------------------------------------------------------------------------
+// LUT gradients: G^c_p[i][j] = sum_px dy_c * bilinear weight of vertex (i, j)
+// at (x_alpha, x_beta) for pair p = (alpha, beta).
+// grid (P, B); CTA p owns rows [p H / P, (p+1) H / P) of image blockIdx.y.
+// Output: lut_part[b][p][c][pair][D*D], sums_part[b][p][c] (sum of dy_c).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kLutThreads, 1)
+    lut_grad_kernel(BwdArgs a, int P, float *__restrict__ lut_part, float *__restrict__ sums_part)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = warp / 3, ch = warp - grp * 3;
+    const int b = blockIdx.y, p = blockIdx.x;
+    const int D = a.D, DD = D * D;
+    float *tab = sm + warp * 3 * DD;  // [pair][D][D] for output channel ch
+    float *sums = sm + kLutWarps * 3 * DD;
+    for (int e = threadIdx.x; e < kLutWarps * 3 * DD; e += kLutThreads) sm[e] = 0.f;
+    __syncthreads();
+
+    const int r0 = static_cast<int>((static_cast<long long>(a.H) * p) / P);
+    const int r1 = static_cast<int>((static_cast<long long>(a.H) * (p + 1)) / P);
+    const size_t plane = static_cast<size_t>(a.H) * a.W;
+    const float *xb = a.x + static_cast<size_t>(b) * 3 * plane;
+    const float *gb = a.dy + static_cast<size_t>(b) * 3 * plane + ch * plane;
+    const float fD1 = static_cast<float>(D - 1), fD2 = static_cast<float>(D - 2);
+    const int units = (r1 - r0) * a.strips;
+    float dysum = 0.f;
+    for (int u = grp; u < units; u += kLutWarps / 3) {
+        const int row = r0 + u / a.strips, strip = u - (u / a.strips) * a.strips;
+        const int x = strip * kTileW + lane * 4;
+        const int n = min(4, a.W - x);
+        const size_t o = static_cast<size_t>(row) * a.W + x;
+        float4 pr = make_float4(0.f, 0.f, 0.f, 0.f), pg = pr, pb = pr, g = pr;
+        if (n > 0) {
+            const bool v = a.vec && n == 4;
+            pr = PixIO<float>::load(xb + o, n, v);
+            pg = PixIO<float>::load(xb + plane + o, n, v);
+            pb = PixIO<float>::load(xb + 2 * plane + o, n, v);
+            g = PixIO<float>::load(gb + o, n, v);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool act = k < n;
+            const float gy = act ? get(g, k) : 0.f;
+            dysum += gy;
+            float pc[3] = {get(pr, k), get(pg, k), get(pb, k)}, dc[3];
+            int ic[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                pc[c] = fminf(fmaxf(pc[c], 0.f), 1.f);
+                ic[c] = cell_of(pc[c], fD1, fD2, dc[c]);
+            }
+#pragma unroll
+            for (int pair = 0; pair < 3; ++pair) {
+                const int A = pair == 2 ? 1 : 0, Bx = pair == 0 ? 1 : 2;
+                const float da = dc[A], db = dc[Bx];
+                float v[4][1] = {{gy * (1.f - da) * (1.f - db)}, {gy * da * (1.f - db)},
+                                 {gy * (1.f - da) * db}, {gy * da * db}};
+                warp_scatter<1>(tab + pair * DD, act ? ic[A] * D + ic[Bx] : -1, D, 1, v);
+            }
+        }
+    }
+    dysum = warp_sum(dysum);
+    if (lane == 0) sums[warp] = dysum;
+    __syncthreads();
+    // CTA partial: sum the 4 groups of each channel in order
+    float *out = lut_part + (static_cast<size_t>(b) * P + p) * 9 * DD;
+    for (int e = threadIdx.x; e < 9 * DD; e += kLutThreads) {
+        const int c = e / (3 * DD), r = e - c * 3 * DD;
+        float s = 0.f;
+        for (int gq = 0; gq < kLutWarps / 3; ++gq) s += sm[(gq * 3 + c) * 3 * DD + r];
+        out[e] = s;
+    }
+    if (threadIdx.x < 3) {
+        float s = 0.f;
+        for (int gq = 0; gq < kLutWarps / 3; ++gq) s += sums[gq * 3 + threadIdx.x];
+        sums_part[(static_cast<size_t>(b) * P + p) * 3 + threadIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// grid gradients per output channel c (folded planes F_c = sum_{k=c mod 3}
+// w_k g_k): dFxy_c[iy][ix], dFxc_c[ix][j], dFyc_c[iy][j] = scatters of dy_c.
+// Blocks: 128-px column strip x BH rows (host plan); warp w owns a contiguous
+// run of rows.  Output per block: xy [nvy][nvx][3], xc [3][nvx][Dsc],
+// yc [3][nvy][Dsc] in block-local indexing.
+// ---------------------------------------------------------------------------
+struct GridPlan {
+    int BH, bands, nblk;   // per image
+    int nvx, nvy, rpw, nvyw;  // maxima
+    int blk_stride;        // floats per block partial
+};
+
+__host__ __device__ inline int grid_warp_floats(int nvx, int nvyw, int Dsc)
+{
+    return (3 * nvyw * nvx + 3 * nvx * Dsc + 3 * nvyw * Dsc + 3) & ~3;
+}
+
+__host__ __device__ inline int grid_block_floats(int nvx, int nvy, int Dsc)
+{
+    return 3 * nvy * nvx + 3 * nvx * Dsc + 3 * nvy * Dsc;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    grid_grad_kernel(BwdArgs a, GridPlan gp, float *__restrict__ grid_part)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.y, lb = blockIdx.x;
+    const int band = lb / a.strips, strip = lb - band * a.strips;
+    const int x0 = strip * kTileW, y0 = band * gp.BH;
+    const int rows = min(gp.BH, a.H - y0);
+    if (rows <= 0) return;
+    const int Dsc = a.Dsc, Dc2 = Dsc - 2;
+    // block footprint
+    int ixlo, ixhi, iylo, iyhi;
+    float t;
+    spatial_cell(x0, a.W, a.Dsx, a.rW1, ixlo, t);
+    spatial_cell(min(x0 + kTileW - 1, a.W - 1), a.W, a.Dsx, a.rW1, ixhi, t);
+    spatial_cell(y0, a.H, a.Dsy, a.rH1, iylo, t);
+    spatial_cell(y0 + rows - 1, a.H, a.Dsy, a.rH1, iyhi, t);
+    const int nvx = min(min(ixhi + 1, a.Dsx - 1) - ixlo + 1, gp.nvx);
+    const int nvy = min(min(iyhi + 1, a.Dsy - 1) - iylo + 1, gp.nvy);
+    // this warp's rows and their footprint
+    const int rpw = (rows + kWarps - 1) / kWarps;
+    const int wr0 = min(warp * rpw, rows), wr1 = min(wr0 + rpw, rows);
+    int wylo = iylo, wyhi = iylo;
+    if (wr1 > wr0) {
+        spatial_cell(y0 + wr0, a.H, a.Dsy, a.rH1, wylo, t);
+        spatial_cell(y0 + wr1 - 1, a.H, a.Dsy, a.rH1, wyhi, t);
+    }
+    const int nvyw = min(min(wyhi + 1, a.Dsy - 1) - wylo + 1, gp.nvyw);
+
+    const int wf = grid_warp_floats(gp.nvx, gp.nvyw, Dsc);
+    float *wt = sm + warp * wf;
+    float *txy = wt;                             // [nvyw][nvx][3]
+    float *txc = txy + 3 * gp.nvyw * gp.nvx;     // [3][nvx][Dsc]
+    float *tyc = txc + 3 * gp.nvx * Dsc;         // [3][nvyw][Dsc]
+    for (int e = threadIdx.x; e < kWarps * wf; e += kThreads) sm[e] = 0.f;
+    __syncthreads();
+
+    const size_t plane = static_cast<size_t>(a.H) * a.W;
+    const float *xb = a.x + static_cast<size_t>(b) * 3 * plane;
+    const float *gb = a.dy + static_cast<size_t>(b) * 3 * plane;
+    const float fS1 = static_cast<float>(Dsc - 1), fS2 = static_cast<float>(Dc2);
+    const int x = x0 + lane * 4;
+    const int n = min(4, a.W - x);
+    int ixl[4];
+    float dxk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int ix;
+        spatial_cell(min(x + k, a.W - 1), a.W, a.Dsx, a.rW1, ix, dxk[k]);
+        ixl[k] = max(0, min(ix - ixlo, nvx - 2));
+    }
+    for (int r = wr0; r < wr1; ++r) {
+        const int y = y0 + r;
+        int iy;
+        float dy;
+        spatial_cell(y, a.H, a.Dsy, a.rH1, iy, dy);
+        const int iyw = max(0, min(iy - wylo, nvyw - 2));
+        const size_t o = static_cast<size_t>(y) * a.W + x;
+        float4 P[3], G[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            P[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            G[c] = P[c];
+            if (n > 0) {
+                P[c] = PixIO<float>::load(xb + c * plane + o, n, a.vec && n == 4);
+                G[c] = PixIO<float>::load(gb + c * plane + o, n, a.vec && n == 4);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool act = k < n;
+            const float dx = dxk[k];
+            float gy[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gy[c] = act ? get(G[c], k) : 0.f;
+            {   // xy: corners (iy, ix), (iy+1, ix), (iy, ix+1), (iy+1, ix+1)
+                float v[4][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    v[0][c] = gy[c] * (1.f - dy) * (1.f - dx);
+                    v[1][c] = gy[c] * dy * (1.f - dx);
+                    v[2][c] = gy[c] * (1.f - dy) * dx;
+                    v[3][c] = gy[c] * dy * dx;
+                }
+                warp_scatter<3>(txy, act ? (iyw * gp.nvx + ixl[k]) * 3 : -1, gp.nvx * 3, 3, v);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float pc = fminf(fmaxf(get(P[c], k), 0.f), 1.f);
+                float ec;
+                const int jc = cell_of(pc, fS1, fS2, ec);
+                {   // xc: corners (ix, j), (ix+1, j), (ix, j+1), (ix+1, j+1)
+                    float v[4][1] = {{gy[c] * (1.f - dx) * (1.f - ec)}, {gy[c] * dx * (1.f - ec)},
+                                     {gy[c] * (1.f - dx) * ec}, {gy[c] * dx * ec}};
+                    warp_scatter<1>(txc + c * gp.nvx * Dsc, act ? ixl[k] * Dsc + jc : -1, Dsc, 1, v);
+                }
+                {   // yc: corners (iy, j), (iy+1, j), (iy, j+1), (iy+1, j+1)
+                    float v[4][1] = {{gy[c] * (1.f - dy) * (1.f - ec)}, {gy[c] * dy * (1.f - ec)},
+                                     {gy[c] * (1.f - dy) * ec}, {gy[c] * dy * ec}};
+                    warp_scatter<1>(tyc + c * gp.nvyw * Dsc, act ? iyw * Dsc + jc : -1, Dsc, 1, v);
+                }
+            }
+        }
+    }
+    // the warps' first vertex row relative to the block's
+    __shared__ int wy_off[kWarps], wy_n[kWarps];
+    if (lane == 0) {
+        wy_off[warp] = wylo - iylo;
+        wy_n[warp] = wr1 > wr0 ? nvyw : 0;
+    }
+    __syncthreads();
+    // block partial: sum the warps in order (each block entry independently)
+    float *out = grid_part + (static_cast<size_t>(b) * gp.nblk + lb) * gp.blk_stride;
+    float *oxy = out, *oxc = out + 3 * gp.nvy * gp.nvx, *oyc = oxc + 3 * gp.nvx * Dsc;
+    for (int e = threadIdx.x; e < nvy * nvx * 3; e += kThreads) {
+        const int iyb = e / (nvx * 3), r = e - iyb * nvx * 3;  // r = ix * 3 + c
+        float s = 0.f;
+        for (int w = 0; w < kWarps; ++w) {
+            const int iw = iyb - wy_off[w];
+            if (iw >= 0 && iw < wy_n[w]) s += sm[w * wf + iw * gp.nvx * 3 + r];
+        }
+        oxy[iyb * gp.nvx * 3 + r] = s;
+    }
+    for (int e = threadIdx.x; e < 3 * nvx * Dsc; e += kThreads) {
+        const int c = e / (nvx * Dsc), r = e - c * nvx * Dsc;
+        float s = 0.f;
+        for (int w = 0; w < kWarps; ++w) s += sm[w * wf + 3 * gp.nvyw * gp.nvx + c * gp.nvx * Dsc + r];
+        oxc[c * gp.nvx * Dsc + r] = s;
+    }
+    for (int e = threadIdx.x; e < 3 * nvy * Dsc; e += kThreads) {
+        const int c = e / (nvy * Dsc), r = e - c * nvy * Dsc, iyb = r / Dsc, j = r - iyb * Dsc;
+        float s = 0.f;
+        for (int w = 0; w < kWarps; ++w) {
+            const int iw = iyb - wy_off[w];
+            if (iw >= 0 && iw < wy_n[w])
+                s += sm[w * wf + 3 * gp.nvyw * gp.nvx + 3 * gp.nvx * Dsc + (c * gp.nvyw + iw) * Dsc + j];
+        }
+        oyc[(c * gp.nvy + iyb) * Dsc + j] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LUT finalize: one CTA per (table c*3+pair, image).
+// ---------------------------------------------------------------------------
+constexpr int kFinThreads = 256;
+
+__device__ inline float block_sum(float v, float *red)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float s = 0.f;
+    for (int w = 0; w < kFinThreads / 32; ++w) s += red[w];
+    return s;
+}
+
+struct FinArgs {
+    const float *U, *S, *V, *lw;
+    float *dU, *dS, *dV, *dlw;
+    int D, R, P;
+};
+
+__global__ void __launch_bounds__(kFinThreads)
+    lut_finalize_kernel(FinArgs f, const float *__restrict__ lut_part, const float *__restrict__ sums_part)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int cp = blockIdx.x, b = blockIdx.y, c = cp / 3, pair = cp - c * 3;
+    const int D = f.D, R = f.R, DD = D * D, DR = D * R;
+    float *G = sm, *T = sm + DD, *Q = T + DD, *red = Q + DR;  // Q[i][r] = sum_j dT[i][j] V[j][r]
+    const float *U = f.U + (static_cast<size_t>(b) * 9 + cp) * DR;
+    const float *V = f.V + (static_cast<size_t>(b) * 9 + cp) * DR;
+    const float *S = f.S + (static_cast<size_t>(b) * 9 + cp) * R;
+    const float w = f.lw[static_cast<size_t>(b) * 12 + c * 4 + pair];
+    for (int e = threadIdx.x; e < DD; e += kFinThreads) {
+        float s = 0.f;
+        for (int p = 0; p < f.P; ++p) s += lut_part[((static_cast<size_t>(b) * f.P + p) * 9 + cp) * DD + e];
+        G[e] = s;
+        const int i = e / D, j = e - i * D;
+        float tv = 0.f;
+        for (int r = 0; r < R; ++r) tv = fmaf(U[i * R + r] * S[r], V[j * R + r], tv);
+        T[e] = tv;
+    }
+    __syncthreads();
+    // dw = <G, T>
+    float part = 0.f;
+    for (int e = threadIdx.x; e < DD; e += kFinThreads) part = fmaf(G[e], T[e], part);
+    const float dw = block_sum(part, red);
+    if (threadIdx.x == 0 && f.dlw) {
+        f.dlw[static_cast<size_t>(b) * 12 + c * 4 + pair] = dw;
+        if (pair == 0) {
+            float s = 0.f;
+            for (int p = 0; p < f.P; ++p) s += sums_part[(static_cast<size_t>(b) * f.P + p) * 3 + c];
+            f.dlw[static_cast<size_t>(b) * 12 + c * 4 + 3] = s;
+        }
+    }
+    // Q = (w G) V ; dU = Q diag(S) ; dS_r = sum_i U[i][r] Q[i][r]
+    for (int e = threadIdx.x; e < DR; e += kFinThreads) {
+        const int i = e / R, r = e - i * R;
+        float s = 0.f;
+        for (int j = 0; j < D; ++j) s = fmaf(G[i * D + j], V[j * R + r], s);
+        Q[e] = w * s;
+        if (f.dU) f.dU[(static_cast<size_t>(b) * 9 + cp) * DR + e] = w * s * S[r];
+    }
+    // dV = (w G)^T U diag(S)
+    if (f.dV)
+        for (int e = threadIdx.x; e < DR; e += kFinThreads) {
+            const int j = e / R, r = e - j * R;
+            float s = 0.f;
+            for (int i = 0; i < D; ++i) s = fmaf(G[i * D + j], U[i * R + r], s);
+            f.dV[(static_cast<size_t>(b) * 9 + cp) * DR + e] = w * s * S[r];
+        }
+    __syncthreads();
+    if (f.dS && threadIdx.x < R) {
+        const int r = threadIdx.x;
+        float s = 0.f;
+        for (int i = 0; i < D; ++i) s = fmaf(U[i * R + r], Q[i * R + r], s);
+        f.dS[(static_cast<size_t>(b) * 9 + cp) * R + r] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// grid reduce: dF planes per image from the block partials (fixed order over
+// the blocks covering each vertex).  dF layout per image:
+//   xy [Dsy][Dsx][3], xc [3][Dsx][Dsc], yc [3][Dsy][Dsc].
+// ---------------------------------------------------------------------------
+struct GridRed {
+    int B, H, W, Dsx, Dsy, Dsc, strips;
+    float rW1, rH1;
+    GridPlan gp;
+};
+
+// block footprint along one axis: first vertex and count (as grid_grad_kernel)
+__device__ __forceinline__ void axis_span(int p0, int cnt, int n, int Ds, float rn1, int vmax, int &lo, int &nv)
+{
+    int hi;
+    float t;
+    spatial_cell(p0, n, Ds, rn1, lo, t);
+    spatial_cell(p0 + cnt - 1, n, Ds, rn1, hi, t);
+    nv = min(min(hi + 1, Ds - 1) - lo + 1, vmax);
+}
+
+// range of strips / bands whose footprint may contain vertex v (pixel range
+// between the neighbouring vertices)
+__device__ __forceinline__ void cover_range(int v, int n, int Ds, int unit, int nunits, int &u0, int &u1)
+{
+    if (n <= 1) {
+        u0 = 0;
+        u1 = nunits - 1;
+        return;
+    }
+    const long long lo = (static_cast<long long>(max(v - 1, 0)) * (n - 1)) / (Ds - 1);
+    const long long hi = (static_cast<long long>(min(v + 1, Ds - 1)) * (n - 1) + (Ds - 2)) / (Ds - 1);
+    u0 = max(0, static_cast<int>(lo / unit) - 1);
+    u1 = min(nunits - 1, static_cast<int>(hi / unit) + 1);
+}
+
+__global__ void grid_reduce_kernel(GridRed g, const float *__restrict__ grid_part, float *__restrict__ dF)
+{
+    const int b = blockIdx.y;
+    const int Dsx = g.Dsx, Dsy = g.Dsy, Dsc = g.Dsc;
+    const int nxy = Dsy * Dsx * 3, nxc = 3 * Dsx * Dsc, nyc = 3 * Dsy * Dsc;
+    float *out = dF + static_cast<size_t>(b) * (nxy + nxc + nyc);
+    const GridPlan &gp = g.gp;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nxy + nxc + nyc; e += gridDim.x * blockDim.x) {
+        int iy = -1, ix = -1, j = 0, c = 0, plane;
+        if (e < nxy) {
+            plane = 0;
+            iy = e / (Dsx * 3);
+            const int r = e - iy * Dsx * 3;
+            ix = r / 3;
+            c = r - ix * 3;
+        } else if (e < nxy + nxc) {
+            plane = 1;
+            const int q = e - nxy;
+            c = q / (Dsx * Dsc);
+            const int r = q - c * Dsx * Dsc;
+            ix = r / Dsc;
+            j = r - ix * Dsc;
+        } else {
+            plane = 2;
+            const int q = e - nxy - nxc;
+            c = q / (Dsy * Dsc);
+            const int r = q - c * Dsy * Dsc;
+            iy = r / Dsc;
+            j = r - iy * Dsc;
+        }
+        int s0 = 0, s1 = g.strips - 1, b0 = 0, b1 = gp.bands - 1;
+        if (ix >= 0) cover_range(ix, g.W, Dsx, kTileW, g.strips, s0, s1);
+        if (iy >= 0) cover_range(iy, g.H, Dsy, gp.BH, gp.bands, b0, b1);
+        float s = 0.f;
+        for (int bd = b0; bd <= b1; ++bd) {
+            const int y0 = bd * gp.BH, rows = min(gp.BH, g.H - y0);
+            if (rows <= 0) continue;
+            int ylo, nvy;
+            axis_span(y0, rows, g.H, Dsy, g.rH1, gp.nvy, ylo, nvy);
+            if (iy >= 0 && (iy < ylo || iy >= ylo + nvy)) continue;
+            for (int st = s0; st <= s1; ++st) {
+                const int x0 = st * kTileW, cols = min(kTileW, g.W - x0);
+                int xlo, nvx;
+                axis_span(x0, cols, g.W, Dsx, g.rW1, gp.nvx, xlo, nvx);
+                if (ix >= 0 && (ix < xlo || ix >= xlo + nvx)) continue;
+                const float *bp = grid_part + (static_cast<size_t>(b) * gp.nblk + bd * g.strips + st) * gp.blk_stride;
+                if (plane == 0)
+                    s += bp[((iy - ylo) * gp.nvx + (ix - xlo)) * 3 + c];
+                else if (plane == 1)
+                    s += bp[3 * gp.nvy * gp.nvx + (c * gp.nvx + (ix - xlo)) * Dsc + j];
+                else
+                    s += bp[3 * gp.nvy * gp.nvx + 3 * gp.nvx * Dsc + (c * gp.nvy + (iy - ylo)) * Dsc + j];
+            }
+        }
+        out[e] = s;
+    }
+}
+
+// grid finalize: one CTA per (grid k, image):
+//   dg^k_plane = w^k_plane * dF_{k mod 3, plane};  dgrid_w[k] = <dF, g^k> per
+//   plane, bias = sum of dy_{k mod 3} (from the LUT pass partials).
+struct GridFin {
+    const float *gxy, *gxc, *gyc, *gw;
+    float *dgxy, *dgxc, *dgyc, *dgw;
+    int K, Dsx, Dsy, Dsc, P;
+};
+
+__global__ void __launch_bounds__(kFinThreads)
+    grid_finalize_kernel(GridFin f, const float *__restrict__ dF, const float *__restrict__ sums_part)
+{
+    __shared__ float red[kFinThreads / 32];
+    const int k = blockIdx.x, b = blockIdx.y, c = k % 3;
+    const int Dsx = f.Dsx, Dsy = f.Dsy, Dsc = f.Dsc;
+    const int nxy = Dsy * Dsx * 3, nxc = 3 * Dsx * Dsc, nyc = 3 * Dsy * Dsc;
+    const float *F = dF + static_cast<size_t>(b) * (nxy + nxc + nyc);
+    const float *w = f.gw + (static_cast<size_t>(b) * f.K + k) * 4;
+    const size_t kxy = static_cast<size_t>(Dsy) * Dsx, kxc = static_cast<size_t>(Dsx) * Dsc,
+                 kyc = static_cast<size_t>(Dsy) * Dsc;
+    const size_t bk = static_cast<size_t>(b) * f.K + k;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int e = threadIdx.x; e < Dsy * Dsx; e += kFinThreads) {
+        const float F0 = F[e * 3 + c];
+        a0 = fmaf(F0, f.gxy[bk * kxy + e], a0);
+        if (f.dgxy) f.dgxy[bk * kxy + e] = w[0] * F0;
+    }
+    for (int e = threadIdx.x; e < Dsx * Dsc; e += kFinThreads) {
+        const float F1 = F[nxy + c * Dsx * Dsc + e];
+        a1 = fmaf(F1, f.gxc[bk * kxc + e], a1);
+        if (f.dgxc) f.dgxc[bk * kxc + e] = w[1] * F1;
+    }
+    for (int e = threadIdx.x; e < Dsy * Dsc; e += kFinThreads) {
+        const float F2 = F[nxy + nxc + c * Dsy * Dsc + e];
+        a2 = fmaf(F2, f.gyc[bk * kyc + e], a2);
+        if (f.dgyc) f.dgyc[bk * kyc + e] = w[2] * F2;
+    }
+    const float s0 = block_sum(a0, red), s1 = block_sum(a1, red), s2 = block_sum(a2, red);
+    if (threadIdx.x == 0 && f.dgw) {
+        float s = 0.f;
+        for (int p = 0; p < f.P; ++p) s += sums_part[(static_cast<size_t>(b) * f.P + p) * 3 + c];
+        float *o = f.dgw + bk * 4;
+        o[0] = s0;
+        o[1] = s1;
+        o[2] = s2;
+        o[3] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host planning and workspace
+// ---------------------------------------------------------------------------
+struct BwdPlan {
+    int P;             // LUT-pass CTAs per image
+    size_t lut_smem;   // bytes
+    GridPlan gp;
+    size_t grid_smem;  // bytes
+    size_t off_lut, off_sums, off_grid, off_dF, total;  // workspace layout (bytes)
+};
+
+static size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
+
+// Lets kernel f use dynamic shared memory up to the opt-in limit minus its
+// static shared memory.
+static svdlut_status allow_dynamic_smem(const void *f, int max_optin)
+{
+    cudaFuncAttributes fa;
+    SVDLUT_CUDA_TRY(cudaFuncGetAttributes(&fa, f));
+    SVDLUT_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         max_optin - static_cast<int>(fa.sharedSizeBytes)));
+    return SVDLUT_OK;
+}
+
+static svdlut_status plan_backward(const svdlut_dims *d, int B, int H, int W, int sm_count, size_t smem_limit,
+                                   BwdPlan *pl)
+{
+    const int D = d->D_t, Dsc = d->Dsc;
+    pl->lut_smem = sizeof(float) * (static_cast<size_t>(kLutWarps) * 3 * D * D + kLutWarps);
+    if (pl->lut_smem > smem_limit) return fail(SVDLUT_ERR_UNSUPPORTED, "D_t=%d too large for the adjoint", D);
+    pl->P = std::max(1, std::min(H, (sm_count + B - 1) / B));
+    // grid pass: blocks of 128 x BH; bands chosen like the forward plan
+    const int strips = (W + kTileW - 1) / kTileW;
+    const int max_bands = std::max(1, (H + kMinBlockH - 1) / kMinBlockH);
+    int best = -1;
+    double best_score = -1e30;
+    GridPlan bestgp{};
+    for (int bands = 1; bands <= max_bands; ++bands) {
+        GridPlan gp{};
+        gp.BH = (H + bands - 1) / bands;
+        gp.bands = (H + gp.BH - 1) / gp.BH;
+        gp.nvx = span_bound(kTileW, W, d->Dsx);
+        gp.nvy = span_bound(gp.BH, H, d->Dsy);
+        gp.rpw = (gp.BH + kWarps - 1) / kWarps;
+        gp.nvyw = span_bound(gp.rpw, H, d->Dsy);
+        const size_t need = sizeof(float) * static_cast<size_t>(kWarps) * grid_warp_floats(gp.nvx, gp.nvyw, Dsc);
+        if (need + 256 > smem_limit) continue;  // + the kernel's static row offsets
+        const long long T = static_cast<long long>(B) * strips * gp.bands;
+        const double waves = std::ceil(static_cast<double>(T) / sm_count - 1e-9);
+        const double score = static_cast<double>(T) / (waves * sm_count) - 0.002 * waves;
+        if (score > best_score + 1e-12) {
+            best_score = score;
+            best = bands;
+            bestgp = gp;
+        }
+        if (bands >= 4 * sm_count) break;
+    }
+    if (best < 0) return fail(SVDLUT_ERR_UNSUPPORTED, "grid vertices too dense for the adjoint's blocks");
+    bestgp.nblk = strips * bestgp.bands;
+    bestgp.blk_stride = grid_block_floats(bestgp.nvx, bestgp.nvy, Dsc);
+    pl->gp = bestgp;
+    pl->grid_smem = sizeof(float) * static_cast<size_t>(kWarps) * grid_warp_floats(bestgp.nvx, bestgp.nvyw, Dsc);
+    size_t off = 0;
+    pl->off_lut = off;
+    off = align256(off + sizeof(float) * static_cast<size_t>(B) * pl->P * 9 * D * D);
+    pl->off_sums = off;
+    off = align256(off + sizeof(float) * static_cast<size_t>(B) * pl->P * 3);
+    pl->off_grid = off;
+    off = align256(off + sizeof(float) * static_cast<size_t>(B) * bestgp.nblk * bestgp.blk_stride);
+    pl->off_dF = off;
+    off = align256(off + sizeof(float) * static_cast<size_t>(B) *
+                             (3 * d->Dsy * d->Dsx + 3 * d->Dsx * Dsc + 3 * d->Dsy * Dsc));
+    pl->total = off;
+    return SVDLUT_OK;
+}
+
+static svdlut_status check_backward_args(const svdlut_dims *dims, const svdlut_params *params, int B, int H,
+                                         int W, const float *x, const float *dy)
+{
+    svdlut_status st = check_dims(dims);
+    if (st != SVDLUT_OK) return st;
+    if ((st = check_params(dims, params)) != SVDLUT_OK) return st;
+    if (B < 1 || H < 1 || W < 1) return fail(SVDLUT_ERR_INVALID_ARG, "B=%d H=%d W=%d must be >= 1", B, H, W);
+    if (!x || !dy) return fail(SVDLUT_ERR_INVALID_ARG, "x and dy are required");
+    if (!aligned(x, 4) || !aligned(dy, 4)) return fail(SVDLUT_ERR_INVALID_ARG, "x and dy must be 4-byte aligned");
+    return SVDLUT_OK;
+}
+
+}  // namespace svdlut
+
+using namespace svdlut;
+
+extern "C" size_t svdlut_backward_workspace_size(const svdlut_dims *dims, int B, int H, int W)
+{
+    if (check_dims(dims) != SVDLUT_OK || B < 1 || H < 1 || W < 1) return 0;
+    DeviceInfo di;
+    if (device_info(&di) != SVDLUT_OK) return 0;
+    BwdPlan pl;
+    if (plan_backward(dims, B, H, W, di.sm_count, static_cast<size_t>(di.max_smem_optin), &pl) != SVDLUT_OK)
+        return 0;
+    return pl.total;
+}
+
+extern "C" svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_params *params, int B, int H,
+                                         int W, const float *x, const float *dy, float *dx,
+                                         const svdlut_grads *grads, void *ws, size_t ws_bytes,
+                                         svdlut_stream_t stream)
+{
+    clear_error();
+    svdlut_status st = check_backward_args(dims, params, B, H, W, x, dy);
+    if (st != SVDLUT_OK) return st;
+    if (dx && !aligned(dx, 4)) return fail(SVDLUT_ERR_INVALID_ARG, "dx must be 4-byte aligned");
+    const size_t img = static_cast<size_t>(3) * H * W * sizeof(float);
+    if (dx) {
+        const char *ds = reinterpret_cast<const char *>(dx), *xs = reinterpret_cast<const char *>(x),
+                   *gs = reinterpret_cast<const char *>(dy);
+        const size_t n = B * img;
+        if ((ds < xs + n && xs < ds + n) || (ds < gs + n && gs < ds + n))
+            return fail(SVDLUT_ERR_INVALID_ARG, "dx overlaps x or dy");
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceInfo di;
+    if ((st = device_info(&di)) != SVDLUT_OK) return st;
+    const size_t smem_limit = static_cast<size_t>(di.max_smem_optin);
+
+    // 1. dx through the forward kernel's adjoint mode
+    if (dx) {
+        for (int b0 = 0; b0 < B; b0 += kPlainChunk) {
+            LaunchArgs<kPlainChunk> a{};
+            a.n = std::min(kPlainChunk, B - b0);
+            for (int i = 0; i < a.n; ++i) {
+                a.img[i] = make_desc(dims, params, b0 + i, H, W, SVDLUT_F32, x, dx);
+                a.img[i].dy = dy + static_cast<size_t>(b0 + i) * 3 * H * W;
+                a.img[i].vec = a.img[i].vec && aligned(a.img[i].dy, 16);
+            }
+            size_t smem = 0;
+            if ((st = plan_uniform(a, di.sm_count, smem_limit, &smem)) != SVDLUT_OK) return st;
+            if ((st = launch_apply(a, smem, SVDLUT_F32, s, 0, true)) != SVDLUT_OK) return st;
+        }
+    }
+    const svdlut_grads g0{};
+    const svdlut_grads &g = grads ? *grads : g0;
+    const bool want_lut = g.dU || g.dS || g.dV || g.dlut_w;
+    const bool want_grid = dims->K > 0 && (g.dg_xy || g.dg_xc || g.dg_yc || g.dgrid_w);
+    if (!want_lut && !want_grid) return SVDLUT_OK;
+
+    BwdPlan pl;
+    if ((st = plan_backward(dims, B, H, W, di.sm_count, smem_limit, &pl)) != SVDLUT_OK) return st;
+    if (!ws || ws_bytes < pl.total)
+        return fail(SVDLUT_ERR_WORKSPACE, "workspace of %zu bytes needed (got %zu)", pl.total, ws ? ws_bytes : 0);
+    if (!aligned(ws, 256)) return fail(SVDLUT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    char *w = static_cast<char *>(ws);
+    float *lut_part = reinterpret_cast<float *>(w + pl.off_lut);
+    float *sums_part = reinterpret_cast<float *>(w + pl.off_sums);
+    float *grid_part = reinterpret_cast<float *>(w + pl.off_grid);
+    float *dF = reinterpret_cast<float *>(w + pl.off_dF);
+
+    BwdArgs a{};
+    a.x = x;
+    a.dy = dy;
+    a.B = B;
+    a.H = H;
+    a.W = W;
+    a.D = dims->D_t;
+    a.K = dims->K;
+    a.Dsx = dims->Dsx;
+    a.Dsy = dims->Dsy;
+    a.Dsc = dims->Dsc;
+    a.rW1 = W > 1 ? 1.0f / static_cast<float>(W - 1) : 0.f;
+    a.rH1 = H > 1 ? 1.0f / static_cast<float>(H - 1) : 0.f;
+    a.strips = (W + kTileW - 1) / kTileW;
+    a.vec = (W % 4 == 0) && aligned(x, 16) && aligned(dy, 16);
+
+    static bool attr_done[64] = {};
+    if (!attr_done[di.device]) {
+        if ((st = allow_dynamic_smem(reinterpret_cast<const void *>(lut_grad_kernel), di.max_smem_optin)) != SVDLUT_OK)
+            return st;
+        if ((st = allow_dynamic_smem(reinterpret_cast<const void *>(grid_grad_kernel), di.max_smem_optin)) != SVDLUT_OK)
+            return st;
+        if ((st = allow_dynamic_smem(reinterpret_cast<const void *>(lut_finalize_kernel), di.max_smem_optin)) !=
+            SVDLUT_OK)
+            return st;
+        attr_done[di.device] = true;
+    }
+    if (pl.grid_smem + 256 > static_cast<size_t>(di.max_smem_optin) || pl.lut_smem > static_cast<size_t>(di.max_smem_optin))
+        return fail(SVDLUT_ERR_UNSUPPORTED, "adjoint tables do not fit in shared memory");
+    // 2. LUT pass (also produces the dy channel sums used by every bias)
+    lut_grad_kernel<<<dim3(pl.P, B), kLutThreads, pl.lut_smem, s>>>(a, pl.P, lut_part, sums_part);
+    SVDLUT_CUDA_TRY(cudaGetLastError());
+    if (want_lut) {
+        FinArgs f{params->U, params->S, params->V, params->lut_w, g.dU, g.dS, g.dV, g.dlut_w,
+                  dims->D_t, dims->rank, pl.P};
+        const size_t fsm = sizeof(float) * (2 * dims->D_t * dims->D_t + dims->D_t * dims->rank + kFinThreads / 32);
+        lut_finalize_kernel<<<dim3(9, B), kFinThreads, fsm, s>>>(f, lut_part, sums_part);
+        SVDLUT_CUDA_TRY(cudaGetLastError());
+    }
+    if (want_grid) {
+        grid_grad_kernel<<<dim3(pl.gp.nblk, B), kThreads, pl.grid_smem, s>>>(a, pl.gp, grid_part);
+        SVDLUT_CUDA_TRY(cudaGetLastError());
+        GridRed r{B, H, W, dims->Dsx, dims->Dsy, dims->Dsc, a.strips, a.rW1, a.rH1, pl.gp};
+        const int nF = 3 * dims->Dsy * dims->Dsx + 3 * dims->Dsx * dims->Dsc + 3 * dims->Dsy * dims->Dsc;
+        grid_reduce_kernel<<<dim3(std::max(1, std::min(1024, (nF + 255) / 256)), B), 256, 0, s>>>(r, grid_part, dF);
+        SVDLUT_CUDA_TRY(cudaGetLastError());
+        GridFin f{params->g_xy, params->g_xc, params->g_yc, params->grid_w, g.dg_xy, g.dg_xc, g.dg_yc, g.dgrid_w,
+                  dims->K, dims->Dsx, dims->Dsy, dims->Dsc, pl.P};
+        grid_finalize_kernel<<<dim3(dims->K, B), kFinThreads, 0, s>>>(f, dF, sums_part);
+        SVDLUT_CUDA_TRY(cudaGetLastError());
+    }
+    return SVDLUT_OK;
+}
