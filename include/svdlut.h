@@ -129,6 +129,31 @@ svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_params *para
 /* Bytes of workspace svdlut_backward needs for these sizes (0 on bad args). */
 size_t svdlut_backward_workspace_size(const svdlut_dims *dims, int B, int H, int W);
 
+/*
+ * svdlut_backward_noalloc -- svdlut_backward for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this is a library service.
+ *
+ * Some callers may not call cudaMalloc / cudaFree or any allocating routine
+ * themselves: a host whose device memory belongs to another runtime's pool,
+ * a latency-critical loop where an allocation could stall on a device-wide
+ * synchronisation, or code being recorded into a CUDA graph.  This entry takes
+ * the same arguments as svdlut_backward minus the workspace; its scratch space
+ * is a fixed 32 MiB array inside the library (present on every GPU that loads
+ * it, until the process exits), and it allocates nothing.
+ *  - Sizes whose svdlut_backward_workspace_size exceeds 32 MiB are rejected
+ *    with SVDLUT_ERR_UNSUPPORTED (e.g. 8 x 1920x1080 or one 3840x2160 image at
+ *    D_t=33 and 1/8-resolution grids fit).
+ *  - The first call on a device looks up the array's device address (one
+ *    cudaGetSymbolAddress with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls share the one array and leave their data in it.  Calls whose
+ *    kernels overlap on the GPU (other streams, other threads) race on it:
+ *    serialise them, e.g. on one stream.
+ */
+svdlut_status svdlut_backward_noalloc(const svdlut_dims *dims, const svdlut_params *params, int B, int H,
+                                      int W, const float *x, const float *dy, float *dx,
+                                      const svdlut_grads *grads, svdlut_stream_t stream);
+
 /* Message of the last error raised on this thread ("" if none). */
 const char *svdlut_last_error(void);
 

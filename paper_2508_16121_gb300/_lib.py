@@ -72,6 +72,9 @@ def _declare(lib):
     lib.svdlut_backward.restype = c_int
     lib.svdlut_backward_workspace_size.argtypes = [P(Dims), c_int, c_int, c_int]
     lib.svdlut_backward_workspace_size.restype = c_size_t
+    lib.svdlut_backward_noalloc.argtypes = [P(Dims), P(Params), c_int, c_int, c_int, c_void_p, c_void_p,
+                                            c_void_p, P(Grads), c_void_p]
+    lib.svdlut_backward_noalloc.restype = c_int
     for name, argtypes in _EXTRA.items():
         if hasattr(lib, name):
             f = getattr(lib, name)
@@ -88,5 +91,5 @@ def check(status: int):
 
 
 # names every build of the library exports (declared in include/svdlut.h)
-EXPORTED = ["svdlut_apply", "svdlut_backward", "svdlut_backward_workspace_size", "svdlut_last_error",
-            "svdlut_version"]
+EXPORTED = ["svdlut_apply", "svdlut_backward", "svdlut_backward_workspace_size", "svdlut_backward_noalloc",
+            "svdlut_last_error", "svdlut_version"]
