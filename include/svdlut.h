@@ -95,6 +95,54 @@ svdlut_status svdlut_apply(const svdlut_dims *dims, const svdlut_params *params,
                            svdlut_stream_t stream);
 
 /*
+ * One image of a ragged batch for svdlut_apply_batched: its size, transform
+ * sizes and parameters (the svdlut_params layouts without the batch axis),
+ * and device pointers to its [3][H][W] input and output.
+ */
+typedef struct {
+    int32_t H, W;
+    svdlut_dims dims;
+    svdlut_params params;
+    const void *x;
+    void *y;
+} svdlut_image;
+
+/* Launch shape of svdlut_apply_batched: target pixels per work block (0 =
+ * automatic: about four blocks per SM) and persistent CTAs (0 = one per SM). */
+typedef struct {
+    int32_t block_px;
+    int32_t ctas;
+} svdlut_launch_cfg;
+
+/*
+ * svdlut_apply_batched -- the fused transform of svdlut_apply (Eq. 8) over n
+ * images of uneven sizes, each with its own transform, in one persistent
+ * launch per 64 images.  imgs is a HOST array of n descriptors (read during the
+ * call only).  The images' blocks are taken from a counter in ws, so the call
+ * is capturable in a CUDA graph (a 4-byte memset + one kernel per 64 images).
+ * ws: device memory of svdlut_batched_workspace_size(n) bytes, 4-byte aligned;
+ * concurrent calls must use different workspaces.  cfg may be NULL.
+ * Errors: INVALID_ARG (a bad image, reported with its index), WORKSPACE,
+ * UNSUPPORTED, CUDA.
+ */
+svdlut_status svdlut_apply_batched(const svdlut_image *imgs, int n, svdlut_dtype dtype,
+                                   const svdlut_launch_cfg *cfg, void *ws, size_t ws_bytes,
+                                   svdlut_stream_t stream);
+
+/* Workspace bytes for a batch of n images (0 if n < 1). */
+size_t svdlut_batched_workspace_size(int n);
+
+/*
+ * svdlut_autotune_batched -- times svdlut_apply_batched on this batch for a
+ * set of block sizes (reps timed launches each, after one warm-up) and
+ * returns the fastest launch shape in *best (and its time in *best_ms if not
+ * NULL).  Synchronises the stream; not capturable.  Writes the images' y.
+ */
+svdlut_status svdlut_autotune_batched(const svdlut_image *imgs, int n, svdlut_dtype dtype, void *ws,
+                                      size_t ws_bytes, svdlut_stream_t stream, int reps,
+                                      svdlut_launch_cfg *best, float *best_ms);
+
+/*
  * Gradient outputs of svdlut_backward: device FP32 arrays with the layouts of
  * the matching svdlut_params fields (leading batch axis B).  Any pointer may
  * be NULL (that gradient is not computed).  Wanted outputs are overwritten.

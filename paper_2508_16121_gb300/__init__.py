@@ -174,3 +174,58 @@ def apply_autograd(x, params):
     """Differentiable apply (float32): gradients flow to x and every
     parameter tensor through svdlut_backward."""
     return _ApplyFn.get().apply(x, *[params[n] for n in PARAM_NAMES])
+
+
+class Batch:
+    """A ragged batch for svdlut_apply_batched: images of uneven sizes, each
+    with its own parameter dict (per-image layouts, no batch axis).  Holds the
+    host descriptor array and the device workspace so that repeated calls
+    (and CUDA-graph capture of a call) marshal nothing new."""
+
+    def __init__(self, xs, params_list, outs=None):
+        torch = _torch()
+        if len(xs) != len(params_list) or not xs:
+            raise ValueError("need one parameter dict per image")
+        self.dtype = _lib.U8 if xs[0].dtype == torch.uint8 else _lib.F32
+        self.xs = list(xs)
+        self.params = list(params_list)
+        self.outs = list(outs) if outs is not None else [torch.empty_like(x) for x in xs]
+        n = len(xs)
+        self.imgs = (_lib.Image * n)()
+        for i, (x, p, y) in enumerate(zip(self.xs, self.params, self.outs)):
+            if x.dim() != 3 or x.shape[0] != 3 or not x.is_contiguous() or not x.is_cuda:
+                raise ValueError("each image must be a contiguous [3,H,W] CUDA tensor")
+            if (x.dtype == torch.uint8) != (self.dtype == _lib.U8) or y.shape != x.shape or y.dtype != x.dtype:
+                raise ValueError("all images (and outputs) must share one dtype and match in shape")
+            d = dims_of(p)
+            self.imgs[i] = _lib.Image(x.shape[1], x.shape[2], d, _param_struct(p, 1, d),
+                                      ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()))
+        lib = _lib.load()
+        self.ws = torch.zeros(max(int(lib.svdlut_batched_workspace_size(n)), 4), dtype=torch.uint8,
+                              device=xs[0].device)
+        self.cfg = None
+
+    def run(self, stream=None):
+        lib = _lib.load()
+        cfg = ctypes.byref(self.cfg) if self.cfg is not None else None
+        _lib.check(lib.svdlut_apply_batched(self.imgs, len(self.xs), self.dtype, cfg,
+                                            ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                            _stream_ptr(stream)))
+        return self.outs
+
+    def autotune(self, reps=5, stream=None):
+        """Time a set of block sizes on this batch (native autotuner) and keep
+        the fastest; returns (block_px, ms)."""
+        lib = _lib.load()
+        best = _lib.LaunchCfg()
+        ms = ctypes.c_float()
+        _lib.check(lib.svdlut_autotune_batched(self.imgs, len(self.xs), self.dtype,
+                                               ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                               _stream_ptr(stream), reps, ctypes.byref(best), ctypes.byref(ms)))
+        self.cfg = best
+        return best.block_px, ms.value
+
+
+def apply_batched(xs, params_list, outs=None, stream=None):
+    """One persistent launch over images of uneven sizes (svdlut_apply_batched)."""
+    return Batch(xs, params_list, outs).run(stream)

@@ -31,6 +31,15 @@ class Grads(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("dU", "dS", "dV", "dlut_w", "dg_xy", "dg_xc", "dg_yc", "dgrid_w")]
 
 
+class Image(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("dims", Dims), ("params", Params),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p)]
+
+
+class LaunchCfg(ctypes.Structure):
+    _fields_ = [("block_px", ctypes.c_int32), ("ctas", ctypes.c_int32)]
+
+
 class SvdlutError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"svdlut: {STATUS_NAMES.get(status, status)}: {msg}")
@@ -72,6 +81,13 @@ def _declare(lib):
     lib.svdlut_backward.restype = c_int
     lib.svdlut_backward_workspace_size.argtypes = [P(Dims), c_int, c_int, c_int]
     lib.svdlut_backward_workspace_size.restype = c_size_t
+    lib.svdlut_apply_batched.argtypes = [P(Image), c_int, c_int, P(LaunchCfg), c_void_p, c_size_t, c_void_p]
+    lib.svdlut_apply_batched.restype = c_int
+    lib.svdlut_batched_workspace_size.argtypes = [c_int]
+    lib.svdlut_batched_workspace_size.restype = c_size_t
+    lib.svdlut_autotune_batched.argtypes = [P(Image), c_int, c_int, c_void_p, c_size_t, c_void_p, c_int,
+                                            P(LaunchCfg), ctypes.POINTER(ctypes.c_float)]
+    lib.svdlut_autotune_batched.restype = c_int
     lib.svdlut_backward_noalloc.argtypes = [P(Dims), P(Params), c_int, c_int, c_int, c_void_p, c_void_p,
                                             c_void_p, P(Grads), c_void_p]
     lib.svdlut_backward_noalloc.restype = c_int
@@ -91,5 +107,6 @@ def check(status: int):
 
 
 # names every build of the library exports (declared in include/svdlut.h)
-EXPORTED = ["svdlut_apply", "svdlut_backward", "svdlut_backward_workspace_size", "svdlut_backward_noalloc",
+EXPORTED = ["svdlut_apply", "svdlut_apply_batched", "svdlut_batched_workspace_size", "svdlut_autotune_batched",
+            "svdlut_backward", "svdlut_backward_workspace_size", "svdlut_backward_noalloc",
             "svdlut_last_error", "svdlut_version"]

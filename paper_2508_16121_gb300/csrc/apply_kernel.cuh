@@ -54,6 +54,7 @@ struct LaunchArgs {
     int nvx_max, nvy_max, bh_max;
     int lcell_floats;    // floats reserved for the cell table
     int scratch_floats;  // floats of the block buffers / prologue temporaries
+    unsigned int *queue;  // non-null: blocks are taken from this counter (must be 0 at launch)
     ImgDesc img[N];
 };
 
@@ -476,10 +477,21 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
     float *scratch = misc + kMiscFloats;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int G = gridDim.x, gi = blockIdx.x;
-    const int b_begin = static_cast<int>((static_cast<long long>(a.total_blocks) * gi) / G);
-    const int b_end = static_cast<int>((static_cast<long long>(a.total_blocks) * (gi + 1)) / G);
-    if (b_begin >= b_end) return;
+    // Block schedule: a contiguous range per CTA, or (queue) blocks taken in
+    // order from a global counter so that uneven blocks balance out.
+    int *slot = reinterpret_cast<int *>(misc + kMaxK * 4 + 3);
+    int blk, b_end;
+    if (a.queue) {
+        if (threadIdx.x == 0) *slot = static_cast<int>(atomicAdd(a.queue, 1u));
+        __syncthreads();
+        blk = *slot;
+        b_end = a.total_blocks;
+    } else {
+        const int G = gridDim.x, gi = blockIdx.x;
+        blk = static_cast<int>((static_cast<long long>(a.total_blocks) * gi) / G);
+        b_end = static_cast<int>((static_cast<long long>(a.total_blocks) * (gi + 1)) / G);
+    }
+    if (blk >= b_end) return;
 
     using Raw = typename PixIO<T>::Raw;
 
@@ -511,8 +523,8 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
 
     Raw cur[NP], nxt[NP];
     int cur_im = -1;
-    load_row(b_begin, warp, cur);
-    for (int blk = b_begin; blk < b_end; ++blk) {
+    load_row(blk, warp, cur);
+    for (;;) {
         const int im = find_image(blk);
         const ImgDesc &d = a.img[im];
         if (im != cur_im) {
@@ -523,8 +535,11 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         const BlockGeom g = block_geom(d, blk - d.block_begin, a.nvx_max, a.nvy_max);
         const BlockBufs b = block_bufs(scratch, g.nvx, g.nvy, d.Dsc, a.bh_max);
         __syncthreads();  // previous block's rows done with the buffers
+        if (a.queue && threadIdx.x == 0) *slot = static_cast<int>(atomicAdd(a.queue, 1u));
         block_phase_a(d, g, b, misc);
         __syncthreads();
+        const int next = a.queue ? *slot : blk + 1;
+        const bool has_next = next < b_end;
         block_phase_b(d, g, b);
         __syncthreads();
 
@@ -548,7 +563,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         for (int row = warp; row < g.rows; row += kWarps) {
             // next row of this warp, possibly in the next block
             if (row + kWarps < g.rows) load_row(blk, row + kWarps, nxt);
-            else if (blk + 1 < b_end) load_row(blk + 1, warp, nxt);
+            else if (has_next) load_row(next, warp, nxt);
             const int y = g.y0 + row;
             warp_row_tables(g, b, Dsc, row);
             __syncwarp();
@@ -654,7 +669,9 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
 #pragma unroll
             for (int c = 0; c < NP; ++c) cur[c] = nxt[c];
         }
-        if (warp >= g.rows && blk + 1 < b_end) load_row(blk + 1, warp, cur);  // no row here
+        if (warp >= g.rows && has_next) load_row(next, warp, cur);  // no row here
+        if (!has_next) break;
+        blk = next;
     }
 }
 
