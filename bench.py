@@ -35,6 +35,40 @@ METRIC = "Mpix/s and % HBM peak, SVDLUT apply at 4K (plain vs batched/learned), 
 N_SETS = 4  # rotating input/output sets: 4 x 199 MB > 129 MB L2
 
 
+KERNEL_SOURCES = ("paper_2508_16121_gb300/csrc/apply_kernel.cuh", "paper_2508_16121_gb300/csrc/apply_launch.cuh",
+                  "paper_2508_16121_gb300/csrc/svdlut_apply.cu")
+PROFILE_SUMMARY = "profiles/apply_kernel_f32_3840x2160_mix.md"
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    try:
+        text = open(os.path.join(ROOT, PROFILE_SUMMARY)).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_sources_sha256_16") != kernel_hash():
+        return None
+    try:
+        return int(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -192,6 +226,22 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     u8_ms = a.elapsed_time(b) / args.steps
 
+    # ---- image regimes (same 4K workload, all-noise / all-smooth pixels) ----
+    regimes = {}
+    for mode in ("noise", "smooth"):
+        xr, pr = si.make_batch(si.config_seed(1) + 7, 1, H, W, d, mode=mode)
+        xr_t, pr_t = torch.from_numpy(xr).to(dev), svdlut.to_device(pr, dev)
+        yr_t = torch.empty_like(xr_t)
+        regimes[mode] = round(H * W / 1e6 / (time_calls(lambda: svdlut.apply(xr_t, pr_t, out=yr_t), args.steps,
+                                                         stream) / 1e3), 1)
+        del xr_t, yr_t
+
+    # ---- ragged batch: 16 images 480p..4K, one graph-captured launch vs 16 plain calls ----
+    batched = run_batched_variant(svdlut, torch, dev, stream, args)
+
+    # ---- adjoint: 8 x 1920x1080 FP32, all gradients ----
+    backward = run_backward_variant(svdlut, torch, dev, stream, args)
+
     # ---- end to end through the public API with pinned host buffers ----
     xh = sets[0][0].cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
@@ -227,18 +277,92 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}",
                    "l2": f"rotating {N_SETS} input/output sets ({N_SETS * bytes_launch / 1e6:.0f} MB) > 129 MB L2"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "apply_kernel<float>", "bytes_per_launch": bytes_launch,
-                     "kernel_ms": round(kern_ms, 5), "peak_source": peak_src},
+                     "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                     "kernel": "apply_kernel<float, 16, false>", "bytes_per_launch": bytes_launch,
+                     "kernel_ms": round(kern_ms, 5), "peak_source": peak_src,
+                     "kernel_sources_sha256_16": kernel_hash()},
         "e2e": {"value": round(world * mpix / (e2e_ms / 1e3), 1), "unit": "Mpix/s",
                 "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4)},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "variants": {"u8_plain_4k": {"value": round(mpix / (u8_ms / 1e3), 1), "unit": "Mpix/s",
                                      "ms": round(u8_ms, 5),
-                                     "GB/s": round(algo_bytes_apply(H, W, d, 1) / (u8_ms / 1e3) / 1e9, 1)}},
+                                     "GB/s": round(algo_bytes_apply(H, W, d, 1) / (u8_ms / 1e3) / 1e9, 1)},
+                     "f32_plain_4k_by_regime_Mpix/s": regimes,
+                     "batched_16_ragged": batched,
+                     "backward_8x1080p": backward},
     }
     return out, (xh.numpy(), {k: v.cpu().numpy() for k, v in pd.items()}, d)
+
+
+def time_calls(fn, steps, stream, warmup=3):
+    """mean ms per call of fn() on `stream`, CUDA events around the loop"""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_batched_variant(svdlut, torch, dev, stream, args):
+    items = si.make_ragged()
+    xs = [torch.from_numpy(x).to(dev) for x, _, _ in items]
+    ps = [svdlut.to_device(p, dev) for _, _, p in items]
+    batch = svdlut.Batch(xs, ps)
+    block_px, _ = batch.autotune(reps=3)
+    batch.run()
+    torch.cuda.synchronize()
+    mpix = sum(x.shape[1] * x.shape[2] for x in xs) / 1e6
+    bytes_px = sum(algo_bytes_apply(x.shape[1], x.shape[2], d, 4) for (x, d, _) in items)
+    g_b = torch.cuda.CUDAGraph()
+    s_cap = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s_cap):
+        with torch.cuda.graph(g_b, stream=s_cap):
+            batch.run(stream=s_cap)
+    ys = [torch.empty_like(x) for x in xs]
+
+    def seq():
+        for x, p, y in zip(xs, ps, ys):
+            svdlut.apply(x, p, out=y)
+
+    seq()
+    torch.cuda.synchronize()
+    g_s = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s_cap):
+        with torch.cuda.graph(g_s, stream=s_cap):
+            for x, p, y in zip(xs, ps, ys):
+                svdlut.apply(x, p, out=y, stream=s_cap)
+    steps = max(3, args.steps // 4)
+    t_b = time_calls(g_b.replay, steps, stream)
+    t_s = time_calls(g_s.replay, steps, stream)
+    t_e = time_calls(seq, steps, stream)
+    return {"images": len(xs), "Mpix": round(mpix, 2), "autotuned_block_px": block_px,
+            "batched_graph": {"value": round(mpix / (t_b / 1e3), 1), "unit": "Mpix/s", "ms": round(t_b, 4),
+                              "GB/s": round(bytes_px / (t_b / 1e3) / 1e9, 1)},
+            "plain_x16_graph": {"value": round(mpix / (t_s / 1e3), 1), "unit": "Mpix/s", "ms": round(t_s, 4)},
+            "plain_x16_eager": {"value": round(mpix / (t_e / 1e3), 1), "unit": "Mpix/s", "ms": round(t_e, 4)},
+            "speedup_vs_plain_graph": round(t_s / t_b, 3)}
+
+
+def run_backward_variant(svdlut, torch, dev, stream, args):
+    H, W, B = 1080, 1920, 8
+    d = si.spatial_dims(H, W)
+    x, p = si.make_batch(si.config_seed(3), B, H, W, d)
+    xt, pt = torch.from_numpy(x).to(dev), svdlut.to_device(p, dev)
+    gt = torch.from_numpy(si.make_upstream(si.config_seed(3) + 1, x.shape)).to(dev)
+    ws = torch.empty(1 << 28, dtype=torch.uint8, device=dev)
+    steps = max(3, args.steps // 4)
+    ms = time_calls(lambda: svdlut.backward(xt, pt, gt, workspace=ws), steps, stream)
+    px = B * H * W
+    algo = px * 36 + sum(int(v.numel()) * 8 for v in pt.values())  # x, dy in; dx out; params in, grads out
+    return {"value": round(px / 1e6 / (ms / 1e3), 1), "unit": "Mpix/s", "ms": round(ms, 4),
+            "GB/s": round(algo / (ms / 1e3) / 1e9, 1), "workload": "8 x 1920x1080 FP32, all gradients"}
 
 
 def cpu_baseline(x, p, d, reps=2):
@@ -289,7 +413,7 @@ def run_reference(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=8000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
