@@ -1,0 +1,268 @@
+"""FP64 CPU oracle of the SVDLUT factor generator -- TEST INFRASTRUCTURE.
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline leg may import this module.  Plain numpy, float64.
+
+Architecture (Supp. Sec. A, Tables 1-5; m = 8, M_s = M_sw = M_t = M_tw = 8):
+  bilinear downsample of the input to 3 x 256 x 256           (Table 1, row 1)
+  5 x [Conv3x3 stride 2 pad 1 -> LeakyReLU -> InstanceNorm]   (Table 1; no IN
+      after the 5th), channels 3 -> 8 -> 16 -> 32 -> 64 -> 64
+  Dropout(0.5) (training), average pooling 8x8 -> 2x2, reshape to 256 = 32m
+  four heads, each FC 256 -> 8 then FC 8 -> n_out (Tables 2-5):
+     H_s  -> K*3*Ds^2 2D bilateral grids (planes xy, xc, yc per grid)
+     H_sw -> K*(3+1)  grid weights and bias
+     H_t  -> 9*(Dt*Ns + Ns + Dt*Ns): U, S, V of the nine 2D LUTs
+     H_tw -> 3*(3+1)  LUT weights and bias
+Readings (the paper leaves them open; listed in the design notes): LeakyReLU
+slope 0.2; InstanceNorm eps 1e-5 with affine scale/shift and biased variance;
+bilinear downsample with half-pixel centres (align_corners = False) and no
+antialiasing; average pool of 4x4 windows; no nonlinearity between the two FC
+layers of a head (a rank-8 factorisation); H_t's output is split as U, then S,
+then V, each in [c][pair] order; H_s's as [K][plane xy, xc, yc][17][17].
+The parameter count at K = 6 is 160,478, Table 7 ("Ours", 160.478K).
+
+Parity status: the paper prints no activations or outputs of the generator,
+so its values are "parity unpinned" beyond: the parameter count (Table 7 and
+its ablation rows), brute-force convolution on tiny inputs, the
+interpolation/normalisation invariants and central differences of this
+module's own forward (tests/test_oracle_generator.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+M = 8                  # backbone width m
+CH = (3, M, 2 * M, 4 * M, 8 * M, 8 * M)
+THUMB = 256
+SLOPE = 0.2
+EPS = 1e-5
+DT, NS, DS = 33, 8, 17  # LUT vertices, SVD rank, grid vertices
+HIDDEN = 8
+
+
+def head_sizes(K: int):
+    """output sizes of H_s, H_sw, H_t, H_tw"""
+    return (K * 3 * DS * DS, K * 4, 9 * (DT * NS + NS + DT * NS), 12)
+
+
+def param_layout(K: int):
+    """(name, shape) of every parameter, in the flat blob order"""
+    out = []
+    for i in range(5):
+        cin, cout = CH[i], CH[i + 1]
+        out += [(f"conv{i}.w", (cout, cin, 3, 3)), (f"conv{i}.b", (cout,))]
+        if i < 4:
+            out += [(f"in{i}.g", (cout,)), (f"in{i}.b", (cout,))]
+    for h, n in zip(("s", "sw", "t", "tw"), head_sizes(K)):
+        out += [(f"h{h}.w1", (HIDDEN, 32 * M)), (f"h{h}.b1", (HIDDEN,)),
+                (f"h{h}.w2", (n, HIDDEN)), (f"h{h}.b2", (n,))]
+    return out
+
+
+def param_count(K: int) -> int:
+    return int(sum(np.prod(s) for _, s in param_layout(K)))
+
+
+def unpack(blob, K):
+    blob = np.asarray(blob, dtype=np.float64)
+    p, o = {}, 0
+    for n, s in param_layout(K):
+        c = int(np.prod(s))
+        p[n] = blob[o:o + c].reshape(s)
+        o += c
+    assert o == blob.size
+    return p
+
+
+def pack(p, K):
+    return np.concatenate([np.asarray(p[n], dtype=np.float64).ravel() for n, _ in param_layout(K)])
+
+
+# ---------------------------------------------------------------- layers
+
+def downsample(x, S=THUMB):
+    """[B,3,H,W] -> [B,3,S,S]; output i samples source (i + 1/2) H/S - 1/2,
+    clamped to the image, bilinear between the two nearest pixels per axis."""
+    B, C, H, W = x.shape
+
+    def axis(n):
+        src = (np.arange(S) + 0.5) * (n / S) - 0.5
+        src = np.clip(src, 0.0, n - 1)
+        i0 = np.floor(src).astype(int)
+        i1 = np.minimum(i0 + 1, n - 1)
+        return i0, i1, src - i0
+
+    y0, y1, fy = axis(H)
+    x0, x1, fx = axis(W)
+    top = x[:, :, y0][:, :, :, x0] * (1 - fx) + x[:, :, y0][:, :, :, x1] * fx
+    bot = x[:, :, y1][:, :, :, x0] * (1 - fx) + x[:, :, y1][:, :, :, x1] * fx
+    return top * (1 - fy)[:, None] + bot * fy[:, None]
+
+
+def im2col(x):
+    """[B,C,H,W] -> patches [B, Ho, Wo, C, 3, 3] of the stride-2 pad-1 3x3 conv"""
+    B, C, H, W = x.shape
+    Ho, Wo = H // 2, W // 2
+    xp = np.zeros((B, C, H + 2, W + 2))
+    xp[:, :, 1:-1, 1:-1] = x
+    cols = np.empty((B, Ho, Wo, C, 3, 3))
+    for ky in range(3):
+        for kx in range(3):
+            cols[..., ky, kx] = xp[:, :, ky:ky + 2 * Ho:2, kx:kx + 2 * Wo:2].transpose(0, 2, 3, 1)
+    return cols
+
+
+def conv(x, w, b):
+    """3x3, stride 2, padding 1: out[b,o,i,j] = b[o] + sum_{c,ky,kx} w[o,c,ky,kx] x[b,c,2i-1+ky,2j-1+kx]"""
+    cols = im2col(x)
+    out = np.tensordot(cols, w, axes=([3, 4, 5], [1, 2, 3]))  # [B,Ho,Wo,Cout]
+    return out.transpose(0, 3, 1, 2) + b[None, :, None, None]
+
+
+def conv_backward(x, w, dout):
+    cols = im2col(x)
+    dw = np.tensordot(dout.transpose(1, 0, 2, 3), cols, axes=([1, 2, 3], [0, 1, 2]))
+    db = dout.sum(axis=(0, 2, 3))
+    dcols = np.tensordot(dout.transpose(0, 2, 3, 1), w, axes=([3], [0]))  # [B,Ho,Wo,C,3,3]
+    B, C, H, W = x.shape
+    Ho, Wo = H // 2, W // 2
+    dxp = np.zeros((B, C, H + 2, W + 2))
+    for ky in range(3):
+        for kx in range(3):
+            dxp[:, :, ky:ky + 2 * Ho:2, kx:kx + 2 * Wo:2] += dcols[..., ky, kx].transpose(0, 3, 1, 2)
+    return dxp[:, :, 1:-1, 1:-1], dw, db
+
+
+def lrelu(z):
+    return np.where(z > 0, z, SLOPE * z)
+
+
+def inorm(a, g, b):
+    mu = a.mean(axis=(2, 3), keepdims=True)
+    var = a.var(axis=(2, 3), keepdims=True)
+    xh = (a - mu) / np.sqrt(var + EPS)
+    return xh * g[None, :, None, None] + b[None, :, None, None], (xh, var)
+
+
+def inorm_backward(dy, g, cache):
+    xh, var = cache
+    n = xh.shape[2] * xh.shape[3]
+    dg = (dy * xh).sum(axis=(0, 2, 3))
+    db = dy.sum(axis=(0, 2, 3))
+    dxh = dy * g[None, :, None, None]
+    da = (dxh - dxh.mean(axis=(2, 3), keepdims=True)
+          - xh * (dxh * xh).mean(axis=(2, 3), keepdims=True)) / np.sqrt(var + EPS)
+    assert n > 0
+    return da, dg, db
+
+
+def avgpool4(a):
+    B, C, H, W = a.shape
+    return a.reshape(B, C, H // 4, 4, W // 4, 4).mean(axis=(3, 5))
+
+
+# ---------------------------------------------------------------- model
+
+def heads_to_params(outs, K):
+    """split the four head outputs [B, n] into svdlut parameter arrays"""
+    hs, hsw, ht, htw = outs
+    B = hs.shape[0]
+    g = hs.reshape(B, K, 3, DS, DS)
+    nu = 9 * DT * NS
+    return dict(U=ht[:, :nu].reshape(B, 3, 3, DT, NS), S=ht[:, nu:nu + 9 * NS].reshape(B, 3, 3, NS),
+                V=ht[:, nu + 9 * NS:].reshape(B, 3, 3, DT, NS), lut_w=htw.reshape(B, 3, 4),
+                g_xy=np.ascontiguousarray(g[:, :, 0]), g_xc=np.ascontiguousarray(g[:, :, 1]),
+                g_yc=np.ascontiguousarray(g[:, :, 2]), grid_w=hsw.reshape(B, K, 4))
+
+
+def params_to_heads(d, K):
+    """inverse of heads_to_params for gradients"""
+    B = d["U"].shape[0]
+    g = np.stack([d["g_xy"], d["g_xc"], d["g_yc"]], axis=2).reshape(B, -1)
+    ht = np.concatenate([d["U"].reshape(B, -1), d["S"].reshape(B, -1), d["V"].reshape(B, -1)], axis=1)
+    return [g, d["grid_w"].reshape(B, -1), ht, d["lut_w"].reshape(B, -1)]
+
+
+def forward(blob, x, K, drop_mask=None, thumb=None):
+    """x: [B,3,H,W] in [0,1].  drop_mask: None (inference) or [B,64,8,8] of
+    {0, 2} (keep-and-scale mask of Dropout(0.5)).  thumb: optional
+    precomputed [B,3,256,256] thumbnail.  Returns (params dict, cache)."""
+    p = unpack(blob, K)
+    a = downsample(np.asarray(x, dtype=np.float64)) if thumb is None else np.asarray(thumb, dtype=np.float64)
+    cache = {"acts": []}
+    for i in range(5):
+        xin = a
+        z = conv(xin, p[f"conv{i}.w"], p[f"conv{i}.b"])
+        r = lrelu(z)
+        if i < 4:
+            a, nc = inorm(r, p[f"in{i}.g"], p[f"in{i}.b"])
+        else:
+            a, nc = r, None
+        cache["acts"].append((xin, z, nc))
+    if drop_mask is not None:
+        a = a * drop_mask
+    pooled = avgpool4(a)
+    rho = pooled.reshape(pooled.shape[0], -1)
+    hidden, outs = [], []
+    for h in ("s", "sw", "t", "tw"):
+        t = rho @ p[f"h{h}.w1"].T + p[f"h{h}.b1"]
+        hidden.append(t)
+        outs.append(t @ p[f"h{h}.w2"].T + p[f"h{h}.b2"])
+    cache.update(rho=rho, hidden=hidden, drop_mask=drop_mask, feat_shape=a.shape)
+    return heads_to_params(outs, K), cache
+
+
+def backward(blob, K, cache, dparams):
+    """gradient of sum(dparams * params) w.r.t. the parameter blob"""
+    p = unpack(blob, K)
+    g = {}
+    douts = params_to_heads(dparams, K)
+    rho = cache["rho"]
+    drho = np.zeros_like(rho)
+    for h, do, t in zip(("s", "sw", "t", "tw"), douts, cache["hidden"]):
+        g[f"h{h}.w2"] = do.T @ t
+        g[f"h{h}.b2"] = do.sum(axis=0)
+        dt = do @ p[f"h{h}.w2"]
+        g[f"h{h}.w1"] = dt.T @ rho
+        g[f"h{h}.b1"] = dt.sum(axis=0)
+        drho += dt @ p[f"h{h}.w1"]
+    B, C, H, W = cache["feat_shape"]
+    da = np.repeat(np.repeat(drho.reshape(B, C, H // 4, W // 4), 4, axis=2), 4, axis=3) / 16.0
+    if cache["drop_mask"] is not None:
+        da = da * cache["drop_mask"]
+    for i in reversed(range(5)):
+        xin, z, nc = cache["acts"][i]
+        if i < 4:
+            dr, g[f"in{i}.g"], g[f"in{i}.b"] = inorm_backward(da, p[f"in{i}.g"], nc)
+        else:
+            dr = da
+        dz = dr * np.where(z > 0, 1.0, SLOPE)
+        da, g[f"conv{i}.w"], g[f"conv{i}.b"] = conv_backward(xin, p[f"conv{i}.w"], dz)
+    return pack(g, K)
+
+
+def identity_blob(K, rng=None, scale=0.0):
+    """Parameters whose output is the identity transform (final FC weights
+    zero, final biases = identity factors, all grid terms off); with scale > 0
+    the final FC weights are drawn N(0, scale) instead of zero (a seeded,
+    image-dependent perturbation of the identity).  Other weights: He-style
+    normal initialisation from rng (IN scale 1, shift 0)."""
+    import svdlut_inputs as si
+    rng = rng if rng is not None else np.random.default_rng(0)
+    p = {}
+    for n, s in param_layout(K):
+        if n.startswith("conv") and n.endswith(".w"):
+            fan_in = s[1] * 9
+            p[n] = rng.normal(0.0, np.sqrt(2.0 / fan_in), size=s)
+        elif n.startswith("in") and n.endswith(".g"):
+            p[n] = np.ones(s)
+        elif n.endswith(".w1"):
+            p[n] = rng.normal(0.0, np.sqrt(1.0 / s[1]), size=s)
+        elif n.endswith(".w2"):
+            p[n] = rng.normal(0.0, scale, size=s) if scale > 0 else np.zeros(s)
+        else:
+            p[n] = np.zeros(s)
+    ident = si.identity_params(si.Dims(DT, NS, K, DS, DS, DS))
+    p["ht.b2"] = np.concatenate([ident["U"].ravel(), ident["S"].ravel(), ident["V"].ravel()])
+    p["htw.b2"] = ident["lut_w"].ravel()
+    return pack(p, K)

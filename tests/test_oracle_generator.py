@@ -1,0 +1,124 @@
+"""Pins of the FP64 generator oracle (oracle/generator.py).
+
+The paper prints no activations of its generator; what it fixes is the
+architecture (Supp. Tables 1-5) and its parameter counts (Table 7 and the
+dimension ablation), checked here against tests/golden/param_counts.txt.
+The layers are pinned against brute force and their defining invariants,
+the hand-written backward against central differences of the forward.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import generator as G
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "param_counts.txt")
+
+
+def golden():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def head_params(K):
+    return [G.HIDDEN * 256 + G.HIDDEN + n * G.HIDDEN + n for n in G.head_sizes(K)]
+
+
+def test_param_count_matches_table_7():
+    g = golden()
+    K = 6
+    total = G.param_count(K)
+    assert total == g["ours"]
+    hs, hsw, ht, htw = head_params(K)
+    fusion = (K + 3) * 3 + 3  # the (K+3) -> 3 1x1 conv of Eq. 6
+    assert total - hs - hsw == g["only_lut"]
+    assert total - ht - htw + fusion == g["only_grid"]
+    assert total + fusion == g["conv1x1"]
+    # no SVD: H_t emits the nine dense 33x33 tables instead of U, S, V
+    dense = total + (G.HIDDEN + 1) * (9 * 33 * 33 - G.head_sizes(K)[2])
+    assert round(dense / 1000, 1) == g["dense_2d_lut_thousands"]
+
+
+def test_downsample_reproduces_ramps_and_constants():
+    H, W = 300, 517
+    yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    x = np.stack([0.3 + 0 * xx, 0.001 * xx, 0.002 * yy])[None].astype(np.float64)
+    t = G.downsample(x)
+    src_x = (np.arange(256) + 0.5) * (W / 256) - 0.5
+    src_y = (np.arange(256) + 0.5) * (H / 256) - 0.5
+    assert np.abs(t[0, 0] - 0.3).max() <= 1e-15
+    assert np.abs(t[0, 1] - 0.001 * np.clip(src_x, 0, W - 1)[None, :]).max() <= 1e-12
+    assert np.abs(t[0, 2] - 0.002 * np.clip(src_y, 0, H - 1)[:, None]).max() <= 1e-12
+
+
+def test_conv_matches_brute_force():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(2, 3, 6, 8))
+    w = rng.normal(size=(4, 3, 3, 3))
+    b = rng.normal(size=4)
+    out = G.conv(x, w, b)
+    ref = np.zeros((2, 4, 3, 4))
+    for n in range(2):
+        for o in range(4):
+            for i in range(3):
+                for j in range(4):
+                    s = b[o]
+                    for c in range(3):
+                        for ky in range(3):
+                            for kx in range(3):
+                                yy, xx = 2 * i - 1 + ky, 2 * j - 1 + kx
+                                if 0 <= yy < 6 and 0 <= xx < 8:
+                                    s += w[o, c, ky, kx] * x[n, c, yy, xx]
+                    ref[n, o, i, j] = s
+    assert np.abs(out - ref).max() <= 1e-12
+
+
+def test_instance_norm_and_pool_invariants():
+    rng = np.random.default_rng(1)
+    a = rng.normal(3.0, 2.0, size=(2, 5, 8, 8))
+    y, _ = G.inorm(a, np.ones(5), np.zeros(5))
+    assert np.abs(y.mean(axis=(2, 3))).max() <= 1e-12
+    assert np.abs(y.var(axis=(2, 3)) - 1.0).max() <= 1e-4  # eps = 1e-5 vs var ~ 4
+    p = G.avgpool4(a)
+    assert p.shape == (2, 5, 2, 2)
+    assert abs(p[1, 2, 1, 0] - a[1, 2, 4:8, 0:4].mean()) <= 1e-15
+
+
+def test_identity_blob_outputs_identity_factors():
+    import oracle
+    import svdlut_inputs as si
+    K = 8
+    blob = G.identity_blob(K, np.random.default_rng(2))
+    x = si.make_image(np.random.default_rng(3), 64, 96)[None]
+    params, _ = G.forward(blob, x, K)
+    d = si.Dims(33, 8, K, 17, 17, 17)
+    y = oracle.forward(d, {k: v for k, v in params.items()}, x)
+    assert np.abs(y - x).max() <= 1e-12
+
+
+@pytest.mark.parametrize("with_dropout", [False, True])
+def test_backward_matches_central_differences(with_dropout):
+    K = 3
+    rng = np.random.default_rng(4)
+    blob = G.identity_blob(K, rng, scale=0.05)
+    blob = blob + rng.normal(0, 0.01, size=blob.shape)
+    thumb = rng.uniform(0, 1, size=(2, 3, 256, 256))
+    mask = (rng.uniform(size=(2, 64, 8, 8)) < 0.5) * 2.0 if with_dropout else None
+    params, cache = G.forward(blob, None, K, drop_mask=mask, thumb=thumb)
+    dparams = {k: rng.normal(size=v.shape) for k, v in params.items()}
+    g = G.backward(blob, K, cache, dparams)
+    # small step: a LeakyReLU kink crossed inside +-h would bias the difference
+    h = 1e-8
+    for _ in range(3):
+        dirn = rng.normal(size=blob.shape)
+        fp, _ = G.forward(blob + h * dirn, None, K, drop_mask=mask, thumb=thumb)
+        fm, _ = G.forward(blob - h * dirn, None, K, drop_mask=mask, thumb=thumb)
+        fd = sum(((fp[k] - fm[k]) * dparams[k]).sum() for k in fp) / (2 * h)
+        an = float(g @ dirn)
+        assert abs(fd - an) <= 1e-5 * max(1.0, abs(fd)), (fd, an)
