@@ -178,6 +178,73 @@ svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_params *para
 size_t svdlut_backward_workspace_size(const svdlut_dims *dims, int B, int H, int W);
 
 /*
+ * ---- learned factor generator (Supp. Sec. A, Tables 1-5) ----
+ * A 256x256 bilinear thumbnail of the input goes through five 3x3 stride-2
+ * convolutions (3->8->16->32->64->64 channels; LeakyReLU 0.2, then affine
+ * InstanceNorm on the first four), Dropout(0.5) while training, average
+ * pooling to 64x2x2 = 256 features and four heads of two FC layers (256->8->n):
+ * the 2D bilateral grids (K x 3 planes of 17x17), their weights (K x 4), the
+ * SVD factors of the nine 2D LUTs (D_t = 33, rank 8: U, S, V) and the LUT
+ * weights (3 x 4).  Its outputs are the svdlut_params of svdlut_apply with
+ * dims {33, 8, K, 17, 17, 17}.  Convolutions run on BF16 tensor cores with
+ * FP32 accumulation; all other arithmetic is FP32.
+ *
+ * Weights: one FP32 device array of svdlut_generator_param_count(K) floats,
+ * in this order: for conv i = 0..4: w [Cout][Cin][3][3], b [Cout], and for
+ * i < 4 the InstanceNorm scale [Cout] and shift [Cout]; then for the heads
+ * grids, grid weights, LUT factors, LUT weights: w1 [8][256], b1 [8],
+ * w2 [n][8], b2 [n] with n = K*3*17*17, K*4, 9*(33*8+8+33*8), 12.  The factor
+ * head's outputs are U ([3][3][33][8]), then S ([3][3][8]), then V; the grid
+ * head's are [K][plane xy, xc, yc][17][17].  At K = 6 there are 160,478
+ * parameters (the paper's Table 7).
+ */
+
+/* Writable parameter buffers (layouts of svdlut_params, leading batch axis). */
+typedef struct {
+    float *U, *S, *V, *lut_w, *g_xy, *g_xc, *g_yc, *grid_w;
+} svdlut_param_buffers;
+
+/* Number of FP32 weights of the generator with K grids (0 if K is out of range). */
+size_t svdlut_generator_param_count(int K);
+
+/* Workspace bytes for a batch of B images (activations kept for backward). */
+size_t svdlut_generator_workspace_size(int K, int B);
+
+/*
+ * svdlut_generator_forward -- predicts the transform parameters of B images.
+ * x: [B][3][H][W] FP32 device, any H, W >= 1 (bilinearly resized to 256x256).
+ * training != 0 applies Dropout(0.5) with a mask drawn from SplitMix64 counters
+ * (element e of [B][64][8][8] kept when the top bit of splitmix64(seed*2^32+e)
+ * is 0).  ws (256-byte aligned, svdlut_generator_workspace_size bytes) keeps
+ * the activations for svdlut_generator_backward.
+ */
+svdlut_status svdlut_generator_forward(int K, const float *weights, int B, int H, int W, const float *x,
+                                       const svdlut_param_buffers *out, int training, uint64_t seed,
+                                       void *ws, size_t ws_bytes, svdlut_stream_t stream);
+
+/*
+ * svdlut_generator_backward -- gradient of sum(dparams * params) with
+ * respect to the weights (dweights, overwritten), using the activations the
+ * last svdlut_generator_forward left in ws (same K, B, training and seed).
+ * Deterministic (fixed-order reductions, no atomics).
+ */
+svdlut_status svdlut_generator_backward(int K, const float *weights, int B, const svdlut_params *dparams,
+                                        float *dweights, int training, uint64_t seed, void *ws,
+                                        size_t ws_bytes, svdlut_stream_t stream);
+
+/* One Adam step on n FP32 weights (Sec. 4.2 trains with Adam): m, v are the
+ * moment buffers, step >= 1 is the 1-based step count (bias correction). */
+svdlut_status svdlut_generator_adam(float *weights, const float *grads, float *m, float *v, size_t n,
+                                    float lr, float beta1, float beta2, float eps, int step,
+                                    svdlut_stream_t stream);
+
+/* MSE loss (Sec. 3.3, the first term of the training loss): *loss =
+ * mean((y - target)^2) over n floats and, if dy is not NULL, dy = 2 (y -
+ * target) / n.  ws: at least 4096 bytes of device scratch.  Deterministic. */
+svdlut_status svdlut_mse(const float *y, const float *target, size_t n, float *dy, float *loss, void *ws,
+                         size_t ws_bytes, svdlut_stream_t stream);
+
+/*
  * svdlut_backward_noalloc -- svdlut_backward for callers that cannot allocate
  * device memory.  The paper has no counterpart; this is a library service.
  *

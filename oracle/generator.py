@@ -133,6 +133,15 @@ def conv_backward(x, w, dout):
     return dxp[:, :, 1:-1, 1:-1], dw, db
 
 
+def bf16_round(a):
+    """Round to bfloat16 (1 sign, 8 exponent, 7 stored mantissa bits), nearest
+    even, returned as float64.  Used only to take the LeakyReLU sign decisions
+    in the precision the GPU convolution multiplies in."""
+    b = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def lrelu(z):
     return np.where(z > 0, z, SLOPE * z)
 
@@ -183,16 +192,23 @@ def params_to_heads(d, K):
     return [g, d["grid_w"].reshape(B, -1), ht, d["lut_w"].reshape(B, -1)]
 
 
-def forward(blob, x, K, drop_mask=None, thumb=None):
+def forward(blob, x, K, drop_mask=None, thumb=None, conv_operands="fp64"):
     """x: [B,3,H,W] in [0,1].  drop_mask: None (inference) or [B,64,8,8] of
     {0, 2} (keep-and-scale mask of Dropout(0.5)).  thumb: optional
-    precomputed [B,3,256,256] thumbnail.  Returns (params dict, cache)."""
+    precomputed [B,3,256,256] thumbnail.  conv_operands="bf16" multiplies the
+    convolution's inputs and weights rounded to bfloat16 (accumulating in
+    float64), the precision of the tensor-core convolution; the backward
+    pass always uses the exact activations and weights.  Returns (params
+    dict, cache)."""
     p = unpack(blob, K)
     a = downsample(np.asarray(x, dtype=np.float64)) if thumb is None else np.asarray(thumb, dtype=np.float64)
     cache = {"acts": []}
     for i in range(5):
         xin = a
-        z = conv(xin, p[f"conv{i}.w"], p[f"conv{i}.b"])
+        if conv_operands == "bf16":
+            z = conv(bf16_round(xin), bf16_round(p[f"conv{i}.w"]), p[f"conv{i}.b"])
+        else:
+            z = conv(xin, p[f"conv{i}.w"], p[f"conv{i}.b"])
         r = lrelu(z)
         if i < 4:
             a, nc = inorm(r, p[f"in{i}.g"], p[f"in{i}.b"])
@@ -239,6 +255,27 @@ def backward(blob, K, cache, dparams):
         dz = dr * np.where(z > 0, 1.0, SLOPE)
         da, g[f"conv{i}.w"], g[f"conv{i}.b"] = conv_backward(xin, p[f"conv{i}.w"], dz)
     return pack(g, K)
+
+
+def splitmix64(x):
+    """SplitMix64 finaliser (Steele, Lea, Flood 2014; constants as published
+    with Java's SplittableRandom): uint64 -> uint64."""
+    x = np.asarray(x, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = x + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def dropout_mask(seed, B, shape=(64, 8, 8)):
+    """Dropout(0.5) keep-and-scale mask drawn from a counter-based generator:
+    element e (flat index over [B][64][8][8]) is kept (value 2) when the top
+    bit of splitmix64(seed * 2^32 + e) is 0, else dropped (value 0)."""
+    n = B * int(np.prod(shape))
+    idx = (np.uint64(seed) << np.uint64(32)) + np.arange(n, dtype=np.uint64)
+    keep = (splitmix64(idx) >> np.uint64(63)) == 0
+    return (keep * 2.0).reshape((B,) + tuple(shape))
 
 
 def identity_blob(K, rng=None, scale=0.0):

@@ -229,3 +229,92 @@ class Batch:
 def apply_batched(xs, params_list, outs=None, stream=None):
     """One persistent launch over images of uneven sizes (svdlut_apply_batched)."""
     return Batch(xs, params_list, outs).run(stream)
+
+
+GEN_DT, GEN_RANK, GEN_DS = 33, 8, 17
+
+
+class Generator:
+    """The learned factor generator (svdlut_generator_* in the C ABI).
+
+    weights: FP32 CUDA tensor of svdlut_generator_param_count(K) values (the
+    layout documented in include/svdlut.h).  forward() returns the parameter
+    dict svdlut.apply consumes (leading batch axis), backward() the weight
+    gradient of sum(dparams * params) for the last forward."""
+
+    def __init__(self, K, weights, max_batch=64):
+        torch = _torch()
+        lib = _lib.load()
+        self.K = int(K)
+        self.n = int(lib.svdlut_generator_param_count(self.K))
+        if weights.numel() != self.n or weights.dtype != torch.float32 or not weights.is_cuda:
+            raise ValueError(f"weights must be {self.n} float32 values on the GPU")
+        self.weights = weights.contiguous()
+        self.max_batch = int(max_batch)
+        self.ws = torch.empty(int(lib.svdlut_generator_workspace_size(self.K, self.max_batch)), dtype=torch.uint8,
+                              device=weights.device)
+        self.last = None
+
+    def dims(self):
+        return _lib.Dims(GEN_DT, GEN_RANK, self.K, GEN_DS, GEN_DS, GEN_DS)
+
+    def empty_params(self, B):
+        torch = _torch()
+        dev = self.weights.device
+        K, D, R, S = self.K, GEN_DT, GEN_RANK, GEN_DS
+        shapes = {"U": (B, 3, 3, D, R), "S": (B, 3, 3, R), "V": (B, 3, 3, D, R), "lut_w": (B, 3, 4),
+                  "g_xy": (B, K, S, S), "g_xc": (B, K, S, S), "g_yc": (B, K, S, S), "grid_w": (B, K, 4)}
+        return {k: torch.empty(v, dtype=torch.float32, device=dev) for k, v in shapes.items()}
+
+    @staticmethod
+    def _ptrs(d):
+        return _lib.Params(**{k: (d[k].data_ptr() if d[k].numel() else None) for k in PARAM_NAMES})
+
+    def forward(self, x, training=False, seed=0, out=None, stream=None):
+        B, C, H, W = x.shape
+        if C != 3 or B > self.max_batch or x.dtype != _torch().float32 or not x.is_contiguous():
+            raise ValueError("x must be a contiguous float32 [B,3,H,W] with B <= max_batch")
+        out = out if out is not None else self.empty_params(B)
+        lib = _lib.load()
+        _lib.check(lib.svdlut_generator_forward(self.K, ctypes.c_void_p(self.weights.data_ptr()), B, H, W,
+                                                ctypes.c_void_p(x.data_ptr()), ctypes.byref(self._ptrs(out)),
+                                                int(bool(training)), ctypes.c_uint64(seed),
+                                                ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                                _stream_ptr(stream)))
+        self.last = (B, int(bool(training)), int(seed))
+        return out
+
+    def backward(self, dparams, dweights=None, stream=None):
+        torch = _torch()
+        if self.last is None:
+            raise RuntimeError("backward needs a forward first")
+        B, training, seed = self.last
+        dw = dweights if dweights is not None else torch.empty_like(self.weights)
+        lib = _lib.load()
+        _lib.check(lib.svdlut_generator_backward(self.K, ctypes.c_void_p(self.weights.data_ptr()), B,
+                                                 ctypes.byref(self._ptrs(dparams)), ctypes.c_void_p(dw.data_ptr()),
+                                                 training, ctypes.c_uint64(seed),
+                                                 ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                                 _stream_ptr(stream)))
+        return dw
+
+
+def adam_step(weights, grads, m, v, step, lr=1e-4, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One Adam step on FP32 CUDA tensors (svdlut_generator_adam)."""
+    lib = _lib.load()
+    _lib.check(lib.svdlut_generator_adam(ctypes.c_void_p(weights.data_ptr()), ctypes.c_void_p(grads.data_ptr()),
+                                         ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()), weights.numel(),
+                                         lr, beta1, beta2, eps, int(step), _stream_ptr(stream)))
+
+
+def mse(y, target, dy=None, ws=None, stream=None):
+    """MSE loss (0-d CUDA tensor) and, into dy if given, its gradient."""
+    torch = _torch()
+    loss = torch.empty((), dtype=torch.float32, device=y.device)
+    ws = ws if ws is not None else torch.empty(4096, dtype=torch.uint8, device=y.device)
+    lib = _lib.load()
+    _lib.check(lib.svdlut_mse(ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(target.data_ptr()), y.numel(),
+                              ctypes.c_void_p(dy.data_ptr()) if dy is not None else None,
+                              ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                              _stream_ptr(stream)))
+    return loss

@@ -88,6 +88,21 @@ def _declare(lib):
     lib.svdlut_autotune_batched.argtypes = [P(Image), c_int, c_int, c_void_p, c_size_t, c_void_p, c_int,
                                             P(LaunchCfg), ctypes.POINTER(ctypes.c_float)]
     lib.svdlut_autotune_batched.restype = c_int
+    lib.svdlut_generator_param_count.argtypes = [c_int]
+    lib.svdlut_generator_param_count.restype = c_size_t
+    lib.svdlut_generator_workspace_size.argtypes = [c_int, c_int]
+    lib.svdlut_generator_workspace_size.restype = c_size_t
+    lib.svdlut_generator_forward.argtypes = [c_int, c_void_p, c_int, c_int, c_int, c_void_p, P(Params), c_int,
+                                             ctypes.c_uint64, c_void_p, c_size_t, c_void_p]
+    lib.svdlut_generator_forward.restype = c_int
+    lib.svdlut_generator_backward.argtypes = [c_int, c_void_p, c_int, P(Params), c_void_p, c_int, ctypes.c_uint64,
+                                              c_void_p, c_size_t, c_void_p]
+    lib.svdlut_generator_backward.restype = c_int
+    lib.svdlut_generator_adam.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, ctypes.c_float,
+                                          ctypes.c_float, ctypes.c_float, ctypes.c_float, c_int, c_void_p]
+    lib.svdlut_generator_adam.restype = c_int
+    lib.svdlut_mse.argtypes = [c_void_p, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+    lib.svdlut_mse.restype = c_int
     lib.svdlut_backward_noalloc.argtypes = [P(Dims), P(Params), c_int, c_int, c_int, c_void_p, c_void_p,
                                             c_void_p, P(Grads), c_void_p]
     lib.svdlut_backward_noalloc.restype = c_int
@@ -108,5 +123,6 @@ def check(status: int):
 
 # names every build of the library exports (declared in include/svdlut.h)
 EXPORTED = ["svdlut_apply", "svdlut_apply_batched", "svdlut_batched_workspace_size", "svdlut_autotune_batched",
-            "svdlut_backward", "svdlut_backward_workspace_size", "svdlut_backward_noalloc",
+            "svdlut_generator_param_count", "svdlut_generator_workspace_size", "svdlut_generator_forward",
+            "svdlut_generator_backward", "svdlut_generator_adam", "svdlut_mse", "svdlut_backward", "svdlut_backward_workspace_size", "svdlut_backward_noalloc",
             "svdlut_last_error", "svdlut_version"]

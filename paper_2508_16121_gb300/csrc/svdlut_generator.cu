@@ -1,0 +1,856 @@
+// The learned factor generator (Supp. Sec. A, Tables 1-5) on sm_103a: a
+// bilinear 256x256 thumbnail, five 3x3 stride-2 convolutions (BF16 tensor-core
+// implicit GEMMs, FP32 accumulation) with LeakyReLU and InstanceNorm, average
+// pooling to a 256-d context and four two-layer FC heads that emit the SVD
+// factors, LUT weights, 2D bilateral grids and grid weights in the layouts
+// svdlut_apply reads.  Forward, backward and an Adam step; every reduction is
+// done in a fixed order (no atomics), so training is bitwise repeatable.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "svdlut_internal.cuh"
+
+namespace svdlut {
+namespace gen {
+
+constexpr int kCh[6] = {3, 8, 16, 32, 64, 64};
+constexpr int kSz[6] = {256, 128, 64, 32, 16, 8};  // spatial size of the input of conv i / output of conv i-1
+constexpr int kThumb = 256;
+constexpr float kSlope = 0.2f;
+constexpr float kEps = 1e-5f;
+constexpr int kDT = 33, kNS = 8, kDS = 17, kHidden = 8, kRho = 256;
+
+struct Layout {
+    size_t conv_w[5], conv_b[5], in_g[4], in_b[4];
+    size_t w1[4], b1[4], w2[4], b2[4];
+    int head_n[4];
+    size_t total;
+};
+
+__host__ __device__ inline int head_n(int K, int h)
+{
+    return h == 0 ? K * 3 * kDS * kDS : (h == 1 ? K * 4 : (h == 2 ? 9 * (kDT * kNS + kNS + kDT * kNS) : 12));
+}
+
+inline Layout make_layout(int K)
+{
+    Layout L{};
+    size_t o = 0;
+    for (int i = 0; i < 5; ++i) {
+        L.conv_w[i] = o;
+        o += static_cast<size_t>(kCh[i + 1]) * kCh[i] * 9;
+        L.conv_b[i] = o;
+        o += kCh[i + 1];
+        if (i < 4) {
+            L.in_g[i] = o;
+            o += kCh[i + 1];
+            L.in_b[i] = o;
+            o += kCh[i + 1];
+        }
+    }
+    for (int h = 0; h < 4; ++h) {
+        L.head_n[h] = head_n(K, h);
+        L.w1[h] = o;
+        o += static_cast<size_t>(kHidden) * kRho;
+        L.b1[h] = o;
+        o += kHidden;
+        L.w2[h] = o;
+        o += static_cast<size_t>(L.head_n[h]) * kHidden;
+        L.b2[h] = o;
+        o += L.head_n[h];
+    }
+    L.total = o;
+    return L;
+}
+
+// Workspace (floats): forward activations kept for the backward pass, then
+// backward temporaries.
+struct WsLayout {
+    size_t thumb, r[5], a[4], mean[4], rstd[4], rho, hidden;
+    size_t dz[2], dact, wpart, dhid, drho, insum;
+    size_t total;
+};
+
+constexpr int kWChunk = 4096;  // pixels per weight-gradient partial
+
+inline size_t act_size(int B, int i) { return static_cast<size_t>(B) * kCh[i + 1] * kSz[i + 1] * kSz[i + 1]; }
+
+inline WsLayout make_ws(int B)
+{
+    WsLayout w{};
+    size_t o = 0;
+    auto take = [&](size_t n) {
+        const size_t at = o;
+        o += (n + 63) & ~static_cast<size_t>(63);
+        return at;
+    };
+    w.thumb = take(static_cast<size_t>(B) * 3 * kThumb * kThumb);
+    for (int i = 0; i < 5; ++i) w.r[i] = take(act_size(B, i));
+    for (int i = 0; i < 4; ++i) {
+        w.a[i] = take(act_size(B, i));
+        w.mean[i] = take(static_cast<size_t>(B) * kCh[i + 1]);
+        w.rstd[i] = take(static_cast<size_t>(B) * kCh[i + 1]);
+    }
+    w.rho = take(static_cast<size_t>(B) * kRho);
+    w.hidden = take(static_cast<size_t>(B) * 4 * kHidden);
+    const size_t amax = act_size(B, 0);
+    w.dz[0] = take(amax);
+    w.dz[1] = take(amax);
+    w.dact = take(amax);
+    size_t wp = 0;
+    for (int i = 0; i < 5; ++i) {
+        const size_t pix = static_cast<size_t>(B) * kSz[i + 1] * kSz[i + 1];
+        const size_t chunks = (pix + kWChunk - 1) / kWChunk;
+        wp = std::max(wp, chunks * kCh[i + 1] * kCh[i] * 9);
+    }
+    w.wpart = take(wp);
+    w.dhid = take(static_cast<size_t>(B) * 4 * kHidden);
+    w.drho = take(static_cast<size_t>(B) * kRho);
+    w.insum = take(static_cast<size_t>(B) * 64 * 2);
+    w.total = o;
+    return w;
+}
+
+// ---------------------------------------------------------------- kernels
+
+// Bilinear downsample to 256x256 with half-pixel centres, no antialiasing.
+__global__ void downsample_kernel(const float *__restrict__ x, int B, int H, int W, float *__restrict__ t)
+{
+    const size_t n = static_cast<size_t>(B) * 3 * kThumb * kThumb;
+    const float sy_ = static_cast<float>(H) / kThumb, sx_ = static_cast<float>(W) / kThumb;
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int ox = static_cast<int>(e % kThumb), oy = static_cast<int>((e / kThumb) % kThumb);
+        const size_t bc = e / (kThumb * kThumb);
+        float sy = fminf(fmaxf((oy + 0.5f) * sy_ - 0.5f, 0.f), static_cast<float>(H - 1));
+        float sx = fminf(fmaxf((ox + 0.5f) * sx_ - 0.5f, 0.f), static_cast<float>(W - 1));
+        const int y0 = static_cast<int>(sy), x0 = static_cast<int>(sx);
+        const int y1 = min(y0 + 1, H - 1), x1 = min(x0 + 1, W - 1);
+        const float fy = sy - y0, fx = sx - x0;
+        const float *p = x + bc * H * W;
+        const float top = (1.f - fx) * __ldg(p + static_cast<size_t>(y0) * W + x0) + fx * __ldg(p + static_cast<size_t>(y0) * W + x1);
+        const float bot = (1.f - fx) * __ldg(p + static_cast<size_t>(y1) * W + x0) + fx * __ldg(p + static_cast<size_t>(y1) * W + x1);
+        t[e] = (1.f - fy) * top + fy * bot;
+    }
+}
+
+// ---- BF16 tensor-core GEMM:  C[m][n] = sum_k A(m, k) B(k, n) ----
+// 64 x 64 tile per CTA, 4 warps of 32 x 32, K staged 32 at a time in shared
+// memory as BF16 (rows padded to 40 elements: conflict-free fragment loads),
+// mma.sync m16n8k16 with FP32 accumulators.  A and B are gather functors
+// (im2col and friends); the epilogue functor stores C.  blockIdx.z selects a
+// reduction chunk (the functors map (k, z) to their global index).
+constexpr int kGT = 128;
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// SPLIT = false: operands rounded to BF16 (forward).  SPLIT = true: each FP32
+// operand is carried as hi + lo BF16 parts and the product is accumulated as
+// hi*hi + hi*lo + lo*hi (three MMAs, ~16 mantissa bits): the backward passes
+// sum long chains of cancelling terms, where plain BF16 loses too much.
+template <bool SPLIT, class AL, class BL, class EP>
+__global__ void __launch_bounds__(kGT) mma_gemm_kernel(int M, int N, int Kd, AL al, BL bl, EP ep)
+{
+    constexpr int NP = SPLIT ? 2 : 1;
+    __shared__ __align__(16) __nv_bfloat16 As[NP][64][40];
+    __shared__ __align__(16) __nv_bfloat16 Bs[NP][64][40];
+    const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64, z = blockIdx.z;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    for (int k0 = 0; k0 < Kd; k0 += 32) {
+        for (int e = tid; e < 64 * 32; e += kGT) {
+            const int r = e >> 5, c = e & 31, k = k0 + c;
+            const int m = m0 + r, n = n0 + r;
+            const float va = (m < M && k < Kd) ? al(m, k, z) : 0.f;
+            const float vb = (n < N && k < Kd) ? bl(k, n, z) : 0.f;
+            const __nv_bfloat16 ha = __float2bfloat16_rn(va), hb = __float2bfloat16_rn(vb);
+            As[0][r][c] = ha;
+            Bs[0][r][c] = hb;
+            if (SPLIT) {
+                As[NP - 1][r][c] = __float2bfloat16_rn(va - __bfloat162float(ha));
+                Bs[NP - 1][r][c] = __float2bfloat16_rn(vb - __bfloat162float(hb));
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 32; kk += 16) {
+            uint32_t a[NP][2][4], b[NP][4][2];
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp) {
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi) {
+                    const int r = wm + mi * 16 + g;
+                    a[pp][mi][0] = *reinterpret_cast<const uint32_t *>(&As[pp][r][kk + 2 * t]);
+                    a[pp][mi][1] = *reinterpret_cast<const uint32_t *>(&As[pp][r + 8][kk + 2 * t]);
+                    a[pp][mi][2] = *reinterpret_cast<const uint32_t *>(&As[pp][r][kk + 8 + 2 * t]);
+                    a[pp][mi][3] = *reinterpret_cast<const uint32_t *>(&As[pp][r + 8][kk + 8 + 2 * t]);
+                }
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) {
+                    const int n = wn + ni * 8 + g;
+                    b[pp][ni][0] = *reinterpret_cast<const uint32_t *>(&Bs[pp][n][kk + 2 * t]);
+                    b[pp][ni][1] = *reinterpret_cast<const uint32_t *>(&Bs[pp][n][kk + 8 + 2 * t]);
+                }
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) {
+                    if (SPLIT) {
+                        mma_bf16(acc[mi][ni], a[NP - 1][mi], b[0][ni]);
+                        mma_bf16(acc[mi][ni], a[0][mi], b[NP - 1][ni]);
+                    }
+                    mma_bf16(acc[mi][ni], a[0][mi], b[0][ni]);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int m = m0 + wm + mi * 16 + g + (q >= 2 ? 8 : 0);
+                const int n = n0 + wn + ni * 8 + 2 * t + (q & 1);
+                if (m < M && n < N) ep(m, n, z, acc[mi][ni][q]);
+            }
+}
+
+// im2col of the stride-2 pad-1 3x3 convolution: row m = (b, oy, ox), column
+// k = (c, ky, kx) (the order of the weight tensor [Cout][Cin][3][3]).
+struct Im2col {
+    const float *in;
+    int C, S, So;
+    __device__ float operator()(int m, int k, int /*z*/) const
+    {
+        const int b = m / (So * So), r = m - b * So * So, oy = r / So, ox = r - oy * So;
+        const int c = k / 9, tt = k - c * 9, ky = tt / 3, kx = tt - ky * 3;
+        const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
+        return (iy >= 0 && iy < S && ix >= 0 && ix < S) ? __ldg(in + (static_cast<size_t>(b * C + c) * S + iy) * S + ix) : 0.f;
+    }
+};
+struct WeightKN {  // B(k, n) = w[n][k]
+    const float *w;
+    int Kd;
+    __device__ float operator()(int k, int n, int) const { return __ldg(w + static_cast<size_t>(n) * Kd + k); }
+};
+struct ConvOut {  // r = LeakyReLU(acc + bias), stored [B][Cout][So][So]
+    const float *bias;
+    float *r;
+    int N, So;
+    __device__ void operator()(int m, int n, int, float v) const
+    {
+        const float zz = v + bias[n];
+        const int b = m / (So * So), rr = m - b * So * So;
+        r[(static_cast<size_t>(b) * N + n) * So * So + rr] = zz > 0.f ? zz : kSlope * zz;
+    }
+};
+// weight gradient: rows i = output channel, columns j = (c, ky, kx), the
+// reduction over pixels is chunked by blockIdx.z (partials summed later)
+struct DzRows {  // A(i, kk) = dz[b][i][p] for pixel kk of chunk z
+    const float *dz;
+    int N, So, pix;
+    __device__ float operator()(int i, int kk, int z) const
+    {
+        const int m = z * kWChunk + kk;
+        if (m >= pix) return 0.f;
+        const int b = m / (So * So), rr = m - b * So * So;
+        return __ldg(dz + (static_cast<size_t>(b) * N + i) * So * So + rr);
+    }
+};
+struct Im2colChunk {  // B(kk, j) = im2col(m = z * chunk + kk, j)
+    Im2col ic;
+    int pix;
+    __device__ float operator()(int kk, int j, int z) const
+    {
+        const int m = z * kWChunk + kk;
+        return m < pix ? ic(m, j, 0) : 0.f;
+    }
+};
+struct PartOut {
+    float *part;
+    int N, Kd;
+    __device__ void operator()(int i, int j, int z, float v) const
+    {
+        part[(static_cast<size_t>(z) * N + i) * Kd + j] = v;
+    }
+};
+// input gradient: rows m = input pixel (b, iy, ix), columns n = input channel,
+// reduction k = (o, ky, kx) over the output taps that read this pixel.
+struct DgradA {
+    const float *dz;
+    int N, S, So;
+    __device__ float operator()(int m, int k, int) const
+    {
+        const int b = m / (S * S), r = m - b * S * S, iy = r / S, ix = r - iy * S;
+        const int o = k / 9, tt = k - o * 9, ky = tt / 3, kx = tt - ky * 3;
+        const int ty = iy + 1 - ky, tx = ix + 1 - kx;
+        if ((ty | tx) < 0 || (ty & 1) || (tx & 1)) return 0.f;
+        const int oy = ty >> 1, ox = tx >> 1;
+        if (oy >= So || ox >= So) return 0.f;
+        return __ldg(dz + (static_cast<size_t>(b) * N + o) * So * So + oy * So + ox);
+    }
+};
+struct DgradB {  // B(k = (o, ky, kx), n = c) = w[o][c][ky][kx]
+    const float *w;
+    int C;
+    __device__ float operator()(int k, int c, int) const
+    {
+        const int o = k / 9, tt = k - o * 9;
+        return __ldg(w + (static_cast<size_t>(o) * C + c) * 9 + tt);
+    }
+};
+struct DgradOut {
+    float *dact;
+    int C, S;
+    __device__ void operator()(int m, int c, int, float v) const
+    {
+        const int b = m / (S * S), r = m - b * S * S;
+        dact[(static_cast<size_t>(b) * C + c) * S * S + r] = v;
+    }
+};
+
+template <bool SPLIT = false, class AL, class BL, class EP>
+static svdlut_status gemm(int M, int N, int Kd, int Z, AL al, BL bl, EP ep, cudaStream_t s)
+{
+    dim3 grid((M + 63) / 64, (N + 63) / 64, Z);
+    mma_gemm_kernel<SPLIT><<<grid, kGT, 0, s>>>(M, N, Kd, al, bl, ep);
+    SVDLUT_CUDA_TRY(cudaGetLastError());
+    return SVDLUT_OK;
+}
+
+// Fixed-order block sum (256 threads); every thread gets the total.
+__device__ __forceinline__ float block_sum256(float v, float *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += red[w];
+    return s;
+}
+
+// InstanceNorm statistics: one CTA per (b, c); mean and 1/sqrt(var + eps)
+// with the biased variance, two passes.
+__global__ void __launch_bounds__(256) in_stats_kernel(const float *__restrict__ r, int HW, float *mean, float *rstd)
+{
+    __shared__ float red[8];
+    const float *p = r + static_cast<size_t>(blockIdx.x) * HW;
+    float s = 0.f;
+    for (int i = threadIdx.x; i < HW; i += 256) s += p[i];
+    const float mu = block_sum256(s, red) / HW;
+    float q = 0.f;
+    for (int i = threadIdx.x; i < HW; i += 256) {
+        const float d = p[i] - mu;
+        q = fmaf(d, d, q);
+    }
+    const float var = block_sum256(q, red) / HW;
+    if (threadIdx.x == 0) {
+        mean[blockIdx.x] = mu;
+        rstd[blockIdx.x] = rsqrtf(var + kEps);
+    }
+}
+
+__global__ void in_apply_kernel(const float *__restrict__ r, const float *mean, const float *rstd, const float *gam,
+                                const float *bet, int C, int HW, size_t n, float *__restrict__ a)
+{
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const size_t bc = e / HW;
+        const int c = static_cast<int>(bc % C);
+        a[e] = (r[e] - mean[bc]) * rstd[bc] * gam[c] + bet[c];
+    }
+}
+
+// SplitMix64 finaliser (Steele, Lea, Flood 2014), the counter-based
+// generator of the dropout mask: element e of [B][64][8][8] is kept (x2)
+// when the top bit of splitmix64(seed * 2^32 + e) is 0.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float drop_scale(int training, uint64_t seed, size_t e)
+{
+    if (!training) return 1.f;
+    return (splitmix64((seed << 32) + e) >> 63) == 0 ? 2.f : 0.f;
+}
+
+// Dropout + 4x4 average pooling of the last feature map [B][64][8][8] -> rho [B][256].
+__global__ void pool_kernel(const float *__restrict__ r4, int B, int training, uint64_t seed, float *__restrict__ rho)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= B * kRho) return;
+    const int b = e / kRho, i = e - b * kRho, c = i >> 2, py = (i >> 1) & 1, px = i & 1;
+    float s = 0.f;
+    for (int yy = 0; yy < 4; ++yy)
+        for (int xx = 0; xx < 4; ++xx) {
+            const size_t f = ((static_cast<size_t>(b) * 64 + c) * 8 + py * 4 + yy) * 8 + px * 4 + xx;
+            s += r4[f] * drop_scale(training, seed, f);
+        }
+    rho[e] = s * (1.f / 16.f);
+}
+
+struct HeadW {
+    const float *w1[4], *b1[4], *w2[4], *b2[4];
+    int n[4];
+    int K;
+};
+
+struct ParamOut {
+    float *U, *S, *V, *lw, *gxy, *gxc, *gyc, *gw;
+};
+
+// destination of head h, output n of image b in the svdlut parameter layouts
+__device__ __forceinline__ float *head_dst(const ParamOut &o, int K, int h, int b, int n)
+{
+    if (h == 0) {
+        const int k = n / (3 * kDS * kDS), rem = n - k * 3 * kDS * kDS, plane = rem / (kDS * kDS),
+                  e = rem - plane * kDS * kDS;
+        float *base = plane == 0 ? o.gxy : (plane == 1 ? o.gxc : o.gyc);
+        return base + (static_cast<size_t>(b) * K + k) * kDS * kDS + e;
+    }
+    if (h == 1) return o.gw + static_cast<size_t>(b) * K * 4 + n;
+    if (h == 3) return o.lw + static_cast<size_t>(b) * 12 + n;
+    const int nu = 9 * kDT * kNS, ns = 9 * kNS;
+    if (n < nu) return o.U + static_cast<size_t>(b) * nu + n;
+    if (n < nu + ns) return o.S + static_cast<size_t>(b) * ns + (n - nu);
+    return o.V + static_cast<size_t>(b) * nu + (n - nu - ns);
+}
+
+__global__ void fc1_kernel(const float *__restrict__ rho, HeadW hw, int B, float *__restrict__ hidden)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (b, h, j)
+    if (e >= B * 32) return;
+    const int b = e >> 5, h = (e >> 3) & 3, j = e & 7;
+    const float *w = hw.w1[h] + j * kRho, *x = rho + static_cast<size_t>(b) * kRho;
+    float s = hw.b1[h][j];
+    for (int i = 0; i < kRho; ++i) s = fmaf(w[i], x[i], s);
+    hidden[e] = s;
+}
+
+__global__ void fc2_kernel(const float *__restrict__ hidden, HeadW hw, int B, int ntot, ParamOut o)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * ntot; e += gridDim.x * blockDim.x) {
+        const int b = e / ntot;
+        int n = e - b * ntot, h = 0;
+        while (n >= hw.n[h]) n -= hw.n[h++];
+        const float *w = hw.w2[h] + static_cast<size_t>(n) * kHidden, *x = hidden + b * 32 + h * 8;
+        float s = hw.b2[h][n];
+#pragma unroll
+        for (int j = 0; j < kHidden; ++j) s = fmaf(w[j], x[j], s);
+        *head_dst(o, hw.K, h, b, n) = s;
+    }
+}
+
+struct HeadGrads {  // where the head weight gradients go (passed by value)
+    float *dw2[4], *db2[4], *dw1[4], *db1[4];
+};
+
+struct ParamIn {
+    const float *U, *S, *V, *lw, *gxy, *gxc, *gyc, *gw;
+};
+
+__device__ __forceinline__ float head_src(const ParamIn &i, int K, int h, int b, int n)
+{
+    ParamOut o{const_cast<float *>(i.U), const_cast<float *>(i.S), const_cast<float *>(i.V), const_cast<float *>(i.lw),
+               const_cast<float *>(i.gxy), const_cast<float *>(i.gxc), const_cast<float *>(i.gyc),
+               const_cast<float *>(i.gw)};
+    return *head_dst(o, K, h, b, n);
+}
+
+// dW2, db2: one thread per (h, n), sums over the batch in order.
+__global__ void fc2_wgrad_kernel(const float *__restrict__ hidden, ParamIn d, HeadW hw, int B, int ntot, HeadGrads hg)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ntot; e += gridDim.x * blockDim.x) {
+        int n = e, h = 0;
+        while (n >= hw.n[h]) n -= hw.n[h++];
+        float sw[kHidden] = {}, sb = 0.f;
+        for (int b = 0; b < B; ++b) {
+            const float g = head_src(d, hw.K, h, b, n);
+            sb += g;
+#pragma unroll
+            for (int j = 0; j < kHidden; ++j) sw[j] = fmaf(g, hidden[b * 32 + h * 8 + j], sw[j]);
+        }
+        hg.db2[h][n] = sb;
+#pragma unroll
+        for (int j = 0; j < kHidden; ++j) hg.dw2[h][static_cast<size_t>(n) * kHidden + j] = sw[j];
+    }
+}
+
+// dhidden[b][h][j] = sum_n dout[b][h][n] w2[h][n][j]: one CTA per (b, h).
+__global__ void __launch_bounds__(256) fc2_dgrad_kernel(ParamIn d, HeadW hw, float *__restrict__ dhid)
+{
+    __shared__ float red[8];
+    const int b = blockIdx.x, h = blockIdx.y;
+    float s[kHidden] = {};
+    for (int n = threadIdx.x; n < hw.n[h]; n += 256) {
+        const float g = head_src(d, hw.K, h, b, n);
+#pragma unroll
+        for (int j = 0; j < kHidden; ++j) s[j] = fmaf(g, hw.w2[h][static_cast<size_t>(n) * kHidden + j], s[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kHidden; ++j) {
+        const float t = block_sum256(s[j], red);
+        if (threadIdx.x == 0) dhid[b * 32 + h * 8 + j] = t;
+    }
+}
+
+// dW1, db1 (thread per weight, sum over the batch in order) and drho.
+__global__ void fc1_bwd_kernel(const float *__restrict__ rho, const float *__restrict__ dhid, HeadW hw, int B,
+                               HeadGrads hg, float *__restrict__ drho)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < 4 * kHidden * kRho) {
+        const int h = e / (kHidden * kRho), r = e - h * kHidden * kRho, j = r / kRho, i = r - j * kRho;
+        float s = 0.f;
+        for (int b = 0; b < B; ++b) s = fmaf(dhid[b * 32 + h * 8 + j], rho[static_cast<size_t>(b) * kRho + i], s);
+        hg.dw1[h][r] = s;
+        if (i == 0) {
+            float sb = 0.f;
+            for (int b = 0; b < B; ++b) sb += dhid[b * 32 + h * 8 + j];
+            hg.db1[h][j] = sb;
+        }
+    }
+    if (e < B * kRho) {
+        const int b = e / kRho, i = e - b * kRho;
+        float s = 0.f;
+        for (int h = 0; h < 4; ++h)
+            for (int j = 0; j < kHidden; ++j) s = fmaf(dhid[b * 32 + h * 8 + j], hw.w1[h][j * kRho + i], s);
+        drho[e] = s;
+    }
+}
+
+// pooling, dropout and LeakyReLU backward: dz4 [B][64][8][8]
+__global__ void pool_bwd_kernel(const float *__restrict__ drho, const float *__restrict__ r4, int B, int training,
+                                uint64_t seed, float *__restrict__ dz)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= B * 64 * 64) return;
+    const int b = e / 4096, r = e - b * 4096, c = r >> 6, y = (r >> 3) & 7, x = r & 7;
+    const float g = drho[b * kRho + c * 4 + (y >> 2) * 2 + (x >> 2)] * (1.f / 16.f);
+    dz[e] = g * drop_scale(training, seed, e) * (r4[e] > 0.f ? 1.f : kSlope);
+}
+
+// sum of partial weight gradients over chunks (in order) and bias gradient
+__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int chunks, int n_out, float *__restrict__ dw)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_out; e += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < chunks; ++z) s += part[static_cast<size_t>(z) * n_out + e];
+        dw[e] = s;
+    }
+}
+
+// db[o] = sum over (b, pixels) of dz: one CTA per output channel
+__global__ void __launch_bounds__(256) bias_grad_kernel(const float *__restrict__ dz, int B, int N, int HW, float *db)
+{
+    __shared__ float red[8];
+    const int o = blockIdx.x;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b)
+        for (int i = threadIdx.x; i < HW; i += 256) s += dz[(static_cast<size_t>(b) * N + o) * HW + i];
+    const float t = block_sum256(s, red);
+    if (threadIdx.x == 0) db[o] = t;
+}
+
+// InstanceNorm backward, pass 1 (one CTA per (b, c)): s1 = sum dA xh, s2 = sum dA
+__global__ void __launch_bounds__(256) in_bwd_sums_kernel(const float *__restrict__ da, const float *__restrict__ r,
+                                                          const float *mean, const float *rstd, int HW, float *sums)
+{
+    __shared__ float red[8];
+    const size_t o = static_cast<size_t>(blockIdx.x) * HW;
+    const float mu = mean[blockIdx.x], rs = rstd[blockIdx.x];
+    float s1 = 0.f, s2 = 0.f;
+    for (int i = threadIdx.x; i < HW; i += 256) {
+        const float g = da[o + i];
+        s1 = fmaf(g, (r[o + i] - mu) * rs, s1);
+        s2 += g;
+    }
+    const float t1 = block_sum256(s1, red);
+    const float t2 = block_sum256(s2, red);
+    if (threadIdx.x == 0) {
+        sums[2 * blockIdx.x] = t1;
+        sums[2 * blockIdx.x + 1] = t2;
+    }
+}
+
+// pass 2: dz = LeakyReLU'(r) * rstd * gamma * (dA - s2/n - xh s1/n)
+__global__ void in_bwd_apply_kernel(const float *__restrict__ da, const float *__restrict__ r, const float *mean,
+                                    const float *rstd, const float *gam, const float *sums, int C, int HW, size_t n,
+                                    float *__restrict__ dz)
+{
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const size_t bc = e / HW;
+        const int c = static_cast<int>(bc % C);
+        const float rs = rstd[bc], xh = (r[e] - mean[bc]) * rs;
+        const float inv = 1.f / HW;
+        const float dr = rs * gam[c] * (da[e] - sums[2 * bc + 1] * inv - xh * sums[2 * bc] * inv);
+        dz[e] = r[e] > 0.f ? dr : kSlope * dr;
+    }
+}
+
+// dgamma[c], dbeta[c] = sums over the batch (in order)
+__global__ void in_param_grad_kernel(const float *sums, int B, int C, float *dg, float *db)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float a = 0.f, b2 = 0.f;
+    for (int b = 0; b < B; ++b) {
+        a += sums[2 * (b * C + c)];
+        b2 += sums[2 * (b * C + c) + 1];
+    }
+    dg[c] = a;
+    db[c] = b2;
+}
+
+__global__ void adam_kernel(float *w, const float *__restrict__ g, float *m, float *v, size_t n, float lr, float b1,
+                            float b2, float eps, float c1, float c2)
+{
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const float gg = g[e];
+        const float mm = b1 * m[e] + (1.f - b1) * gg;
+        const float vv = b2 * v[e] + (1.f - b2) * gg * gg;
+        m[e] = mm;
+        v[e] = vv;
+        w[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+    }
+}
+
+// MSE loss (Eq. 9, first term): per-CTA partial sums of (y - t)^2 and the
+// gradient dy = 2 (y - t) / n; partials are summed in order by mse_final.
+__global__ void __launch_bounds__(256) mse_kernel(const float *__restrict__ y, const float *__restrict__ t, size_t n,
+                                                  float *__restrict__ dy, float *__restrict__ part)
+{
+    __shared__ float red[8];
+    const float sc = 2.f / static_cast<float>(n);
+    float s = 0.f;
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const float d = y[e] - t[e];
+        s = fmaf(d, d, s);
+        if (dy) dy[e] = sc * d;
+    }
+    const float tot = block_sum256(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void mse_final_kernel(const float *part, int nb, size_t n, float *loss)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nb; ++i) s += part[i];
+        *loss = static_cast<float>(s / static_cast<double>(n));
+    }
+}
+
+inline int blocks_for(size_t n, int t = 256) { return static_cast<int>(std::min<size_t>((n + t - 1) / t, 152 * 8)); }
+
+inline HeadW head_weights(const float *w, const Layout &L, int K)
+{
+    HeadW h{};
+    for (int i = 0; i < 4; ++i) {
+        h.w1[i] = w + L.w1[i];
+        h.b1[i] = w + L.b1[i];
+        h.w2[i] = w + L.w2[i];
+        h.b2[i] = w + L.b2[i];
+        h.n[i] = L.head_n[i];
+    }
+    h.K = K;
+    return h;
+}
+
+}  // namespace gen
+}  // namespace svdlut
+
+using namespace svdlut;
+using namespace svdlut::gen;
+
+extern "C" size_t svdlut_generator_param_count(int K)
+{
+    if (K < 0 || K > kMaxK) return 0;
+    return make_layout(K).total;
+}
+
+extern "C" size_t svdlut_generator_workspace_size(int K, int B)
+{
+    if (K < 0 || K > kMaxK || B < 1) return 0;
+    return make_ws(B).total * sizeof(float);
+}
+
+static svdlut_status gen_check(int K, const float *weights, int B, void *ws, size_t ws_bytes)
+{
+    if (K < 0 || K > kMaxK) return fail(SVDLUT_ERR_INVALID_ARG, "K=%d out of [0, %d]", K, kMaxK);
+    if (B < 1) return fail(SVDLUT_ERR_INVALID_ARG, "B=%d must be >= 1", B);
+    if (!weights) return fail(SVDLUT_ERR_INVALID_ARG, "weights is NULL");
+    if (!ws || ws_bytes < svdlut_generator_workspace_size(K, B))
+        return fail(SVDLUT_ERR_WORKSPACE, "generator workspace of %zu bytes needed",
+                    svdlut_generator_workspace_size(K, B));
+    if (!aligned(ws, 256) || !aligned(weights, 4)) return fail(SVDLUT_ERR_INVALID_ARG, "misaligned weights or workspace");
+    return SVDLUT_OK;
+}
+
+extern "C" svdlut_status svdlut_generator_forward(int K, const float *weights, int B, int H, int W, const float *x,
+                                                  const svdlut_param_buffers *out, int training, uint64_t seed,
+                                                  void *ws, size_t ws_bytes, svdlut_stream_t stream)
+{
+    clear_error();
+    svdlut_status st = gen_check(K, weights, B, ws, ws_bytes);
+    if (st != SVDLUT_OK) return st;
+    if (!x || !out || H < 1 || W < 1) return fail(SVDLUT_ERR_INVALID_ARG, "x/out missing or H=%d W=%d", H, W);
+    if (!out->U || !out->S || !out->V || !out->lut_w || (K > 0 && (!out->g_xy || !out->g_xc || !out->g_yc || !out->grid_w)))
+        return fail(SVDLUT_ERR_INVALID_ARG, "every output buffer is required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const Layout L = make_layout(K);
+    const WsLayout wl = make_ws(B);
+    float *w = static_cast<float *>(ws);
+    downsample_kernel<<<blocks_for(static_cast<size_t>(B) * 3 * kThumb * kThumb), 256, 0, s>>>(x, B, H, W, w + wl.thumb);
+    SVDLUT_CUDA_TRY(cudaGetLastError());
+    const float *in = w + wl.thumb;
+    for (int i = 0; i < 5; ++i) {
+        const int Cin = kCh[i], Cout = kCh[i + 1], S = kSz[i], So = kSz[i + 1];
+        const int M = B * So * So, Kd = Cin * 9;
+        float *r = w + wl.r[i];
+        st = gemm(M, Cout, Kd, 1, Im2col{in, Cin, S, So}, WeightKN{weights + L.conv_w[i], Kd},
+                  ConvOut{weights + L.conv_b[i], r, Cout, So}, s);
+        if (st != SVDLUT_OK) return st;
+        if (i < 4) {
+            in_stats_kernel<<<B * Cout, 256, 0, s>>>(r, So * So, w + wl.mean[i], w + wl.rstd[i]);
+            const size_t n = act_size(B, i);
+            in_apply_kernel<<<blocks_for(n), 256, 0, s>>>(r, w + wl.mean[i], w + wl.rstd[i], weights + L.in_g[i],
+                                                          weights + L.in_b[i], Cout, So * So, n, w + wl.a[i]);
+            SVDLUT_CUDA_TRY(cudaGetLastError());
+            in = w + wl.a[i];
+        }
+    }
+    pool_kernel<<<(B * kRho + 255) / 256, 256, 0, s>>>(w + wl.r[4], B, training, seed, w + wl.rho);
+    const HeadW hw = head_weights(weights, L, K);
+    fc1_kernel<<<(B * 32 + 255) / 256, 256, 0, s>>>(w + wl.rho, hw, B, w + wl.hidden);
+    const int ntot = L.head_n[0] + L.head_n[1] + L.head_n[2] + L.head_n[3];
+    ParamOut po{out->U, out->S, out->V, out->lut_w, out->g_xy, out->g_xc, out->g_yc, out->grid_w};
+    fc2_kernel<<<blocks_for(static_cast<size_t>(B) * ntot), 256, 0, s>>>(w + wl.hidden, hw, B, ntot, po);
+    SVDLUT_CUDA_TRY(cudaGetLastError());
+    return SVDLUT_OK;
+}
+
+extern "C" svdlut_status svdlut_generator_backward(int K, const float *weights, int B, const svdlut_params *dparams,
+                                                   float *dweights, int training, uint64_t seed, void *ws,
+                                                   size_t ws_bytes, svdlut_stream_t stream)
+{
+    clear_error();
+    svdlut_status st = gen_check(K, weights, B, ws, ws_bytes);
+    if (st != SVDLUT_OK) return st;
+    if (!dparams || !dweights) return fail(SVDLUT_ERR_INVALID_ARG, "dparams and dweights are required");
+    if (!dparams->U || !dparams->S || !dparams->V || !dparams->lut_w ||
+        (K > 0 && (!dparams->g_xy || !dparams->g_xc || !dparams->g_yc || !dparams->grid_w)))
+        return fail(SVDLUT_ERR_INVALID_ARG, "every output gradient is required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const Layout L = make_layout(K);
+    const WsLayout wl = make_ws(B);
+    float *w = static_cast<float *>(ws);
+    HeadGrads hg{};
+    for (int h = 0; h < 4; ++h) {
+        hg.dw2[h] = dweights + L.w2[h];
+        hg.db2[h] = dweights + L.b2[h];
+        hg.dw1[h] = dweights + L.w1[h];
+        hg.db1[h] = dweights + L.b1[h];
+    }
+    const HeadW hw = head_weights(weights, L, K);
+    const ParamIn pin{dparams->U, dparams->S, dparams->V, dparams->lut_w, dparams->g_xy, dparams->g_xc,
+                      dparams->g_yc, dparams->grid_w};
+    const int ntot = L.head_n[0] + L.head_n[1] + L.head_n[2] + L.head_n[3];
+    fc2_wgrad_kernel<<<blocks_for(ntot), 256, 0, s>>>(w + wl.hidden, pin, hw, B, ntot, hg);
+    fc2_dgrad_kernel<<<dim3(B, 4), 256, 0, s>>>(pin, hw, w + wl.dhid);
+    fc1_bwd_kernel<<<(std::max(4 * kHidden * kRho, B * kRho) + 255) / 256, 256, 0, s>>>(
+        w + wl.rho, w + wl.dhid, hw, B, hg, w + wl.drho);
+    float *dz = w + wl.dz[0];
+    pool_bwd_kernel<<<(B * 4096 + 255) / 256, 256, 0, s>>>(w + wl.drho, w + wl.r[4], B, training, seed, dz);
+    SVDLUT_CUDA_TRY(cudaGetLastError());
+    for (int i = 4; i >= 0; --i) {
+        const int Cin = kCh[i], Cout = kCh[i + 1], S = kSz[i], So = kSz[i + 1];
+        const int pix = B * So * So, Kd = Cin * 9, chunks = (pix + kWChunk - 1) / kWChunk;
+        const float *in = i == 0 ? w + wl.thumb : w + wl.a[i - 1];
+        // weight gradient: partial per pixel chunk, then an ordered sum
+        st = gemm<true>(Cout, Kd, kWChunk, chunks, DzRows{dz, Cout, So, pix}, Im2colChunk{Im2col{in, Cin, S, So}, pix},
+                  PartOut{w + wl.wpart, Cout, Kd}, s);
+        if (st != SVDLUT_OK) return st;
+        wgrad_reduce_kernel<<<blocks_for(static_cast<size_t>(Cout) * Kd), 256, 0, s>>>(w + wl.wpart, chunks, Cout * Kd,
+                                                                                       dweights + L.conv_w[i]);
+        bias_grad_kernel<<<Cout, 256, 0, s>>>(dz, B, Cout, So * So, dweights + L.conv_b[i]);
+        SVDLUT_CUDA_TRY(cudaGetLastError());
+        if (i == 0) break;
+        // input gradient, then InstanceNorm + LeakyReLU backward of layer i-1
+        float *dact = w + wl.dact;
+        st = gemm<true>(B * S * S, Cin, Cout * 9, 1, DgradA{dz, Cout, S, So}, DgradB{weights + L.conv_w[i], Cin},
+                  DgradOut{dact, Cin, S}, s);
+        if (st != SVDLUT_OK) return st;
+        const int j = i - 1;
+        float *dz_next = dz == w + wl.dz[0] ? w + wl.dz[1] : w + wl.dz[0];
+        in_bwd_sums_kernel<<<B * Cin, 256, 0, s>>>(dact, w + wl.r[j], w + wl.mean[j], w + wl.rstd[j], S * S,
+                                                   w + wl.insum);
+        const size_t n = act_size(B, j);
+        in_bwd_apply_kernel<<<blocks_for(n), 256, 0, s>>>(dact, w + wl.r[j], w + wl.mean[j], w + wl.rstd[j],
+                                                          weights + L.in_g[j], w + wl.insum, Cin, S * S, n, dz_next);
+        in_param_grad_kernel<<<1, 64, 0, s>>>(w + wl.insum, B, Cin, dweights + L.in_g[j], dweights + L.in_b[j]);
+        SVDLUT_CUDA_TRY(cudaGetLastError());
+        dz = dz_next;
+    }
+    return SVDLUT_OK;
+}
+
+extern "C" svdlut_status svdlut_generator_adam(float *weights, const float *grads, float *m, float *v, size_t n,
+                                               float lr, float beta1, float beta2, float eps, int step,
+                                               svdlut_stream_t stream)
+{
+    clear_error();
+    if (!weights || !grads || !m || !v || n == 0 || step < 1)
+        return fail(SVDLUT_ERR_INVALID_ARG, "adam: null buffer, n = 0 or step < 1");
+    const float c1 = 1.f - powf(beta1, static_cast<float>(step));
+    const float c2 = 1.f - powf(beta2, static_cast<float>(step));
+    adam_kernel<<<blocks_for(n), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(weights, grads, m, v, n, lr, beta1,
+                                                                                    beta2, eps, c1, c2);
+    SVDLUT_CUDA_TRY(cudaGetLastError());
+    return SVDLUT_OK;
+}
+
+extern "C" svdlut_status svdlut_mse(const float *y, const float *target, size_t n, float *dy, float *loss, void *ws,
+                                    size_t ws_bytes, svdlut_stream_t stream)
+{
+    clear_error();
+    if (!y || !target || !loss || n == 0) return fail(SVDLUT_ERR_INVALID_ARG, "mse: null buffer or n = 0");
+    const int nb = std::min(blocks_for(n), 1024);
+    if (!ws || ws_bytes < sizeof(float) * static_cast<size_t>(nb))
+        return fail(SVDLUT_ERR_WORKSPACE, "mse: workspace of %zu bytes needed", sizeof(float) * static_cast<size_t>(1024));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float *part = static_cast<float *>(ws);
+    mse_kernel<<<nb, 256, 0, s>>>(y, target, n, dy, part);
+    mse_final_kernel<<<1, 32, 0, s>>>(part, nb, n, loss);
+    SVDLUT_CUDA_TRY(cudaGetLastError());
+    return SVDLUT_OK;
+}

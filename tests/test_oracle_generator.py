@@ -122,3 +122,13 @@ def test_backward_matches_central_differences(with_dropout):
         fd = sum(((fp[k] - fm[k]) * dparams[k]).sum() for k in fp) / (2 * h)
         an = float(g @ dirn)
         assert abs(fd - an) <= 1e-5 * max(1.0, abs(fd)), (fd, an)
+
+
+def test_bf16_rounding_definition():
+    # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties to even -> 1
+    assert G.bf16_round(1.0 + 2.0 ** -8) == 1.0
+    assert G.bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6  # tie between odd and even -> even
+    assert G.bf16_round(1.0 + 2.0 ** -7) == 1.0 + 2.0 ** -7      # representable
+    assert G.bf16_round(-3.0) == -3.0 and G.bf16_round(0.0) == 0.0
+    x = np.random.default_rng(5).normal(size=1000)
+    assert np.all(np.abs(G.bf16_round(x) - x) <= np.abs(x) * 2.0 ** -8)
