@@ -279,27 +279,10 @@ def dropout_mask(seed, B, shape=(64, 8, 8)):
 
 
 def identity_blob(K, rng=None, scale=0.0):
-    """Parameters whose output is the identity transform (final FC weights
-    zero, final biases = identity factors, all grid terms off); with scale > 0
-    the final FC weights are drawn N(0, scale) instead of zero (a seeded,
-    image-dependent perturbation of the identity).  Other weights: He-style
-    normal initialisation from rng (IN scale 1, shift 0)."""
+    """The seeded initial weights of svdlut_inputs.generator_init (identity
+    transform at scale = 0, final FC weights N(0, scale) otherwise)."""
     import svdlut_inputs as si
     rng = rng if rng is not None else np.random.default_rng(0)
-    p = {}
-    for n, s in param_layout(K):
-        if n.startswith("conv") and n.endswith(".w"):
-            fan_in = s[1] * 9
-            p[n] = rng.normal(0.0, np.sqrt(2.0 / fan_in), size=s)
-        elif n.startswith("in") and n.endswith(".g"):
-            p[n] = np.ones(s)
-        elif n.endswith(".w1"):
-            p[n] = rng.normal(0.0, np.sqrt(1.0 / s[1]), size=s)
-        elif n.endswith(".w2"):
-            p[n] = rng.normal(0.0, scale, size=s) if scale > 0 else np.zeros(s)
-        else:
-            p[n] = np.zeros(s)
-    ident = si.identity_params(si.Dims(DT, NS, K, DS, DS, DS))
-    p["ht.b2"] = np.concatenate([ident["U"].ravel(), ident["S"].ravel(), ident["V"].ravel()])
-    p["htw.b2"] = ident["lut_w"].ravel()
-    return pack(p, K)
+    blob = si.generator_init(K, rng, scale)
+    assert blob.size == param_count(K)
+    return blob

@@ -191,3 +191,72 @@ def make_ragged(seed: int = SEED_BASE + 2, n: int = 16, sizes=None, mode: str = 
 def make_upstream(seed: int, shape) -> np.ndarray:
     """Random float32 upstream gradient ~ N(0,1)."""
     return np.random.default_rng(seed).standard_normal(size=shape).astype(np.float32)
+
+
+# ---------------------------------------------------------------- generator inputs
+
+GEN_M, GEN_HIDDEN = 8, 8
+GEN_CH = (3, 8, 16, 32, 64, 64)
+
+
+def generator_shapes(K: int):
+    """(name, shape) of the generator's weights in the flat FP32 layout
+    documented with svdlut_generator_forward (include/svdlut.h)."""
+    heads = (K * 3 * 17 * 17, K * 4, 9 * (33 * 8 + 8 + 33 * 8), 12)
+    out = []
+    for i in range(5):
+        cin, cout = GEN_CH[i], GEN_CH[i + 1]
+        out += [(f"conv{i}.w", (cout, cin, 3, 3)), (f"conv{i}.b", (cout,))]
+        if i < 4:
+            out += [(f"in{i}.g", (cout,)), (f"in{i}.b", (cout,))]
+    for h, n in zip(("s", "sw", "t", "tw"), heads):
+        out += [(f"h{h}.w1", (GEN_HIDDEN, 32 * GEN_M)), (f"h{h}.b1", (GEN_HIDDEN,)),
+                (f"h{h}.w2", (n, GEN_HIDDEN)), (f"h{h}.b2", (n,))]
+    return out
+
+
+def generator_init(K: int, rng: np.random.Generator, final_scale: float = 0.0) -> np.ndarray:
+    """Seeded initial weights (float64 flat blob).  Convolutions and first FC
+    layers: zero-mean normal with variance 2/fan_in resp. 1/fan_in; biases 0;
+    InstanceNorm scale 1, shift 0.  The last FC layer of every head: N(0,
+    final_scale) (zero when final_scale = 0), its bias the identity factors
+    (all grid terms off), so that at final_scale = 0 the predicted transform
+    is the identity for every image."""
+    parts = {}
+    for n, s in generator_shapes(K):
+        if n.startswith("conv") and n.endswith(".w"):
+            parts[n] = rng.normal(0.0, np.sqrt(2.0 / (s[1] * 9)), size=s)
+        elif n.startswith("in") and n.endswith(".g"):
+            parts[n] = np.ones(s)
+        elif n.endswith(".w1"):
+            parts[n] = rng.normal(0.0, np.sqrt(1.0 / s[1]), size=s)
+        elif n.endswith(".w2"):
+            parts[n] = rng.normal(0.0, final_scale, size=s) if final_scale > 0 else np.zeros(s)
+        else:
+            parts[n] = np.zeros(s)
+    ident = identity_params(Dims(33, 8, K, 17, 17, 17))
+    parts["ht.b2"] = np.concatenate([ident["U"].ravel(), ident["S"].ravel(), ident["V"].ravel()])
+    parts["htw.b2"] = ident["lut_w"].ravel()
+    return np.concatenate([parts[n].ravel() for n, _ in generator_shapes(K)])
+
+
+def torch_photos(gen, B: int, H: int, W: int, device="cuda"):
+    """B photo-like synthetic images [B,3,H,W] float32 on `device` from the
+    seeded torch.Generator `gen`: per-channel linear ramps plus two seeded
+    sinusoids (the smooth tiles of make_image), then a global exposure gain
+    U(0.5, 1.5), a per-channel colour cast U(0.75, 1.25), a gamma
+    U(0.7, 1.4) and mild pixel noise N(0, 0.01), clipped to [0,1]."""
+    import torch
+    kw = dict(device=device, generator=gen)
+    yy = torch.linspace(0, 1, H, device=device).view(1, 1, H, 1)
+    xx = torch.linspace(0, 1, W, device=device).view(1, 1, 1, W)
+    u = lambda *s, lo=0.0, hi=1.0: lo + (hi - lo) * torch.rand(*s, **kw)
+    img = u(B, 3, 1, 1, lo=0.1, hi=0.5) + u(B, 3, 1, 1, lo=-0.4, hi=0.4) * xx + u(B, 3, 1, 1, lo=-0.4, hi=0.4) * yy
+    for _ in range(2):
+        amp, fx, fy = u(B, 3, 1, 1, lo=0.05, hi=0.25), u(B, 3, 1, 1, lo=0.5, hi=3.0), u(B, 3, 1, 1, lo=0.5, hi=3.0)
+        ph = u(B, 3, 1, 1, hi=2 * np.pi)
+        img = img + amp * torch.sin(2 * np.pi * (fx * xx + fy * yy) + ph)
+    img = img.clamp(0, 1) * u(B, 1, 1, 1, lo=0.5, hi=1.5) * u(B, 3, 1, 1, lo=0.75, hi=1.25)
+    img = img.clamp(1e-6, 1) ** u(B, 1, 1, 1, lo=0.7, hi=1.4)
+    img = img + 0.01 * torch.randn(B, 3, H, W, **kw)
+    return img.clamp(0, 1).contiguous()
