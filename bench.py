@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -40,12 +41,24 @@ KERNEL_SOURCES = ("paper_2508_16121_gb300/csrc/apply_kernel.cuh", "paper_2508_16
 PROFILE_SUMMARY = "profiles/apply_kernel_f32_3840x2160_mix.md"
 
 
-def kernel_hash() -> str:
+def _code_only(src: str) -> str:
+    """Source text without comments and blank lines, so that a comment edit
+    does not detach the recorded counters from the code they were taken on."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(l.rstrip() for l in src.splitlines() if l.strip())
+
+
+def kernel_hash(read=None) -> str:
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        if read is None:
+            with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+                text = fh.read()
+        else:
+            text = read(f)
+        h.update(_code_only(text).encode())
     return h.hexdigest()[:16]
 
 
@@ -242,6 +255,9 @@ def run_ours(args, world, rank, local):
     # ---- adjoint: 8 x 1920x1080 FP32, all gradients ----
     backward = run_backward_variant(svdlut, torch, dev, stream, args)
 
+    # ---- learned: generator + apply on 4 x 4K in one graph; training step ----
+    learned = run_learned_variant(svdlut, torch, dev, stream, args)
+
     # ---- end to end through the public API with pinned host buffers ----
     xh = sets[0][0].cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
@@ -290,7 +306,8 @@ def run_ours(args, world, rank, local):
                                      "GB/s": round(algo_bytes_apply(H, W, d, 1) / (u8_ms / 1e3) / 1e9, 1)},
                      "f32_plain_4k_by_regime_Mpix/s": regimes,
                      "batched_16_ragged": batched,
-                     "backward_8x1080p": backward},
+                     "backward_8x1080p": backward,
+                     "learned_4x4k": learned},
     }
     return out, (xh.numpy(), {k: v.cpu().numpy() for k, v in pd.items()}, d)
 
@@ -363,6 +380,60 @@ def run_backward_variant(svdlut, torch, dev, stream, args):
     algo = px * 36 + sum(int(v.numel()) * 8 for v in pt.values())  # x, dy in; dx out; params in, grads out
     return {"value": round(px / 1e6 / (ms / 1e3), 1), "unit": "Mpix/s", "ms": round(ms, 4),
             "GB/s": round(algo / (ms / 1e3) / 1e9, 1), "workload": "8 x 1920x1080 FP32, all gradients"}
+
+
+def run_learned_variant(svdlut, torch, dev, stream, args):
+    """Generator (thumbnail, BF16 tensor-core backbone, heads) + one apply
+    over 4 x 3840x2160, captured in one CUDA graph, against the plain
+    per-image path (4 svdlut_apply calls with given factors)."""
+    from paper_2508_16121_gb300 import train
+    K, B, H, W = 8, 4, H4K, W4K
+    x, _ = si.make_batch(si.config_seed(4), B, H, W, si.Dims(33, 8, K, 17, 17, 17))
+    xt = torch.from_numpy(x).to(dev)
+    w = torch.tensor(si.generator_init(K, np.random.default_rng(si.config_seed(4)), 0.05), dtype=torch.float32,
+                     device=dev)
+    gen = svdlut.Generator(K, w, max_batch=B)
+    params = gen.forward(xt)
+    y = torch.empty_like(xt)
+    svdlut.apply(xt, params, out=y)
+    torch.cuda.synchronize()
+    s_cap = torch.cuda.Stream(dev)
+    g_l = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s_cap):
+        with torch.cuda.graph(g_l, stream=s_cap):
+            gen.forward(xt, out=params, stream=s_cap)
+            svdlut.apply(xt, params, out=y, stream=s_cap)
+    per = [{k: v[i:i + 1].clone() for k, v in params.items()} for i in range(B)]
+    ys = [torch.empty_like(xt[i:i + 1]) for i in range(B)]
+    g_p = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s_cap):
+        with torch.cuda.graph(g_p, stream=s_cap):
+            for i in range(B):
+                svdlut.apply(xt[i:i + 1], per[i], out=ys[i], stream=s_cap)
+    steps = max(3, args.steps // 40)
+    t_l = time_calls(g_l.replay, steps, stream)
+    t_p = time_calls(g_p.replay, steps, stream)
+    t_g = time_calls(lambda: gen.forward(xt, out=params), steps, stream)
+    mpix = B * H * W / 1e6
+    # one training step (batch 64 of 256x256 pairs) through the library kernels
+    tr = train.Trainer(K=K, batch=64, size=256, lr=1e-3)
+    tr.run(3)
+    torch.cuda.synchronize()
+    a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_tr = 20
+    a_.record(stream)
+    tr.run(n_tr)
+    b_.record(stream)
+    torch.cuda.synchronize()
+    t_tr = a_.elapsed_time(b_) / n_tr
+    return {"workload": "4 x 3840x2160 FP32, K=8 grids 17^3, D_t=33 rank 8",
+            "generator_plus_apply_graph": {"value": round(mpix / (t_l / 1e3), 1), "unit": "Mpix/s",
+                                           "ms": round(t_l, 4)},
+            "plain_x4_graph": {"value": round(mpix / (t_p / 1e3), 1), "unit": "Mpix/s", "ms": round(t_p, 4)},
+            "generator_forward_ms": round(t_g, 4),
+            "speedup_vs_plain_graph": round(t_p / t_l, 3),
+            "train_step_ms_batch64_256px": round(t_tr, 3),
+            "train_pairs_per_s": round(64 / (t_tr / 1e3), 1)}
 
 
 def cpu_baseline(x, p, d, reps=2):

@@ -4,7 +4,7 @@
  * SVDLUT (arXiv 2508.16121) enhances an image with an image-adaptive colour
  * transform stored as nine 2D LUTs, each rebuilt from rank-R SVD factors, and
  * adds 2D bilateral-grid slicing for spatial awareness; both are fused into one
- * per-pixel pass (Sec. 3.2.3, Eq. 8; Supp. Sec. C, Eqs. 10-20).
+ * per-pixel pass (Sec. 3.2.3, Eq. 10; Supp. Sec. C, Eqs. 12-22).
  *
  * Conventions shared by every entry point
  *  - All tensor pointers are DEVICE pointers unless stated otherwise; the
@@ -17,9 +17,9 @@
  *    FP32 values are read as they are and clamped to [0,1] before lookup;
  *    8-bit values v are read as v/255.
  *  - Cell rule on an axis with D vertices: u = p (D-1), i = min(floor(u), D-2),
- *    delta = u - i  (Supp. Eq. 12 / Eq. 16 with the upper edge kept inside).
+ *    delta = u - i  (Supp. Eqs. 13 and 18 with the upper edge kept inside).
  *  - Spatial coordinates x' = x/(W-1), y' = y/(H-1) (0 when W or H is 1), pixel
- *    indices as in Supp. Eq. 15.
+ *    indices as in Supp. Eq. 17.
  */
 #ifndef SVDLUT_H
 #define SVDLUT_H
@@ -50,7 +50,7 @@ typedef enum {
 /*
  * Sizes of one transform.
  *   D_t   LUT vertices per axis (paper: 33, Supp. Sec. A)        2 <= D_t <= 33
- *   rank  SVD rank N_s (paper: 8, Eq. 7)                          1 <= rank <= D_t
+ *   rank  SVD rank N_s (paper: 8, Eq. 9)                          1 <= rank <= D_t
  *   K     number of 2D bilateral grids (paper: 6)                 0 <= K <= 48
  *   Dsx, Dsy, Dsc  grid vertices along x, y and intensity (paper: 17 each);
  *         Dsx, Dsy >= 2, 2 <= Dsc <= 64.
@@ -60,27 +60,27 @@ typedef struct {
 } svdlut_dims;
 
 /*
- * Per-image transform parameters (Supp. Tables 3-5), FP32 device arrays with
+ * Per-image transform parameters (Supp. Tables 9-12), FP32 device arrays with
  * a leading batch axis B (one set per image):
  *   U      [B][3 c][3 pair][D_t][rank]  pair order (rg, rb, gb); row i of U is
  *                                       vertex i of the pair's first axis
  *   S      [B][3][3][rank]              singular values (any sign)
  *   V      [B][3][3][D_t][rank]         row j is vertex j of the second axis
- *          so that t^c_p[i][j] = sum_r U[i][r] S[r] V[j][r]          (Eq. 7)
- *   lut_w  [B][3 c][4]                  (w_rg, w_rb, w_gb, b)        (Eq. 4)
+ *          so that t^c_p[i][j] = sum_r U[i][r] S[r] V[j][r]          (Eq. 9)
+ *   lut_w  [B][3 c][4]                  (w_rg, w_rb, w_gb, b)        (Eq. 5)
  *   g_xy   [B][K][Dsy][Dsx]             plane over (y, x)
  *   g_xc   [B][K][Dsx][Dsc]             plane over (x, intensity)
  *   g_yc   [B][K][Dsy][Dsc]             plane over (y, intensity)
- *   grid_w [B][K][4]                    (w_xy, w_xc, w_yc, b)        (Eq. 19)
+ *   grid_w [B][K][4]                    (w_xy, w_xc, w_yc, b)        (Supp. Eq. 21)
  * Grid k uses the intensity of channel k mod 3 and adds to output channel
- * k mod 3 (Eq. 8 / Supp. Eq. 20).  g_* and grid_w may be NULL when K == 0.
+ * k mod 3 (Eq. 10 / Supp. Eq. 22).  g_* and grid_w may be NULL when K == 0.
  */
 typedef struct {
     const float *U, *S, *V, *lut_w, *g_xy, *g_xc, *g_yc, *grid_w;
 } svdlut_params;
 
 /*
- * svdlut_apply -- the fused 2D slicing + 2D LUT transform (Eq. 8, Supp. Eq. 20):
+ * svdlut_apply -- the fused 2D slicing + 2D LUT transform (Eq. 10, Supp. Eq. 22):
  *   Y_c = sum_p w^c_p I_bi(x, t^c_p) + b^c
  *       + sum_{k = c mod 3} [ w_xy I_bi((x',y'), g_xy) + w_xc I_bi((x',x_c), g_xc)
  *                             + w_yc I_bi((y',x_c), g_yc) + b_k ]
@@ -115,7 +115,7 @@ typedef struct {
 } svdlut_launch_cfg;
 
 /*
- * svdlut_apply_batched -- the fused transform of svdlut_apply (Eq. 8) over n
+ * svdlut_apply_batched -- the fused transform of svdlut_apply (Eq. 10) over n
  * images of uneven sizes, each with its own transform, in one persistent
  * launch per 64 images.  imgs is a HOST array of n descriptors (read during the
  * call only).  The images' blocks are taken from a counter in ws, so the call
@@ -178,7 +178,7 @@ svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_params *para
 size_t svdlut_backward_workspace_size(const svdlut_dims *dims, int B, int H, int W);
 
 /*
- * ---- learned factor generator (Supp. Sec. A, Tables 1-5) ----
+ * ---- learned factor generator (Supp. Sec. A, Tables 8-12) ----
  * A 256x256 bilinear thumbnail of the input goes through five 3x3 stride-2
  * convolutions (3->8->16->32->64->64 channels; LeakyReLU 0.2, then affine
  * InstanceNorm on the first four), Dropout(0.5) while training, average
@@ -196,7 +196,7 @@ size_t svdlut_backward_workspace_size(const svdlut_dims *dims, int B, int H, int
  * w2 [n][8], b2 [n] with n = K*3*17*17, K*4, 9*(33*8+8+33*8), 12.  The factor
  * head's outputs are U ([3][3][33][8]), then S ([3][3][8]), then V; the grid
  * head's are [K][plane xy, xc, yc][17][17].  At K = 6 there are 160,478
- * parameters (the paper's Table 7).
+ * parameters (the paper's Table 6).
  */
 
 /* Writable parameter buffers (layouts of svdlut_params, leading batch axis). */

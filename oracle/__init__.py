@@ -4,10 +4,10 @@ Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
 baseline leg may import this package.  The product (the CUDA library and
 its Python binding) never calls it, and it shares no code with it.
 
-``svdlut_oracle.c`` holds the arithmetic (Eq. 7 reconstruction, Supp.
-Eqs. 10-20 transform and slicing, and their adjoint); this module compiles
+``svdlut_oracle.c`` holds the arithmetic (Eq. 9 reconstruction, Supp.
+Eqs. 12-22 transform and slicing, and their adjoint); this module compiles
 it with gcc and marshals numpy arrays.  ``generator.py`` holds the FP64
-oracle of the learned factor generator (Supp. Tables 1-5).
+oracle of the learned factor generator (Supp. Tables 8-12).
 
 Parity status: forward and adjoint are pinned (tests/test_oracle_*.py);
 the generator's numeric outputs are "parity unpinned" beyond the paper's
@@ -90,7 +90,7 @@ def _batched(params, x):
 
 
 def lut_from_svd(U, S, V):
-    """Eq. 7 for one table: U [D][R], S [R], V [D][R] -> T [D][D]."""
+    """Eq. 9 for one table: U [D][R], S [R], V [D][R] -> T [D][D]."""
     U, S, V = _d(U), _d(S), _d(V)
     D, R = U.shape
     T = np.empty((D, D))

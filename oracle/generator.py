@@ -3,12 +3,12 @@
 Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
 baseline leg may import this module.  Plain numpy, float64.
 
-Architecture (Supp. Sec. A, Tables 1-5; m = 8, M_s = M_sw = M_t = M_tw = 8):
-  bilinear downsample of the input to 3 x 256 x 256           (Table 1, row 1)
-  5 x [Conv3x3 stride 2 pad 1 -> LeakyReLU -> InstanceNorm]   (Table 1; no IN
+Architecture (Supp. Sec. A, Tables 8-12; m = 8, M_s = M_sw = M_t = M_tw = 8):
+  bilinear downsample of the input to 3 x 256 x 256           (Table 8, row 1)
+  5 x [Conv3x3 stride 2 pad 1 -> LeakyReLU -> InstanceNorm]   (Table 8; no IN
       after the 5th), channels 3 -> 8 -> 16 -> 32 -> 64 -> 64
   Dropout(0.5) (training), average pooling 8x8 -> 2x2, reshape to 256 = 32m
-  four heads, each FC 256 -> 8 then FC 8 -> n_out (Tables 2-5):
+  four heads, each FC 256 -> 8 then FC 8 -> n_out (Tables 9-12):
      H_s  -> K*3*Ds^2 2D bilateral grids (planes xy, xc, yc per grid)
      H_sw -> K*(3+1)  grid weights and bias
      H_t  -> 9*(Dt*Ns + Ns + Dt*Ns): U, S, V of the nine 2D LUTs
@@ -19,10 +19,10 @@ bilinear downsample with half-pixel centres (align_corners = False) and no
 antialiasing; average pool of 4x4 windows; no nonlinearity between the two FC
 layers of a head (a rank-8 factorisation); H_t's output is split as U, then S,
 then V, each in [c][pair] order; H_s's as [K][plane xy, xc, yc][17][17].
-The parameter count at K = 6 is 160,478, Table 7 ("Ours", 160.478K).
+The parameter count at K = 6 is 160,478, Table 6 ("Ours", 160.478K).
 
 Parity status: the paper prints no activations or outputs of the generator,
-so its values are "parity unpinned" beyond: the parameter count (Table 7 and
+so its values are "parity unpinned" beyond: the parameter count (Table 6 and
 its ablation rows), brute-force convolution on tiny inputs, the
 interpolation/normalisation invariants and central differences of this
 module's own forward (tests/test_oracle_generator.py).

@@ -7,22 +7,22 @@
  *
  * It computes, term by term and in double precision, what the paper
  * defines:
- *   - 2D LUTs rebuilt from SVD factors, T = U diag(S) V^T   (Eq. 7, gen_LUT_SVD)
- *   - 2D LUT transform by bilinear interpolation           (Eq. 4 / Supp. Eqs. 11-14)
- *   - 2D slicing of bilateral grids                         (Eq. 6 / Supp. Eqs. 15-19)
- *   - the fused sum Y_c = Phi^c + sum_{k = c mod 3} Psi^k   (Eq. 8 / Supp. Eq. 20)
+ *   - 2D LUTs rebuilt from SVD factors, T = U diag(S) V^T   (Eq. 9)
+ *   - 2D LUT transform by bilinear interpolation           (Eq. 5 / Supp. Eqs. 12-16)
+ *   - 2D slicing of bilateral grids                         (Eq. 7 / Supp. Eqs. 17-21)
+ *   - the fused sum Y_c = Phi^c + sum_{k = c mod 3} Psi^k   (Eq. 10 / Supp. Eq. 22)
  * plus the adjoint of that map (the paper trains end to end through it,
  * Sec. 4.2, but prints no formula: the adjoint below is the derivative of
  * the forward written here).
  *
  * Readings of the paper taken here (each is also listed in the design notes):
- *   - Supp. Eq. 14 repeats w_rb*phi_rb; the third term is w_gb*phi_gb (Eq. 4).
+ *   - Supp. Eq. 16 repeats w_rb*phi_rb; the third term is w_gb*phi_gb (Eq. 5).
  *   - Cell of a query p on D vertices: u = p (D-1), i = min(floor(u), D-2),
- *     delta = u - i  (Supp. Eq. 12 with the upper edge kept inside the table).
+ *     delta = u - i  (Supp. Eq. 13 with the upper edge kept inside the table).
  *   - Inputs are clamped to [0,1] before lookup.
  *   - x' = x/(W-1), y' = y/(H-1) with integer pixel indices; 0 when W or H is 1.
  *   - Grid k feeds output channel k mod 3 and uses that channel's intensity,
- *     for any K >= 0 (Supp. Eq. 20 generalised from K divisible by 3).
+ *     for any K >= 0 (Supp. Eq. 22 generalised from K divisible by 3).
  *   - Layouts: U, V [3 c][3 pair][D][R] (pair order rg, rb, gb; U rows index
  *     the first axis of the pair), S [3][3][R], lut_w [3][4] = (w_rg, w_rb,
  *     w_gb, b); g_xy [K][Dsy][Dsx], g_xc [K][Dsx][Dsc], g_yc [K][Dsy][Dsc],
@@ -40,11 +40,11 @@
 /* dims[6] = {D_t, rank, K, Dsx, Dsy, Dsc} */
 enum { O_DT = 0, O_R, O_K, O_DSX, O_DSY, O_DSC };
 
-/* channel on each axis of a pair: rg, rb, gb (Supp. Eq. 10) */
+/* channel on each axis of a pair: rg, rb, gb (Supp. Eq. 12) */
 static const int AX_A[3] = {0, 0, 1};
 static const int AX_B[3] = {1, 2, 2};
 
-/* ---- Eq. 7: T = U diag(S) V^T for one D x D table ---- */
+/* ---- Eq. 9: T = U diag(S) V^T for one D x D table ---- */
 void oracle_lut_from_svd(int D, int R, const double *U, const double *S,
                          const double *V, double *T)
 {
@@ -57,7 +57,7 @@ void oracle_lut_from_svd(int D, int R, const double *U, const double *S,
         }
 }
 
-/* Supp. Eq. 12 cell rule: lower vertex index and fractional position. */
+/* Supp. Eq. 13 cell rule: lower vertex index and fractional position. */
 static void cell(double p, int D, int *i, double *d)
 {
     double u = p * (double)(D - 1);
@@ -68,7 +68,7 @@ static void cell(double p, int D, int *i, double *d)
     *d = u - (double)k;
 }
 
-/* Supp. Eqs. 12-13 (and 16-18): bilinear read of tab[a][b] with row stride ld,
+/* Supp. Eqs. 13-15 (and 18-20): bilinear read of tab[a][b] with row stride ld,
  * Da x Db vertices, at (pa, pb) in [0,1]^2. */
 static double bilinear(const double *tab, int ld, int Da, int Db, double pa, double pb)
 {
@@ -123,7 +123,7 @@ static double *build_tables(const img_params *q)
     return T;
 }
 
-/* Forward of one pixel: Eq. 4 (LUT transform), Eq. 6 (slicing), Eq. 8 (sum).
+/* Forward of one pixel: Eq. 5 (LUT transform), Eq. 7 (slicing), Eq. 10 (sum).
  * p[3] clamped colour, (xs, ys) normalised position. */
 static void pixel_forward(const img_params *q, const double *T, const double p[3],
                           double xs, double ys, double y[3])

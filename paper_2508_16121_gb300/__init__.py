@@ -62,7 +62,7 @@ def _stream_ptr(stream=None):
 
 
 def apply(x, params, out=None, stream=None):
-    """Fused SVDLUT apply (Eq. 8).  x: CUDA tensor [B,3,H,W] or [3,H,W],
+    """Fused SVDLUT apply (Eq. 10).  x: CUDA tensor [B,3,H,W] or [3,H,W],
     float32 or uint8, contiguous.  params: dict of float32 CUDA tensors with
     an optional leading batch axis (see include/svdlut.h).  Returns y with
     x's shape and dtype."""

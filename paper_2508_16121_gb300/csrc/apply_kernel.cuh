@@ -1,4 +1,4 @@
-// Fused 2D slicing + 2D LUT transform kernel (Eq. 8, Supp. Eq. 20) for sm_103a.
+// Fused 2D slicing + 2D LUT transform kernel (Eq. 10, Supp. Eq. 22) for sm_103a.
 //
 // One persistent CTA per SM walks a contiguous range of pixel blocks; a block
 // is a 128-pixel-wide column strip of one image, BH rows tall (BH is planned
@@ -6,13 +6,13 @@
 // consecutive pixels of a row (one 16-byte load/store per plane); warp w owns
 // rows w, w + kWarps, ... of the block.
 //  - Prologue, once per image a CTA meets: the nine 2D LUTs are rebuilt from
-//    their SVD factors (Eq. 7) in shared memory, multiplied by their LUT
-//    weights (Eq. 4) and turned into per-cell bilinear coefficients
-//    (phi = a + b da + c db + d da db, Supp. Eq. 13) for the three output
+//    their SVD factors (Eq. 9) in shared memory, multiplied by their LUT
+//    weights (Eq. 5) and turned into per-cell bilinear coefficients
+//    (phi = a + b da + c db + d da db, Supp. Eq. 15) for the three output
 //    channels: 3 float4 per cell and pair.
 //  - Per block: the grid slices of the block's footprint are summed over the
 //    grids that feed each output channel (grid k feeds channel k mod 3, Supp.
-//    Eq. 20) with their weights (Eq. 19); the xc slice is packed as
+//    Eq. 22) with their weights (Eq. 21); the xc slice is packed as
 //    (x, x+1) x (j, j+1) corners.
 //  - Per row: a warp interpolates the xy and yc slices along y for its row.
 //  - Per pixel: 9 LDS.128 for the three LUT pairs, 2 LDS.128 (xy), 3 LDS.128
@@ -59,7 +59,7 @@ struct LaunchArgs {
 };
 
 // Spatial cell of pixel index x on an axis of n pixels and Ds vertices
-// (x' = x/(n-1), u = x' (Ds-1), Supp. Eqs. 15-16), computed exactly in
+// (x' = x/(n-1), u = x' (Ds-1), Supp. Eqs. 17-18), computed exactly in
 // integers: i = floor(x (Ds-1) / (n-1)) clamped to Ds-2, delta = remainder
 // / (n-1).  A float product x * (Ds-1)/(n-1) would lose up to half an ulp of
 // u (1.5e-5 at u ~ 479), too much for the grid term at 4K.
@@ -179,7 +179,7 @@ __device__ __forceinline__ float get(const float4 &v, int k)
 // Cell of p in [0,1] on an axis with D vertices (fDm1 = D-1, fDm2 = D-2), on
 // the FMA pipe: i = round-to-nearest(min(p (D-1) - 1/2, D-2)) via the
 // 1.5 * 2^23 magic constant, frac = p (D-1) - i in [0, 1].  This is the
-// Supp. Eq. 12 cell except exactly on a vertex, where the cell below may be
+// Supp. Eq. 13 cell except exactly on a vertex, where the cell below may be
 // chosen with frac = 1; bilinear interpolation is continuous there, so the
 // value is the same.
 __device__ __forceinline__ int cell_of(float p, float fDm1, float fDm2, float &frac)
@@ -190,7 +190,7 @@ __device__ __forceinline__ int cell_of(float p, float fDm1, float fDm2, float &f
     return __float_as_int(m) - 0x4B400000;
 }
 
-// ---- LUT prologue: Eq. 7 reconstruction, Eq. 4 weight fold, cell coefficients ----
+// ---- LUT prologue: Eq. 9 reconstruction, Eq. 5 weight fold, cell coefficients ----
 // Factor rows are padded to an odd stride so that lanes reading different
 // rows hit different banks.
 __host__ __device__ inline int padded_rank(int R) { return R | 1; }
@@ -349,7 +349,7 @@ __device__ __forceinline__ BlockBufs block_bufs(float *scratch, int nvx, int nvy
 }
 
 // sum_{k = c, c+3, ... < K} w_k[which] * src[k * kstride]: the grids feeding one
-// output channel (Supp. Eq. 20), weighted (Eq. 19).  Terms are taken four at a
+// output channel (Supp. Eq. 22), weighted (Eq. 21).  Terms are taken four at a
 // time with all four loads issued before their FMAs.
 __device__ __forceinline__ float fold_k(const float *src, size_t kstride, int c, int K, const float *misc, int which)
 {
@@ -449,7 +449,7 @@ __device__ __forceinline__ void warp_row_tables(const BlockGeom &g, const BlockB
 }
 
 // One LUT pair: add the folded, weighted bilinear value of the three output
-// channels (coefficient form of Supp. Eq. 13).  q points at the cell's 3 float4.
+// channels (coefficient form of Supp. Eq. 15).  q points at the cell's 3 float4.
 __device__ __forceinline__ void lut_pair(const float4 *__restrict__ q, float da, float db, float &y0, float &y1,
                                          float &y2)
 {

@@ -2,7 +2,7 @@
 //
 // The paper trains end to end through its slicing + LUT transform (Sec. 4.2)
 // and prints no derivative; everything here is the exact derivative of the
-// forward map of Eq. 8 / Supp. Eqs. 10-20.  Passes (all on the caller's
+// forward map of Eq. 10 / Supp. Eqs. 12-22.  Passes (all on the caller's
 // stream, no atomics, every sum in a fixed order -> bitwise repeatable):
 //   1. dx      : apply_kernel<float, N, true> (slopes of the same cells).
 //   2. lut     : lut_grad_kernel scatters dy_c * bilinear weights into
@@ -11,7 +11,7 @@
 //   3. grid    : grid_grad_kernel does the same for the folded grid planes
 //                (xy, xc, yc per output channel) over 128-px column blocks.
 //   4. reduce  : lut_finalize_kernel sums the CTA partials and contracts
-//                through T = U diag(S) V^T (Eq. 7) to dU, dS, dV, dlut_w;
+//                through T = U diag(S) V^T (Eq. 9) to dU, dS, dV, dlut_w;
 //                grid_reduce_kernel + grid_finalize_kernel give dg_* and dgrid_w.
 #include <algorithm>
 #include <cmath>

@@ -1,4 +1,4 @@
-// The learned factor generator (Supp. Sec. A, Tables 1-5) on sm_103a: a
+// The learned factor generator (Supp. Sec. A, Tables 8-12) on sm_103a: a
 // bilinear 256x256 thumbnail, five 3x3 stride-2 convolutions (BF16 tensor-core
 // implicit GEMMs, FP32 accumulation) with LeakyReLU and InstanceNorm, average
 // pooling to a 256-d context and four two-layer FC heads that emit the SVD
@@ -643,7 +643,7 @@ __global__ void adam_kernel(float *w, const float *__restrict__ g, float *m, flo
     }
 }
 
-// MSE loss (Eq. 9, first term): per-CTA partial sums of (y - t)^2 and the
+// MSE loss (Eq. 11, first term): per-CTA partial sums of (y - t)^2 and the
 // gradient dy = 2 (y - t) / n; partials are summed in order by mse_final.
 __global__ void __launch_bounds__(256) mse_kernel(const float *__restrict__ y, const float *__restrict__ t, size_t n,
                                                   float *__restrict__ dy, float *__restrict__ part)

@@ -1,7 +1,7 @@
 """Teacher-student training of the factor generator on synthetic pairs.
 
 The paper trains the generator end to end through the fused transform with
-Adam (Sec. 4.2; loss Eq. 9, whose MSE term is used here).  Its photo datasets
+Adam (Sec. 4.2; loss Eq. 11, whose MSE term is used here).  Its photo datasets
 are not available, so the training pairs are made by the transform itself:
 a frozen, seeded teacher generator (identity-biased output layer, final
 weights N(0, teacher_scale)) predicts image-dependent parameters, svdlut_apply

@@ -2,9 +2,9 @@
 oracle's forward map (a different code path) in FP64.
 
 The transform is linear in the LUT weights and in every grid plane and grid
-weight, and linear in each of U, S and V separately (Eq. 7), so central
+weight, and linear in each of U, S and V separately (Eq. 9), so central
 differences along those directions are exact up to rounding.  In the pixel
-values it is piecewise bilinear (Supp. Eq. 13): differences are exact away
+values it is piecewise bilinear (Supp. Eq. 15): differences are exact away
 from cell edges, so pixels within 1e-4 of a vertex are kept out of the
 pixel-gradient check.
 """

@@ -2,12 +2,12 @@
 mathematics fix, independently of the oracle's own code.
 
 - identity factors reproduce the input (bilinear interpolation is exact on
-  affine functions, Supp. Eq. 13);
+  affine functions, Supp. Eq. 15);
 - a full-rank SVD of a dense table reproduces scipy's bilinear interpolation
-  of that table (Eq. 7 + Supp. Eqs. 11-14);
-- Eckart-Young fixes the rank-truncated reconstruction (Eq. 7, Sec. 3.2.2);
+  of that table (Eq. 9 + Supp. Eqs. 13-16);
+- Eckart-Young fixes the rank-truncated reconstruction (Eq. 9, Sec. 3.2.2);
 - the slicing term equals scipy's bilinear interpolation of each grid plane
-  (Supp. Eqs. 15-19), with grid k feeding channel k mod 3 (Supp. Eq. 20);
+  (Supp. Eqs. 17-21), with grid k feeding channel k mod 3 (Supp. Eq. 22);
 - on-vertex queries return vertex values; continuity across cell edges;
   linearity in weights; clamping; degenerate W = 1 / H = 1.
 Planted mistakes (operands swapped in the oracle's inputs) must fail the pins.

@@ -1,7 +1,7 @@
 """Pins of the FP64 generator oracle (oracle/generator.py).
 
 The paper prints no activations of its generator; what it fixes is the
-architecture (Supp. Tables 1-5) and its parameter counts (Table 7 and the
+architecture (Supp. Tables 8-12) and its parameter counts (Table 6 and the
 dimension ablation), checked here against tests/golden/param_counts.txt.
 The layers are pinned against brute force and their defining invariants,
 the hand-written backward against central differences of the forward.
@@ -36,7 +36,7 @@ def test_param_count_matches_table_7():
     total = G.param_count(K)
     assert total == g["ours"]
     hs, hsw, ht, htw = head_params(K)
-    fusion = (K + 3) * 3 + 3  # the (K+3) -> 3 1x1 conv of Eq. 6
+    fusion = (K + 3) * 3 + 3  # the (K+3) -> 3 1x1 conv of Eq. 8
     assert total - hs - hsw == g["only_lut"]
     assert total - ht - htw + fusion == g["only_grid"]
     assert total + fusion == g["conv1x1"]
