@@ -30,7 +30,7 @@ def head_params(K):
     return [G.HIDDEN * 256 + G.HIDDEN + n * G.HIDDEN + n for n in G.head_sizes(K)]
 
 
-def test_param_count_matches_table_7():
+def test_param_count_matches_table_6():
     g = golden()
     K = 6
     total = G.param_count(K)
