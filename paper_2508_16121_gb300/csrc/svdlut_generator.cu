@@ -66,9 +66,10 @@ inline Layout make_layout(int K)
 }
 
 // Workspace (floats): forward activations kept for the backward pass, then
-// backward temporaries.
+// backward temporaries.  InstanceNorm is not materialised: the layer after it
+// reads r[i] and applies the per-(b, c) affine map sc * r + sh on load.
 struct WsLayout {
-    size_t thumb, r[5], a[4], mean[4], rstd[4], rho, hidden;
+    size_t thumb, r[5], mean[4], rstd[4], sc[4], sh[4], part, rho, hidden;
     size_t dz[2], dact, wpart, dhid, drho, insum;
     size_t total;
 };
@@ -76,6 +77,18 @@ struct WsLayout {
 constexpr int kWChunk = 4096;  // pixels per weight-gradient partial
 
 inline size_t act_size(int B, int i) { return static_cast<size_t>(B) * kCh[i + 1] * kSz[i + 1] * kSz[i + 1]; }
+
+// Split-K factor of forward conv i: enough (M-tile, K-slice) CTAs to cover
+// the SMs twice, at most one 32-wide K step per slice.
+inline int fwd_split(int B, int i)
+{
+    const int M = B * kSz[i + 1] * kSz[i + 1], tiles = (M + 63) / 64, ksteps = (kCh[i] * 9 + 31) / 32;
+    const int want = (2 * 152 + tiles - 1) / tiles;
+    return std::max(1, std::min(ksteps, want));
+}
+
+// K steps per slice for a split of Z
+inline int fwd_ksteps(int i, int Z) { return ((kCh[i] * 9 + 31) / 32 + Z - 1) / Z; }
 
 inline WsLayout make_ws(int B)
 {
@@ -89,10 +102,14 @@ inline WsLayout make_ws(int B)
     w.thumb = take(static_cast<size_t>(B) * 3 * kThumb * kThumb);
     for (int i = 0; i < 5; ++i) w.r[i] = take(act_size(B, i));
     for (int i = 0; i < 4; ++i) {
-        w.a[i] = take(act_size(B, i));
         w.mean[i] = take(static_cast<size_t>(B) * kCh[i + 1]);
         w.rstd[i] = take(static_cast<size_t>(B) * kCh[i + 1]);
+        w.sc[i] = take(static_cast<size_t>(B) * kCh[i + 1]);
+        w.sh[i] = take(static_cast<size_t>(B) * kCh[i + 1]);
     }
+    size_t pp = 0;
+    for (int i = 0; i < 5; ++i) pp = std::max(pp, static_cast<size_t>(fwd_split(B, i)) * act_size(B, i));
+    w.part = take(pp);
     w.rho = take(static_cast<size_t>(B) * kRho);
     w.hidden = take(static_cast<size_t>(B) * 4 * kHidden);
     const size_t amax = act_size(B, 0);
@@ -175,17 +192,25 @@ __global__ void __launch_bounds__(kGT) mma_gemm_kernel(int M, int N, int Kd, AL 
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
     for (int k0 = 0; k0 < Kd; k0 += 32) {
-        for (int e = tid; e < 64 * 32; e += kGT) {
-            const int r = e >> 5, c = e & 31, k = k0 + c;
+        // all 2 x 16 gathers of this thread are issued before any is used
+        constexpr int kPer = 64 * 32 / kGT;
+        float va[kPer], vb[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int e = tid + q * kGT, r = e >> 5, c = e & 31, k = k0 + c;
             const int m = m0 + r, n = n0 + r;
-            const float va = (m < M && k < Kd) ? al(m, k, z) : 0.f;
-            const float vb = (n < N && k < Kd) ? bl(k, n, z) : 0.f;
-            const __nv_bfloat16 ha = __float2bfloat16_rn(va), hb = __float2bfloat16_rn(vb);
+            va[q] = (m < M && k < Kd) ? al(m, k, z) : 0.f;
+            vb[q] = (n < N && k < Kd) ? bl(k, n, z) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int e = tid + q * kGT, r = e >> 5, c = e & 31;
+            const __nv_bfloat16 ha = __float2bfloat16_rn(va[q]), hb = __float2bfloat16_rn(vb[q]);
             As[0][r][c] = ha;
             Bs[0][r][c] = hb;
             if (SPLIT) {
-                As[NP - 1][r][c] = __float2bfloat16_rn(va - __bfloat162float(ha));
-                Bs[NP - 1][r][c] = __float2bfloat16_rn(vb - __bfloat162float(hb));
+                As[NP - 1][r][c] = __float2bfloat16_rn(va[q] - __bfloat162float(ha));
+                Bs[NP - 1][r][c] = __float2bfloat16_rn(vb[q] - __bfloat162float(hb));
             }
         }
         __syncthreads();
@@ -236,31 +261,20 @@ __global__ void __launch_bounds__(kGT) mma_gemm_kernel(int M, int N, int Kd, AL 
 
 // im2col of the stride-2 pad-1 3x3 convolution: row m = (b, oy, ox), column
 // k = (c, ky, kx) (the order of the weight tensor [Cout][Cin][3][3]).
+// With sc/sh set, the input is the InstanceNorm output sc[b][c] * r + sh[b][c]
+// of the raw activation r (zero padding is applied after the map).
 struct Im2col {
     const float *in;
     int C, S, So;
+    const float *sc = nullptr, *sh = nullptr;
     __device__ float operator()(int m, int k, int /*z*/) const
     {
         const int b = m / (So * So), r = m - b * So * So, oy = r / So, ox = r - oy * So;
         const int c = k / 9, tt = k - c * 9, ky = tt / 3, kx = tt - ky * 3;
         const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
-        return (iy >= 0 && iy < S && ix >= 0 && ix < S) ? __ldg(in + (static_cast<size_t>(b * C + c) * S + iy) * S + ix) : 0.f;
-    }
-};
-struct WeightKN {  // B(k, n) = w[n][k]
-    const float *w;
-    int Kd;
-    __device__ float operator()(int k, int n, int) const { return __ldg(w + static_cast<size_t>(n) * Kd + k); }
-};
-struct ConvOut {  // r = LeakyReLU(acc + bias), stored [B][Cout][So][So]
-    const float *bias;
-    float *r;
-    int N, So;
-    __device__ void operator()(int m, int n, int, float v) const
-    {
-        const float zz = v + bias[n];
-        const int b = m / (So * So), rr = m - b * So * So;
-        r[(static_cast<size_t>(b) * N + n) * So * So + rr] = zz > 0.f ? zz : kSlope * zz;
+        if (iy < 0 || iy >= S || ix < 0 || ix >= S) return 0.f;
+        const float v = __ldg(in + (static_cast<size_t>(b * C + c) * S + iy) * S + ix);
+        return sc ? fmaf(v, __ldg(sc + b * C + c), __ldg(sh + b * C + c)) : v;
     }
 };
 // weight gradient: rows i = output channel, columns j = (c, ky, kx), the
@@ -328,6 +342,191 @@ struct DgradOut {
     }
 };
 
+// ---- forward convolution (implicit GEMM, split over K) ----
+// Rows m = output pixel (b, oy, ox), columns n = output channel, reduction
+// k = (c, ky, kx) in the order of the weight tensor [N][C][3][3].  CTA z of a
+// split takes K steps [z ks, (z+1) ks) of 32 and writes its raw partial sums
+// to part[z][n][m]; conv_finish_kernel adds the partials in z order.  The
+// loader keeps one output pixel and 16 consecutive k per thread, so the
+// im2col index is stepped, not divided, per element; the input may be the
+// InstanceNorm output sc * r + sh of the previous layer's raw activation.
+struct ConvFwd {
+    const float *in;       // [B][C][S][S]
+    const float *sc, *sh;  // [B][C] affine map of the input, or null
+    const float *w;        // [N][C * 9]
+    float *part;           // [Z][N][M]
+    int C, S, So, N, M, Kd, ks;
+};
+
+__global__ void __launch_bounds__(kGT) conv_fwd_kernel(const ConvFwd p)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[64][40];
+    __shared__ __align__(16) __nv_bfloat16 Bs[64][40];
+    const int m0 = blockIdx.x * 64, z = blockIdx.z;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int g = lane >> 2, t = lane & 3;
+    const int lr = tid >> 1, lk = (tid & 1) * 16;  // loader: tile row and first k
+    const int m = m0 + lr, P = p.So * p.So;
+    const bool mvalid = m < p.M, nvalid = lr < p.N;
+    int b = 0, oy = 0, ox = 0;
+    if (mvalid) {
+        b = m / P;
+        const int rr = m - b * P;
+        oy = rr / p.So;
+        ox = rr - oy * p.So;
+    }
+    const int iy0 = 2 * oy - 1, ix0 = 2 * ox - 1;
+    const float *inb = p.in + static_cast<size_t>(b) * p.C * p.S * p.S;
+    const float *scb = p.sc ? p.sc + b * p.C : nullptr;
+    const float *shb = p.sh ? p.sh + b * p.C : nullptr;
+    const float *wrow = p.w + static_cast<size_t>(nvalid ? lr : 0) * p.Kd;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    const int kbeg = z * p.ks * 32, kend = min(p.Kd, kbeg + p.ks * 32);
+    for (int k0 = kbeg; k0 < kend; k0 += 32) {
+        const int k = k0 + lk;
+        int c = k / 9, tt = k - c * 9, ky = tt / 3, kx = tt - ky * 3;
+        float va[16], vb[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const bool kin = k + q < kend;
+            const int iy = iy0 + ky, ix = ix0 + kx;
+            const bool ok = mvalid && kin && static_cast<unsigned>(iy) < static_cast<unsigned>(p.S) &&
+                            static_cast<unsigned>(ix) < static_cast<unsigned>(p.S);
+            float v = ok ? __ldg(inb + (c * p.S + iy) * p.S + ix) : 0.f;
+            if (scb && ok) v = fmaf(v, __ldg(scb + c), __ldg(shb + c));
+            va[q] = v;
+            vb[q] = (nvalid && kin) ? __ldg(wrow + k + q) : 0.f;
+            if (++kx == 3) {
+                kx = 0;
+                if (++ky == 3) {
+                    ky = 0;
+                    ++c;
+                }
+            }
+        }
+        uint4 pa[2], pb[2];
+        uint32_t *ua = reinterpret_cast<uint32_t *>(pa), *ub = reinterpret_cast<uint32_t *>(pb);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const __nv_bfloat162 ha = __floats2bfloat162_rn(va[2 * q], va[2 * q + 1]);
+            const __nv_bfloat162 hb = __floats2bfloat162_rn(vb[2 * q], vb[2 * q + 1]);
+            ua[q] = *reinterpret_cast<const uint32_t *>(&ha);
+            ub[q] = *reinterpret_cast<const uint32_t *>(&hb);
+        }
+        *reinterpret_cast<uint4 *>(&As[lr][lk]) = pa[0];
+        *reinterpret_cast<uint4 *>(&As[lr][lk + 8]) = pa[1];
+        *reinterpret_cast<uint4 *>(&Bs[lr][lk]) = pb[0];
+        *reinterpret_cast<uint4 *>(&Bs[lr][lk + 8]) = pb[1];
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 32; kk += 16) {
+            uint32_t a[2][4], bb[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const int r = wm + mi * 16 + g;
+                a[mi][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * t]);
+                a[mi][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * t]);
+                a[mi][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 8 + 2 * t]);
+                a[mi][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 8 + 2 * t]);
+            }
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) {
+                const int n = wn + ni * 8 + g;
+                bb[ni][0] = *reinterpret_cast<const uint32_t *>(&Bs[n][kk + 2 * t]);
+                bb[ni][1] = *reinterpret_cast<const uint32_t *>(&Bs[n][kk + 8 + 2 * t]);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], bb[ni]);
+        }
+        __syncthreads();
+    }
+    float *pz = p.part + static_cast<size_t>(z) * p.N * p.M;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int mm = m0 + wm + mi * 16 + g + (q >= 2 ? 8 : 0);
+                const int n = wn + ni * 8 + 2 * t + (q & 1);
+                if (mm < p.M && n < p.N) pz[static_cast<size_t>(n) * p.M + mm] = acc[mi][ni][q];
+            }
+}
+
+// Fixed-order sum over the NW warps of a block; every thread gets the total.
+template <int NW>
+__device__ __forceinline__ float block_sum(float v, float *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s += red[w];
+    return s;
+}
+
+// One CTA per (b, n) plane of conv i: r = LeakyReLU(sum_z part + bias); with
+// gam set, also the InstanceNorm statistics of the plane (two passes, biased
+// variance) and its affine map sc = gamma rstd, sh = beta - mean sc.
+__global__ void __launch_bounds__(512) conv_finish_kernel(const float *__restrict__ part, int Z, int N, int M, int P,
+                                                          const float *__restrict__ bias, float *__restrict__ r,
+                                                          const float *gam, const float *bet, float *mean, float *rstd,
+                                                          float *sc, float *sh)
+{
+    __shared__ float red[16];
+    const int bn = blockIdx.x, b = bn / N, n = bn - b * N;
+    const float *src = part + static_cast<size_t>(n) * M + static_cast<size_t>(b) * P;
+    const size_t zs = static_cast<size_t>(N) * M;
+    float *dst = r + static_cast<size_t>(bn) * P;
+    const float bi = __ldg(bias + n);
+    float s = 0.f;
+    for (int i0 = threadIdx.x; i0 < P; i0 += 4 * 512) {
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int zz = 0; zz < Z; ++zz) {
+            float t[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) t[u] = i0 + u * 512 < P ? src[zz * zs + i0 + u * 512] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] += t[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (i0 + u * 512 >= P) break;
+            float x = v[u] + bi;
+            x = x > 0.f ? x : kSlope * x;
+            dst[i0 + u * 512] = x;
+            s += x;
+        }
+    }
+    if (!gam) return;
+    const float mu = block_sum<16>(s, red) / P;
+    float q = 0.f;
+    for (int i = threadIdx.x; i < P; i += 512) {
+        const float d = dst[i] - mu;
+        q = fmaf(d, d, q);
+    }
+    const float var = block_sum<16>(q, red) / P;
+    if (threadIdx.x == 0) {
+        const float rs = rsqrtf(var + kEps), gs = rs * gam[n];
+        mean[bn] = mu;
+        rstd[bn] = rs;
+        sc[bn] = gs;
+        sh[bn] = bet[n] - mu * gs;
+    }
+}
+
 template <bool SPLIT = false, class AL, class BL, class EP>
 static svdlut_status gemm(int M, int N, int Kd, int Z, AL al, BL bl, EP ep, cudaStream_t s)
 {
@@ -338,50 +537,7 @@ static svdlut_status gemm(int M, int N, int Kd, int Z, AL al, BL bl, EP ep, cuda
 }
 
 // Fixed-order block sum (256 threads); every thread gets the total.
-__device__ __forceinline__ float block_sum256(float v, float *red)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float s = 0.f;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) s += red[w];
-    return s;
-}
-
-// InstanceNorm statistics: one CTA per (b, c); mean and 1/sqrt(var + eps)
-// with the biased variance, two passes.
-__global__ void __launch_bounds__(256) in_stats_kernel(const float *__restrict__ r, int HW, float *mean, float *rstd)
-{
-    __shared__ float red[8];
-    const float *p = r + static_cast<size_t>(blockIdx.x) * HW;
-    float s = 0.f;
-    for (int i = threadIdx.x; i < HW; i += 256) s += p[i];
-    const float mu = block_sum256(s, red) / HW;
-    float q = 0.f;
-    for (int i = threadIdx.x; i < HW; i += 256) {
-        const float d = p[i] - mu;
-        q = fmaf(d, d, q);
-    }
-    const float var = block_sum256(q, red) / HW;
-    if (threadIdx.x == 0) {
-        mean[blockIdx.x] = mu;
-        rstd[blockIdx.x] = rsqrtf(var + kEps);
-    }
-}
-
-__global__ void in_apply_kernel(const float *__restrict__ r, const float *mean, const float *rstd, const float *gam,
-                                const float *bet, int C, int HW, size_t n, float *__restrict__ a)
-{
-    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
-         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const size_t bc = e / HW;
-        const int c = static_cast<int>(bc % C);
-        a[e] = (r[e] - mean[bc]) * rstd[bc] * gam[c] + bet[c];
-    }
-}
+__device__ __forceinline__ float block_sum256(float v, float *red) { return block_sum<8>(v, red); }
 
 // SplitMix64 finaliser (Steele, Lea, Flood 2014), the counter-based
 // generator of the dropout mask: element e of [B][64][8][8] is kept (x2)
@@ -400,19 +556,20 @@ __device__ __forceinline__ float drop_scale(int training, uint64_t seed, size_t 
     return (splitmix64((seed << 32) + e) >> 63) == 0 ? 2.f : 0.f;
 }
 
-// Dropout + 4x4 average pooling of the last feature map [B][64][8][8] -> rho [B][256].
-__global__ void pool_kernel(const float *__restrict__ r4, int B, int training, uint64_t seed, float *__restrict__ rho)
+// Dropout + 4x4 average pooling of the last feature map [B][64][8][8] -> rho
+// [B][256], one thread per rho element (kept for the backward pass).
+__device__ __forceinline__ float pool_one(const float *__restrict__ r4, int b, int i, int training, uint64_t seed)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= B * kRho) return;
-    const int b = e / kRho, i = e - b * kRho, c = i >> 2, py = (i >> 1) & 1, px = i & 1;
+    const int c = i >> 2, py = (i >> 1) & 1, px = i & 1;
     float s = 0.f;
+#pragma unroll
     for (int yy = 0; yy < 4; ++yy)
+#pragma unroll
         for (int xx = 0; xx < 4; ++xx) {
             const size_t f = ((static_cast<size_t>(b) * 64 + c) * 8 + py * 4 + yy) * 8 + px * 4 + xx;
-            s += r4[f] * drop_scale(training, seed, f);
+            s += __ldg(r4 + f) * drop_scale(training, seed, f);
         }
-    rho[e] = s * (1.f / 16.f);
+    return s * (1.f / 16.f);
 }
 
 struct HeadW {
@@ -442,15 +599,30 @@ __device__ __forceinline__ float *head_dst(const ParamOut &o, int K, int h, int 
     return o.V + static_cast<size_t>(b) * nu + (n - nu - ns);
 }
 
-__global__ void fc1_kernel(const float *__restrict__ rho, HeadW hw, int B, float *__restrict__ hidden)
+// Pooling and the first FC layer of the four heads, one CTA (256 threads) per
+// image: rho in shared memory, then each warp reduces 4 of the 32 hidden
+// units (lane-strided products, butterfly sum: a fixed order).
+__global__ void __launch_bounds__(256) pool_fc1_kernel(const float *__restrict__ r4, HeadW hw, int training,
+                                                       uint64_t seed, float *__restrict__ rho,
+                                                       float *__restrict__ hidden)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (b, h, j)
-    if (e >= B * 32) return;
-    const int b = e >> 5, h = (e >> 3) & 3, j = e & 7;
-    const float *w = hw.w1[h] + j * kRho, *x = rho + static_cast<size_t>(b) * kRho;
-    float s = hw.b1[h][j];
-    for (int i = 0; i < kRho; ++i) s = fmaf(w[i], x[i], s);
-    hidden[e] = s;
+    __shared__ float sr[kRho];
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float v = pool_one(r4, b, tid, training, seed);
+    sr[tid] = v;
+    rho[static_cast<size_t>(b) * kRho + tid] = v;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int o = warp * 4 + q, h = o >> 3, j = o & 7;
+        const float *w = hw.w1[h] + j * kRho;
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < kRho / 32; ++i) s = fmaf(__ldg(w + i * 32 + lane), sr[i * 32 + lane], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) hidden[b * 32 + o] = s + hw.b1[h][j];
+    }
 }
 
 __global__ void fc2_kernel(const float *__restrict__ hidden, HeadW hw, int B, int ntot, ParamOut o)
@@ -730,28 +902,31 @@ extern "C" svdlut_status svdlut_generator_forward(int K, const float *weights, i
     const Layout L = make_layout(K);
     const WsLayout wl = make_ws(B);
     float *w = static_cast<float *>(ws);
-    downsample_kernel<<<blocks_for(static_cast<size_t>(B) * 3 * kThumb * kThumb), 256, 0, s>>>(x, B, H, W, w + wl.thumb);
+    downsample_kernel<<<static_cast<int>((static_cast<size_t>(B) * 3 * kThumb * kThumb + 255) / 256), 256, 0, s>>>(
+        x, B, H, W, w + wl.thumb);
     SVDLUT_CUDA_TRY(cudaGetLastError());
-    const float *in = w + wl.thumb;
+    const float *in = w + wl.thumb, *isc = nullptr, *ish = nullptr;
     for (int i = 0; i < 5; ++i) {
         const int Cin = kCh[i], Cout = kCh[i + 1], S = kSz[i], So = kSz[i + 1];
         const int M = B * So * So, Kd = Cin * 9;
+        const int ks = fwd_ksteps(i, fwd_split(B, i)), Z = ((Kd + 31) / 32 + ks - 1) / ks;
         float *r = w + wl.r[i];
-        st = gemm(M, Cout, Kd, 1, Im2col{in, Cin, S, So}, WeightKN{weights + L.conv_w[i], Kd},
-                  ConvOut{weights + L.conv_b[i], r, Cout, So}, s);
-        if (st != SVDLUT_OK) return st;
-        if (i < 4) {
-            in_stats_kernel<<<B * Cout, 256, 0, s>>>(r, So * So, w + wl.mean[i], w + wl.rstd[i]);
-            const size_t n = act_size(B, i);
-            in_apply_kernel<<<blocks_for(n), 256, 0, s>>>(r, w + wl.mean[i], w + wl.rstd[i], weights + L.in_g[i],
-                                                          weights + L.in_b[i], Cout, So * So, n, w + wl.a[i]);
-            SVDLUT_CUDA_TRY(cudaGetLastError());
-            in = w + wl.a[i];
+        conv_fwd_kernel<<<dim3((M + 63) / 64, 1, Z), kGT, 0, s>>>(
+            ConvFwd{in, isc, ish, weights + L.conv_w[i], w + wl.part, Cin, S, So, Cout, M, Kd, ks});
+        const bool norm = i < 4;
+        conv_finish_kernel<<<B * Cout, 512, 0, s>>>(
+            w + wl.part, Z, Cout, M, So * So, weights + L.conv_b[i], r, norm ? weights + L.in_g[i] : nullptr,
+            norm ? weights + L.in_b[i] : nullptr, norm ? w + wl.mean[i] : nullptr, norm ? w + wl.rstd[i] : nullptr,
+            norm ? w + wl.sc[i] : nullptr, norm ? w + wl.sh[i] : nullptr);
+        SVDLUT_CUDA_TRY(cudaGetLastError());
+        in = r;
+        if (norm) {
+            isc = w + wl.sc[i];
+            ish = w + wl.sh[i];
         }
     }
-    pool_kernel<<<(B * kRho + 255) / 256, 256, 0, s>>>(w + wl.r[4], B, training, seed, w + wl.rho);
     const HeadW hw = head_weights(weights, L, K);
-    fc1_kernel<<<(B * 32 + 255) / 256, 256, 0, s>>>(w + wl.rho, hw, B, w + wl.hidden);
+    pool_fc1_kernel<<<B, 256, 0, s>>>(w + wl.r[4], hw, training, seed, w + wl.rho, w + wl.hidden);
     const int ntot = L.head_n[0] + L.head_n[1] + L.head_n[2] + L.head_n[3];
     ParamOut po{out->U, out->S, out->V, out->lut_w, out->g_xy, out->g_xc, out->g_yc, out->grid_w};
     fc2_kernel<<<blocks_for(static_cast<size_t>(B) * ntot), 256, 0, s>>>(w + wl.hidden, hw, B, ntot, po);
@@ -795,9 +970,10 @@ extern "C" svdlut_status svdlut_generator_backward(int K, const float *weights, 
     for (int i = 4; i >= 0; --i) {
         const int Cin = kCh[i], Cout = kCh[i + 1], S = kSz[i], So = kSz[i + 1];
         const int pix = B * So * So, Kd = Cin * 9, chunks = (pix + kWChunk - 1) / kWChunk;
-        const float *in = i == 0 ? w + wl.thumb : w + wl.a[i - 1];
+        const Im2col icol = i == 0 ? Im2col{w + wl.thumb, Cin, S, So}
+                                   : Im2col{w + wl.r[i - 1], Cin, S, So, w + wl.sc[i - 1], w + wl.sh[i - 1]};
         // weight gradient: partial per pixel chunk, then an ordered sum
-        st = gemm<true>(Cout, Kd, kWChunk, chunks, DzRows{dz, Cout, So, pix}, Im2colChunk{Im2col{in, Cin, S, So}, pix},
+        st = gemm<true>(Cout, Kd, kWChunk, chunks, DzRows{dz, Cout, So, pix}, Im2colChunk{icol, pix},
                   PartOut{w + wl.wpart, Cout, Kd}, s);
         if (st != SVDLUT_OK) return st;
         wgrad_reduce_kernel<<<blocks_for(static_cast<size_t>(Cout) * Kd), 256, 0, s>>>(w + wl.wpart, chunks, Cout * Kd,
