@@ -3,8 +3,10 @@
 // One persistent CTA per SM walks a contiguous range of pixel blocks; a block
 // is a 128-pixel-wide column strip of one image, BH rows tall (BH is planned
 // on the host so that the blocks cover the SMs evenly).  A lane owns 4
-// consecutive pixels of a row (one 16-byte load/store per plane); warp w owns
-// rows w, w + kWarps, ... of the block.
+// pixels of a row: columns lane + 32 k of the tile for float images (every
+// warp-wide access covers 32 adjacent pixels, which keeps the table gathers of
+// smooth regions on few cells), or 4 adjacent pixels for 8-bit images (one
+// 32-bit load/store per plane); warp w owns rows w, w + kWarps, ... of the block.
 //  - Prologue, once per image a CTA meets: the nine 2D LUTs are rebuilt from
 //    their SVD factors (Eq. 9) in shared memory, multiplied by their LUT
 //    weights (Eq. 5) and turned into per-cell bilinear coefficients
@@ -19,6 +21,8 @@
 //    (xc) and 3 LDS.64 (yc).  Row data is loaded one row ahead, across block
 //    boundaries.
 #pragma once
+
+#include <type_traits>
 
 #include "svdlut_internal.cuh"
 
@@ -111,6 +115,23 @@ struct PixIO<float> {
         return v;
     }
     static __device__ __forceinline__ float4 to_float(Raw v) { return v; }
+    // pixel k of a lane at p + 32 k (k < n): one coalesced 128-byte row per warp instruction
+    static __device__ __forceinline__ Raw load_s(const float *p, int n)
+    {
+        Raw v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n > 0) v.x = __ldcs(p);
+        if (n > 1) v.y = __ldcs(p + 32);
+        if (n > 2) v.z = __ldcs(p + 64);
+        if (n > 3) v.w = __ldcs(p + 96);
+        return v;
+    }
+    static __device__ __forceinline__ void store_s(float *p, float4 v, int n)
+    {
+        if (n > 0) __stcs(p, v.x);
+        if (n > 1) __stcs(p + 32, v.y);
+        if (n > 2) __stcs(p + 64, v.z);
+        if (n > 3) __stcs(p + 96, v.w);
+    }
     static __device__ __forceinline__ void store(float *p, float4 v, int n, bool vec)
     {
         if (vec && n == 4) {
@@ -494,6 +515,16 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
     if (blk >= b_end) return;
 
     using Raw = typename PixIO<T>::Raw;
+    // Pixel k of a lane in a 128-pixel tile row: column lane + 32 k for float
+    // images (each warp-wide access covers 32 adjacent pixels, so lanes of a
+    // coherent region gather the same table cells), lane * 4 + k for 8-bit
+    // images (one 32-bit load or store per lane and plane).
+    constexpr bool kStride = std::is_same<T, float>::value;
+    auto lane_px = [&](int W, int x0, int &x) {
+        x = x0 + (kStride ? lane : lane * 4);
+        if (kStride) return x < W ? min(4, (W - x + 31) >> 5) : 0;
+        return min(4, W - x);
+    };
 
     auto find_image = [&](int blk) {
         int im = 0;
@@ -506,18 +537,21 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         const ImgDesc &d = a.img[find_image(blk)];
         const int lb = blk - d.block_begin;
         const int band = lb / d.strips, strip = lb - band * d.strips;
-        const int x = strip * kTileW + lane * 4;
-        const int n = min(4, d.W - x);
+        int x;
+        const int n = lane_px(d.W, strip * kTileW, x);
         const int y = band * d.BH + row;
         const size_t plane = static_cast<size_t>(d.H) * d.W;
         const T *src = static_cast<const T *>(d.x) + static_cast<size_t>(y) * d.W + x;
         const bool ok = row < d.BH && y < d.H && n > 0;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) dst[c] = ok ? PixIO<T>::load(src + c * plane, n, d.vec) : Raw();
+        for (int c = 0; c < 3; ++c) {
+            if constexpr (kStride) dst[c] = ok ? PixIO<T>::load_s(src + c * plane, n) : Raw();
+            else dst[c] = ok ? PixIO<T>::load(src + c * plane, n, d.vec) : Raw();
+        }
         if constexpr (DX) {
             const float *g = d.dy + static_cast<size_t>(y) * d.W + x;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) dst[3 + c] = ok ? PixIO<float>::load(g + c * plane, n, d.vec) : Raw();
+            for (int c = 0; c < 3; ++c) dst[3 + c] = ok ? PixIO<float>::load_s(g + c * plane, n) : Raw();
         }
     };
 
@@ -550,12 +584,16 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         const float fD1 = static_cast<float>(D - 1), fD2 = static_cast<float>(D - 2);
         const float fS1 = static_cast<float>(Dc1), fS2 = static_cast<float>(Dsc - 2);
         const float bias0 = misc[kMaxK * 4 + 0], bias1 = misc[kMaxK * 4 + 1], bias2 = misc[kMaxK * 4 + 2];
-        const int xbase = g.x0 + lane * 4;
-        const int n = min(4, d.W - xbase);
-        const int4 ixl4 = reinterpret_cast<const int4 *>(b.coli)[lane];
-        const float4 dx4 = reinterpret_cast<const float4 *>(b.cold)[lane];
-        const int ixl[4] = {ixl4.x, ixl4.y, ixl4.z, ixl4.w};
-        const float dxk[4] = {dx4.x, dx4.y, dx4.z, dx4.w};
+        int xbase;
+        const int n = lane_px(d.W, g.x0, xbase);
+        int ixl[4];
+        float dxk[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int col = kStride ? lane + 32 * k : lane * 4 + k;
+            ixl[k] = b.coli[col];
+            dxk[k] = b.cold[col];
+        }
         const int xcs = (g.nvx - 1) * Dsc;  // float4 per channel of pxc
         const size_t plane = static_cast<size_t>(d.H) * d.W;
         T *dst = static_cast<T *>(d.y);
@@ -568,8 +606,8 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
             warp_row_tables(g, b, Dsc, row);
             __syncwarp();
             if (n > 0 && !DX) {
-                // the lane's 4 pixels usually span at most two x-cells: 3 vertices
-                const bool xy_fast = ixl[3] - ixl[0] <= 1;
+                // adjacent pixels (8-bit images) usually span at most two x-cells: 3 vertices
+                const bool xy_fast = !kStride && ixl[3] - ixl[0] <= 1;
                 float4 xa, xb, xc;
                 if (xy_fast) {
                     xa = b.rxy[ixl[0]];
@@ -615,8 +653,12 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                 }
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    PixIO<T>::store(dst + c * plane + static_cast<size_t>(y) * d.W + xbase,
-                                    make_float4(out[c][0], out[c][1], out[c][2], out[c][3]), n, d.vec);
+                {
+                    T *o = dst + c * plane + static_cast<size_t>(y) * d.W + xbase;
+                    const float4 v = make_float4(out[c][0], out[c][1], out[c][2], out[c][3]);
+                    if constexpr (kStride) PixIO<T>::store_s(o, v, n);
+                    else PixIO<T>::store(o, v, n, d.vec);
+                }
             }
             if (n > 0 && DX) {
                 float outd[3][4];
@@ -662,8 +704,8 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                 }
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    PixIO<float>::store(reinterpret_cast<float *>(d.y) + c * plane + static_cast<size_t>(y) * d.W + xbase,
-                                        make_float4(outd[c][0], outd[c][1], outd[c][2], outd[c][3]), n, d.vec);
+                    PixIO<float>::store_s(reinterpret_cast<float *>(d.y) + c * plane + static_cast<size_t>(y) * d.W + xbase,
+                                          make_float4(outd[c][0], outd[c][1], outd[c][2], outd[c][3]), n);
             }
             __syncwarp();  // row tables are rewritten for the next row
 #pragma unroll
