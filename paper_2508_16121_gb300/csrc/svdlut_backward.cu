@@ -5,9 +5,10 @@
 // forward map of Eq. 10 / Supp. Eqs. 12-22.  Passes (all on the caller's
 // stream, no atomics, every sum in a fixed order -> bitwise repeatable):
 //   1. dx      : apply_kernel<float, N, true> (slopes of the same cells).
-//   2. lut     : lut_grad_kernel scatters dy_c * bilinear weights into
-//                warp-private tables G^c_p (one channel per warp), then sums
-//                the warps of a CTA into a per-CTA partial.
+//   2. lut     : lut_grad_kernel scatters dy * bilinear weights into
+//                warp-private tables G_p[i][j][c] (one LUT pair, all three
+//                output channels per warp: one key match per pixel and pair),
+//                then sums the warps of a CTA into a per-CTA partial.
 //   3. grid    : grid_grad_kernel does the same for the folded grid planes
 //                (xy, xc, yc per output channel) over 128-px column blocks.
 //   4. reduce  : lut_finalize_kernel sums the CTA partials and contracts
@@ -99,7 +100,7 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-constexpr int kLutWarps = 12;  // 4 groups x 3 output channels
+constexpr int kLutWarps = 12;  // 4 groups x 3 LUT pairs
 constexpr int kLutThreads = kLutWarps * 32;
 
 struct BwdArgs {
@@ -115,6 +116,8 @@ struct BwdArgs {
 // LUT gradients: G^c_p[i][j] = sum_px dy_c * bilinear weight of vertex (i, j)
 // at (x_alpha, x_beta) for pair p = (alpha, beta).
 // grid (P, B); CTA p owns rows [p H / P, (p+1) H / P) of image blockIdx.y.
+// Warp (group g, pair q) scatters the pixels of group g into its table
+// [D][D][3 channels] for pair q.
 // Output: lut_part[b][p][c][pair][D*D], sums_part[b][p][c] (sum of dy_c).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kLutThreads, 1)
@@ -122,10 +125,11 @@ __global__ void __launch_bounds__(kLutThreads, 1)
 {
     extern __shared__ __align__(16) float sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int grp = warp / 3, ch = warp - grp * 3;
+    const int grp = warp / 3, pair = warp - grp * 3;
+    const int A = pair == 2 ? 1 : 0, Bx = pair == 0 ? 1 : 2;  // axes of the pair
     const int b = blockIdx.y, p = blockIdx.x;
     const int D = a.D, DD = D * D;
-    float *tab = sm + warp * 3 * DD;  // [pair][D][D] for output channel ch
+    float *tab = sm + warp * 3 * DD;  // [D][D][3 channels] of this warp's pair
     float *sums = sm + kLutWarps * 3 * DD;
     for (int e = threadIdx.x; e < kLutWarps * 3 * DD; e += kLutThreads) sm[e] = 0.f;
     __syncthreads();
@@ -134,54 +138,57 @@ __global__ void __launch_bounds__(kLutThreads, 1)
     const int r1 = static_cast<int>((static_cast<long long>(a.H) * (p + 1)) / P);
     const size_t plane = static_cast<size_t>(a.H) * a.W;
     const float *xb = a.x + static_cast<size_t>(b) * 3 * plane;
-    const float *gb = a.dy + static_cast<size_t>(b) * 3 * plane + ch * plane;
+    const float *gb = a.dy + static_cast<size_t>(b) * 3 * plane;
     const float fD1 = static_cast<float>(D - 1), fD2 = static_cast<float>(D - 2);
     const int units = (r1 - r0) * a.strips;
-    float dysum = 0.f;
+    float dysum[3] = {0.f, 0.f, 0.f};
     for (int u = grp; u < units; u += kLutWarps / 3) {
         const int row = r0 + u / a.strips, strip = u - (u / a.strips) * a.strips;
         const int x = strip * kTileW + lane * 4;
         const int n = min(4, a.W - x);
         const size_t o = static_cast<size_t>(row) * a.W + x;
-        float4 pr = make_float4(0.f, 0.f, 0.f, 0.f), pg = pr, pb = pr, g = pr;
+        float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa, g0 = pa, g1 = pa, g2 = pa;
         if (n > 0) {
             const bool v = a.vec && n == 4;
-            pr = PixIO<float>::load(xb + o, n, v);
-            pg = PixIO<float>::load(xb + plane + o, n, v);
-            pb = PixIO<float>::load(xb + 2 * plane + o, n, v);
-            g = PixIO<float>::load(gb + o, n, v);
+            pa = PixIO<float>::load(xb + A * plane + o, n, v);
+            pb = PixIO<float>::load(xb + Bx * plane + o, n, v);
+            g0 = PixIO<float>::load(gb + o, n, v);
+            g1 = PixIO<float>::load(gb + plane + o, n, v);
+            g2 = PixIO<float>::load(gb + 2 * plane + o, n, v);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const bool act = k < n;
-            const float gy = act ? get(g, k) : 0.f;
-            dysum += gy;
-            float pc[3] = {get(pr, k), get(pg, k), get(pb, k)}, dc[3];
-            int ic[3];
+            const float gy[3] = {act ? get(g0, k) : 0.f, act ? get(g1, k) : 0.f, act ? get(g2, k) : 0.f};
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                pc[c] = fminf(fmaxf(pc[c], 0.f), 1.f);
-                ic[c] = cell_of(pc[c], fD1, fD2, dc[c]);
-            }
+            for (int c = 0; c < 3; ++c) dysum[c] += gy[c];
+            float da, db;
+            const int ia = cell_of(fminf(fmaxf(get(pa, k), 0.f), 1.f), fD1, fD2, da);
+            const int ib = cell_of(fminf(fmaxf(get(pb, k), 0.f), 1.f), fD1, fD2, db);
+            const float w[4] = {(1.f - da) * (1.f - db), da * (1.f - db), (1.f - da) * db, da * db};
+            float v[4][3];
 #pragma unroll
-            for (int pair = 0; pair < 3; ++pair) {
-                const int A = pair == 2 ? 1 : 0, Bx = pair == 0 ? 1 : 2;
-                const float da = dc[A], db = dc[Bx];
-                float v[4][1] = {{gy * (1.f - da) * (1.f - db)}, {gy * da * (1.f - db)},
-                                 {gy * (1.f - da) * db}, {gy * da * db}};
-                warp_scatter<1>(tab + pair * DD, act ? ic[A] * D + ic[Bx] : -1, D, 1, v);
-            }
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[q][c] = gy[c] * w[q];
+            warp_scatter<3>(tab, act ? (ia * D + ib) * 3 : -1, D * 3, 3, v);
         }
     }
-    dysum = warp_sum(dysum);
-    if (lane == 0) sums[warp] = dysum;
+    // sum of dy_c: the pair-0 warps' totals (every pair warp of a group sees the same pixels)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dysum[c] = warp_sum(dysum[c]);
+    if (lane == 0 && pair == 0) {
+        sums[grp * 3 + 0] = dysum[0];
+        sums[grp * 3 + 1] = dysum[1];
+        sums[grp * 3 + 2] = dysum[2];
+    }
     __syncthreads();
-    // CTA partial: sum the 4 groups of each channel in order
+    // CTA partial [c][pair][cell]: sum the 4 groups in order
     float *out = lut_part + (static_cast<size_t>(b) * P + p) * 9 * DD;
     for (int e = threadIdx.x; e < 9 * DD; e += kLutThreads) {
-        const int c = e / (3 * DD), r = e - c * 3 * DD;
+        const int c = e / (3 * DD), r = e - c * 3 * DD, q = r / DD, cell = r - q * DD;
         float s = 0.f;
-        for (int gq = 0; gq < kLutWarps / 3; ++gq) s += sm[(gq * 3 + c) * 3 * DD + r];
+        for (int gq = 0; gq < kLutWarps / 3; ++gq) s += sm[(gq * 3 + q) * 3 * DD + cell * 3 + c];
         out[e] = s;
     }
     if (threadIdx.x < 3) {
