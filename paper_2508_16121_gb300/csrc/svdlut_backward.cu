@@ -273,12 +273,41 @@ __global__ void __launch_bounds__(kThreads, 1)
         spatial_cell(min(x + k, a.W - 1), a.W, a.Dsx, a.rW1, ix, dxk[k]);
         ixl[k] = max(0, min(ix - ixlo, nvx - 2));
     }
+    // xy: the weights factor as (y part) x (x part) and a lane's columns are
+    // fixed, so sum_rows dy_c (1 - dy) and sum_rows dy_c dy are kept per
+    // pixel while the rows stay in one y-cell and scattered when it changes.
+    float sy0[4][3], sy1[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sy0[k][c] = sy1[k][c] = 0.f;
+    int iyw_acc = -1;
+    auto flush_xy = [&]() {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float dx = dxk[k];
+            float v[4][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[0][c] = sy0[k][c] * (1.f - dx);
+                v[1][c] = sy1[k][c] * (1.f - dx);
+                v[2][c] = sy0[k][c] * dx;
+                v[3][c] = sy1[k][c] * dx;
+                sy0[k][c] = sy1[k][c] = 0.f;
+            }
+            warp_scatter<3>(txy, k < n ? (iyw_acc * gp.nvx + ixl[k]) * 3 : -1, gp.nvx * 3, 3, v);
+        }
+    };
     for (int r = wr0; r < wr1; ++r) {
         const int y = y0 + r;
         int iy;
         float dy;
         spatial_cell(y, a.H, a.Dsy, a.rH1, iy, dy);
         const int iyw = max(0, min(iy - wylo, nvyw - 2));
+        if (iyw != iyw_acc) {
+            if (iyw_acc >= 0) flush_xy();
+            iyw_acc = iyw;
+        }
         const size_t o = static_cast<size_t>(y) * a.W + x;
         float4 P[3], G[3];
 #pragma unroll
@@ -297,16 +326,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             float gy[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) gy[c] = act ? get(G[c], k) : 0.f;
-            {   // xy: corners (iy, ix), (iy+1, ix), (iy, ix+1), (iy+1, ix+1)
-                float v[4][3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    v[0][c] = gy[c] * (1.f - dy) * (1.f - dx);
-                    v[1][c] = gy[c] * dy * (1.f - dx);
-                    v[2][c] = gy[c] * (1.f - dy) * dx;
-                    v[3][c] = gy[c] * dy * dx;
-                }
-                warp_scatter<3>(txy, act ? (iyw * gp.nvx + ixl[k]) * 3 : -1, gp.nvx * 3, 3, v);
+            for (int c = 0; c < 3; ++c) {  // xy corners (iy, ix), (iy+1, ix), (iy, ix+1), (iy+1, ix+1)
+                sy0[k][c] = fmaf(gy[c], 1.f - dy, sy0[k][c]);
+                sy1[k][c] = fmaf(gy[c], dy, sy1[k][c]);
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -326,6 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     }
+    if (iyw_acc >= 0) flush_xy();
     // the warps' first vertex row relative to the block's
     __shared__ int wy_off[kWarps], wy_n[kWarps];
     if (lane == 0) {
