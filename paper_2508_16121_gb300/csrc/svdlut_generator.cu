@@ -493,13 +493,20 @@ __global__ void __launch_bounds__(512) conv_finish_kernel(const float *__restric
     const float bi = __ldg(bias + n);
     float s = 0.f;
     for (int i0 = threadIdx.x; i0 < P; i0 += 4 * 512) {
+        // four pixels, partials taken 8 slices at a time with every load
+        // issued before the (in-order) sums
         float v[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int zz = 0; zz < Z; ++zz) {
-            float t[4];
+        for (int z0 = 0; z0 < Z; z0 += 8) {
+            float t[8][4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) t[u] = i0 + u * 512 < P ? src[zz * zs + i0 + u * 512] : 0.f;
+            for (int zz = 0; zz < 8; ++zz)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] += t[u];
+                for (int u = 0; u < 4; ++u)
+                    t[zz][u] = z0 + zz < Z && i0 + u * 512 < P ? src[(z0 + zz) * zs + i0 + u * 512] : 0.f;
+#pragma unroll
+            for (int zz = 0; zz < 8; ++zz)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] += t[zz][u];
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -513,6 +520,7 @@ __global__ void __launch_bounds__(512) conv_finish_kernel(const float *__restric
     if (!gam) return;
     const float mu = block_sum<16>(s, red) / P;
     float q = 0.f;
+#pragma unroll 4
     for (int i = threadIdx.x; i < P; i += 512) {
         const float d = dst[i] - mu;
         q = fmaf(d, d, q);
