@@ -431,7 +431,9 @@ __device__ inline void block_phase_a(const ImgDesc &d, const BlockGeom &g, const
     }
 }
 
-// Block setup, phase B: corner packs of the folded xc slice.
+// Block setup, phase B: the folded xc slice of x-cell ix and intensity cell j
+// in slope form (F, F(j+1) - F(j), F(ix+1) - F(ix), [F(ix+1,j+1) - F(ix+1,j)] -
+// [F(ix,j+1) - F(ix,j)]), so that at (dx, e) it is (x + dx z) + e (y + dx w).
 __device__ inline void block_phase_b(const ImgDesc &d, const BlockGeom &g, const BlockBufs &b)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -440,7 +442,10 @@ __device__ inline void block_phase_b(const ImgDesc &d, const BlockGeom &g, const
         const int c = r / (nvx - 1), ixl = r - c * (nvx - 1);
         const float *f0 = b.fxc + (c * nvx + ixl) * Dsc;
         const float *f1 = f0 + Dsc;
-        for (int j = lane; j < Dc1; j += 32) b.pxc[r * Dsc + j] = make_float4(f0[j], f0[j + 1], f1[j], f1[j + 1]);
+        for (int j = lane; j < Dc1; j += 32) {
+            const float s0 = f0[j + 1] - f0[j], s1 = f1[j + 1] - f1[j];
+            b.pxc[r * Dsc + j] = make_float4(f0[j], s0, f1[j] - f0[j], s1 - s0);
+        }
     }
 }
 
@@ -465,7 +470,8 @@ __device__ __forceinline__ void warp_row_tables(const BlockGeom &g, const BlockB
         const int c = e >= Dc1 ? (e >= 2 * Dc1 ? 2 : 1) : 0, j = e - c * Dc1;
         const float *r0 = b.fyc + (c * nvy + iyl) * Dsc + j;
         const float *r1 = r0 + Dsc;
-        b.ryc[e] = make_float2(fmaf(r1[0] - r0[0], dy, r0[0]), fmaf(r1[1] - r0[1], dy, r0[1]));
+        const float v0 = fmaf(r1[0] - r0[0], dy, r0[0]), v1 = fmaf(r1[1] - r0[1], dy, r0[1]);
+        b.ryc[e] = make_float2(v0, v1 - v0);  // value at j and slope to j + 1
     }
 }
 
@@ -597,11 +603,28 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         const int xcs = (g.nvx - 1) * Dsc;  // float4 per channel of pxc
         const size_t plane = static_cast<size_t>(d.H) * d.W;
         T *dst = static_cast<T *>(d.y);
+        // this lane's pixels in row 0 of the block (input, and dy for the adjoint)
+        const T *xrow = static_cast<const T *>(d.x) + static_cast<size_t>(g.y0) * d.W + xbase;
+        const float *grow = DX ? d.dy + static_cast<size_t>(g.y0) * d.W + xbase : nullptr;
 #pragma unroll 1
         for (int row = warp; row < g.rows; row += kWarps) {
             // next row of this warp, possibly in the next block
-            if (row + kWarps < g.rows) load_row(blk, row + kWarps, nxt);
-            else if (has_next) load_row(next, warp, nxt);
+            if (row + kWarps < g.rows) {
+                const size_t ro = static_cast<size_t>(row + kWarps) * d.W;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (n <= 0) nxt[c] = Raw();
+                    else if constexpr (kStride) nxt[c] = PixIO<T>::load_s(xrow + ro + c * plane, n);
+                    else nxt[c] = PixIO<T>::load(xrow + ro + c * plane, n, d.vec);
+                }
+                if constexpr (DX) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        nxt[3 + c] = n > 0 ? PixIO<float>::load_s(grow + ro + c * plane, n) : Raw();
+                }
+            } else if (has_next) {
+                load_row(next, warp, nxt);
+            }
             const int y = g.y0 + row;
             warp_row_tables(g, b, Dsc, row);
             __syncwarp();
@@ -625,7 +648,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                     float dc[3], ec[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        p[c] = fminf(fmaxf(p[c], 0.f), 1.f);
+                        p[c] = __saturatef(p[c]);
                         ic[c] = cell_of(p[c], fD1, fD2, dc[c]);
                         jc[c] = cell_of(p[c], fS1, fS2, ec[c]);
                     }
@@ -646,9 +669,9 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                     for (int c = 0; c < 3; ++c) {
                         const float4 q = b.pxc[c * xcs + ixl[k] * Dsc + jc[c]];
                         const float2 qy = b.ryc[c * Dc1 + jc[c]];
-                        const float s0 = fmaf(q.z - q.x, dx, q.x) + qy.x;
-                        const float s1 = fmaf(q.w - q.y, dx, q.y) + qy.y;
-                        out[c][k] = yy[c] + fmaf(s1 - s0, ec[c], s0);
+                        const float s0 = fmaf(q.z, dx, q.x) + qy.x;  // value at j
+                        const float sl = fmaf(q.w, dx, q.y) + qy.y;  // slope to j + 1
+                        out[c][k] = fmaf(sl, ec[c], yy[c] + s0);
                     }
                 }
 #pragma unroll
@@ -696,9 +719,8 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                     for (int c = 0; c < 3; ++c) {
                         const float4 q = b.pxc[c * xcs + ixl[k] * Dsc + jc[c]];
                         const float2 qy = b.ryc[c * Dc1 + jc[c]];
-                        const float s0 = fmaf(q.z - q.x, dx, q.x) + qy.x;
-                        const float s1 = fmaf(q.w - q.y, dx, q.y) + qy.y;
-                        gp[c] = fmaf(gy[c] * fS1, s1 - s0, gp[c]);
+                        const float sl = fmaf(q.w, dx, q.y) + qy.y;  // slope to j + 1
+                        gp[c] = fmaf(gy[c] * fS1, sl, gp[c]);
                         outd[c][k] = (xv[c] >= 0.f && xv[c] <= 1.f) ? gp[c] : 0.f;
                     }
                 }
