@@ -74,9 +74,25 @@ struct WsLayout {
     size_t total;
 };
 
-constexpr int kWChunk = 4096;  // pixels per weight-gradient partial
 
 inline size_t act_size(int B, int i) { return static_cast<size_t>(B) * kCh[i + 1] * kSz[i + 1] * kSz[i + 1]; }
+
+// Weight gradient of conv i: the sum over the batch's output pixels is cut
+// into chunks of wgrad_chunk_px pixels (one GEMM slice each, a multiple of the
+// 32-wide K step) so that output tiles x chunks cover the SMs about twice.
+inline int wgrad_chunk_px(int B, int i)
+{
+    const int pix = B * kSz[i + 1] * kSz[i + 1];
+    const int tiles = ((kCh[i + 1] + 63) / 64) * ((kCh[i] * 9 + 1 + 63) / 64);
+    const int want = std::max(1, (2 * 152 + tiles - 1) / tiles);
+    const int px = (pix + want - 1) / want;
+    return std::max(32, (px + 31) / 32 * 32);
+}
+inline int wgrad_chunks(int B, int i)
+{
+    const int pix = B * kSz[i + 1] * kSz[i + 1], c = wgrad_chunk_px(B, i);
+    return (pix + c - 1) / c;
+}
 
 // Split-K factor of forward conv i: enough (M-tile, K-slice) CTAs to cover
 // the SMs twice, at most one 32-wide K step per slice.
@@ -118,9 +134,7 @@ inline WsLayout make_ws(int B)
     w.dact = take(amax);
     size_t wp = 0;
     for (int i = 0; i < 5; ++i) {
-        const size_t pix = static_cast<size_t>(B) * kSz[i + 1] * kSz[i + 1];
-        const size_t chunks = (pix + kWChunk - 1) / kWChunk;
-        wp = std::max(wp, chunks * kCh[i + 1] * kCh[i] * 9);
+        wp = std::max(wp, static_cast<size_t>(wgrad_chunks(B, i)) * kCh[i + 1] * (kCh[i] * 9 + 1));
     }
     w.wpart = take(wp);
     w.dhid = take(static_cast<size_t>(B) * 4 * kHidden);
@@ -174,7 +188,11 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 // operand is carried as hi + lo BF16 parts and the product is accumulated as
 // hi*hi + hi*lo + lo*hi (three MMAs, ~16 mantissa bits): the backward passes
 // sum long chains of cancelling terms, where plain BF16 loses too much.
-template <bool SPLIT, class AL, class BL, class EP>
+// ROWS = true: a loading thread keeps one tile row (m or n) and 16 consecutive
+// k, for functors whose row index is costly to decode (im2col over input
+// pixels); ROWS = false: it keeps one k and strides over rows, for functors
+// whose k index is costly (pixels of a weight-gradient chunk).
+template <bool SPLIT, bool ROWS, class AL, class BL, class EP>
 __global__ void __launch_bounds__(kGT) mma_gemm_kernel(int M, int N, int Kd, AL al, BL bl, EP ep)
 {
     constexpr int NP = SPLIT ? 2 : 1;
@@ -195,22 +213,49 @@ __global__ void __launch_bounds__(kGT) mma_gemm_kernel(int M, int N, int Kd, AL 
         // all 2 x 16 gathers of this thread are issued before any is used
         constexpr int kPer = 64 * 32 / kGT;
         float va[kPer], vb[kPer];
+        if (ROWS) {
+            const int r = tid >> 1, c0 = (tid & 1) * kPer, m = m0 + r, n = n0 + r;
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int e = tid + q * kGT, r = e >> 5, c = e & 31, k = k0 + c;
-            const int m = m0 + r, n = n0 + r;
-            va[q] = (m < M && k < Kd) ? al(m, k, z) : 0.f;
-            vb[q] = (n < N && k < Kd) ? bl(k, n, z) : 0.f;
+            for (int q = 0; q < kPer; ++q) {
+                const int k = k0 + c0 + q;
+                va[q] = (m < M && k < Kd) ? al(m, k, z) : 0.f;
+                vb[q] = (n < N && k < Kd) ? bl(k, n, z) : 0.f;
+            }
+        } else {
+            const int c = tid & 31, k = k0 + c;
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int r = (tid >> 5) + 4 * q, m = m0 + r, n = n0 + r;
+                va[q] = (m < M && k < Kd) ? al(m, k, z) : 0.f;
+                vb[q] = (n < N && k < Kd) ? bl(k, n, z) : 0.f;
+            }
+        }
+        const int r = ROWS ? tid >> 1 : 0, c0 = ROWS ? (tid & 1) * kPer : 0;
+        if (!ROWS) {
+            const int c = tid & 31;
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int rr = (tid >> 5) + 4 * q;
+                const __nv_bfloat16 ha = __float2bfloat16_rn(va[q]), hb = __float2bfloat16_rn(vb[q]);
+                As[0][rr][c] = ha;
+                Bs[0][rr][c] = hb;
+                if (SPLIT) {
+                    As[NP - 1][rr][c] = __float2bfloat16_rn(va[q] - __bfloat162float(ha));
+                    Bs[NP - 1][rr][c] = __float2bfloat16_rn(vb[q] - __bfloat162float(hb));
+                }
+            }
         }
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int e = tid + q * kGT, r = e >> 5, c = e & 31;
-            const __nv_bfloat16 ha = __float2bfloat16_rn(va[q]), hb = __float2bfloat16_rn(vb[q]);
-            As[0][r][c] = ha;
-            Bs[0][r][c] = hb;
+        for (int q = 0; q < (ROWS ? kPer : 0); q += 2) {
+            const __nv_bfloat162 ha = __floats2bfloat162_rn(va[q], va[q + 1]);
+            const __nv_bfloat162 hb = __floats2bfloat162_rn(vb[q], vb[q + 1]);
+            *reinterpret_cast<__nv_bfloat162 *>(&As[0][r][c0 + q]) = ha;
+            *reinterpret_cast<__nv_bfloat162 *>(&Bs[0][r][c0 + q]) = hb;
             if (SPLIT) {
-                As[NP - 1][r][c] = __float2bfloat16_rn(va[q] - __bfloat162float(ha));
-                Bs[NP - 1][r][c] = __float2bfloat16_rn(vb[q] - __bfloat162float(hb));
+                *reinterpret_cast<__nv_bfloat162 *>(&As[NP - 1][r][c0 + q]) = __floats2bfloat162_rn(
+                    va[q] - __low2float(ha), va[q + 1] - __high2float(ha));
+                *reinterpret_cast<__nv_bfloat162 *>(&Bs[NP - 1][r][c0 + q]) = __floats2bfloat162_rn(
+                    vb[q] - __low2float(hb), vb[q + 1] - __high2float(hb));
             }
         }
         __syncthreads();
@@ -281,22 +326,23 @@ struct Im2col {
 // reduction over pixels is chunked by blockIdx.z (partials summed later)
 struct DzRows {  // A(i, kk) = dz[b][i][p] for pixel kk of chunk z
     const float *dz;
-    int N, So, pix;
+    int N, So, pix, chunk;
     __device__ float operator()(int i, int kk, int z) const
     {
-        const int m = z * kWChunk + kk;
+        const int m = z * chunk + kk;
         if (m >= pix) return 0.f;
         const int b = m / (So * So), rr = m - b * So * So;
         return __ldg(dz + (static_cast<size_t>(b) * N + i) * So * So + rr);
     }
 };
-struct Im2colChunk {  // B(kk, j) = im2col(m = z * chunk + kk, j)
+struct Im2colChunk {  // B(kk, j) = im2col(m = z * chunk + kk, j); column Kd is all ones (bias)
     Im2col ic;
-    int pix;
+    int pix, chunk, Kd;
     __device__ float operator()(int kk, int j, int z) const
     {
-        const int m = z * kWChunk + kk;
-        return m < pix ? ic(m, j, 0) : 0.f;
+        const int m = z * chunk + kk;
+        if (m >= pix) return 0.f;
+        return j == Kd ? 1.f : ic(m, j, 0);
     }
 };
 struct PartOut {
@@ -535,11 +581,11 @@ __global__ void __launch_bounds__(512) conv_finish_kernel(const float *__restric
     }
 }
 
-template <bool SPLIT = false, class AL, class BL, class EP>
+template <bool SPLIT, bool ROWS, class AL, class BL, class EP>
 static svdlut_status gemm(int M, int N, int Kd, int Z, AL al, BL bl, EP ep, cudaStream_t s)
 {
     dim3 grid((M + 63) / 64, (N + 63) / 64, Z);
-    mma_gemm_kernel<SPLIT><<<grid, kGT, 0, s>>>(M, N, Kd, al, bl, ep);
+    mma_gemm_kernel<SPLIT, ROWS><<<grid, kGT, 0, s>>>(M, N, Kd, al, bl, ep);
     SVDLUT_CUDA_TRY(cudaGetLastError());
     return SVDLUT_OK;
 }
@@ -736,26 +782,24 @@ __global__ void pool_bwd_kernel(const float *__restrict__ drho, const float *__r
     dz[e] = g * drop_scale(training, seed, e) * (r4[e] > 0.f ? 1.f : kSlope);
 }
 
-// sum of partial weight gradients over chunks (in order) and bias gradient
-__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int chunks, int n_out, float *__restrict__ dw)
+// Sum of the partial weight gradients over chunks: one warp per output, lane
+// l adds chunks l, l + 32, ... in order, then a butterfly (a fixed order).
+// Partials are [chunks][N][Kd + 1]; column Kd is the bias gradient.
+__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int chunks, int N, int Kd, float *__restrict__ dw,
+                                    float *__restrict__ db)
 {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_out; e += gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int z = 0; z < chunks; ++z) s += part[static_cast<size_t>(z) * n_out + e];
-        dw[e] = s;
-    }
-}
-
-// db[o] = sum over (b, pixels) of dz: one CTA per output channel
-__global__ void __launch_bounds__(256) bias_grad_kernel(const float *__restrict__ dz, int B, int N, int HW, float *db)
-{
-    __shared__ float red[8];
-    const int o = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, n_out = N * (Kd + 1);
+    if (e >= n_out) return;  // whole warps leave together
     float s = 0.f;
-    for (int b = 0; b < B; ++b)
-        for (int i = threadIdx.x; i < HW; i += 256) s += dz[(static_cast<size_t>(b) * N + o) * HW + i];
-    const float t = block_sum256(s, red);
-    if (threadIdx.x == 0) db[o] = t;
+    for (int z = lane; z < chunks; z += 32) s += __ldg(part + static_cast<size_t>(z) * n_out + e);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const int i = e / (Kd + 1), j = e - i * (Kd + 1);
+        if (j < Kd) dw[i * Kd + j] = s;
+        else db[i] = s;
+    }
 }
 
 // InstanceNorm backward, pass 1 (one CTA per (b, c)): s1 = sum dA xh, s2 = sum dA
@@ -843,11 +887,13 @@ __global__ void __launch_bounds__(256) mse_kernel(const float *__restrict__ y, c
 
 __global__ void mse_final_kernel(const float *part, int nb, size_t n, float *loss)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < nb; ++i) s += part[i];
-        *loss = static_cast<float>(s / static_cast<double>(n));
-    }
+    // one warp: lane l adds partials l, l + 32, ... in double, then a butterfly
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = lane; i < nb; i += 32) s += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) *loss = static_cast<float>(s / static_cast<double>(n));
 }
 
 inline int blocks_for(size_t n, int t = 256) { return static_cast<int>(std::min<size_t>((n + t - 1) / t, 152 * 8)); }
@@ -977,21 +1023,21 @@ extern "C" svdlut_status svdlut_generator_backward(int K, const float *weights, 
     SVDLUT_CUDA_TRY(cudaGetLastError());
     for (int i = 4; i >= 0; --i) {
         const int Cin = kCh[i], Cout = kCh[i + 1], S = kSz[i], So = kSz[i + 1];
-        const int pix = B * So * So, Kd = Cin * 9, chunks = (pix + kWChunk - 1) / kWChunk;
+        const int pix = B * So * So, Kd = Cin * 9, chunk = wgrad_chunk_px(B, i), chunks = wgrad_chunks(B, i);
         const Im2col icol = i == 0 ? Im2col{w + wl.thumb, Cin, S, So}
                                    : Im2col{w + wl.r[i - 1], Cin, S, So, w + wl.sc[i - 1], w + wl.sh[i - 1]};
-        // weight gradient: partial per pixel chunk, then an ordered sum
-        st = gemm<true>(Cout, Kd, kWChunk, chunks, DzRows{dz, Cout, So, pix}, Im2colChunk{icol, pix},
-                  PartOut{w + wl.wpart, Cout, Kd}, s);
+        // weight and bias gradient: partial per pixel chunk (bias = an extra
+        // all-ones im2col column), then an ordered sum
+        st = gemm<true, false>(Cout, Kd + 1, chunk, chunks, DzRows{dz, Cout, So, pix, chunk},
+                        Im2colChunk{icol, pix, chunk, Kd}, PartOut{w + wl.wpart, Cout, Kd + 1}, s);
         if (st != SVDLUT_OK) return st;
-        wgrad_reduce_kernel<<<blocks_for(static_cast<size_t>(Cout) * Kd), 256, 0, s>>>(w + wl.wpart, chunks, Cout * Kd,
-                                                                                       dweights + L.conv_w[i]);
-        bias_grad_kernel<<<Cout, 256, 0, s>>>(dz, B, Cout, So * So, dweights + L.conv_b[i]);
+        wgrad_reduce_kernel<<<(Cout * (Kd + 1) * 32 + 255) / 256, 256, 0, s>>>(
+            w + wl.wpart, chunks, Cout, Kd, dweights + L.conv_w[i], dweights + L.conv_b[i]);
         SVDLUT_CUDA_TRY(cudaGetLastError());
         if (i == 0) break;
         // input gradient, then InstanceNorm + LeakyReLU backward of layer i-1
         float *dact = w + wl.dact;
-        st = gemm<true>(B * S * S, Cin, Cout * 9, 1, DgradA{dz, Cout, S, So}, DgradB{weights + L.conv_w[i], Cin},
+        st = gemm<true, true>(B * S * S, Cin, Cout * 9, 1, DgradA{dz, Cout, S, So}, DgradB{weights + L.conv_w[i], Cin},
                   DgradOut{dact, Cin, S}, s);
         if (st != SVDLUT_OK) return st;
         const int j = i - 1;

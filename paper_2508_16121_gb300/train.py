@@ -128,3 +128,32 @@ def evaluate(trainer: Trainer, n_batches=4, eval_seed=99, mean_batches=8):
         out["mean_teacher"].append(psnr(apply(x, mean_p), yt))
     torch.cuda.synchronize()
     return {k: float(np.mean(v)) for k, v in out.items()}
+
+
+def main(argv=None):
+    """Command line: train the generator for a number of steps on the GPU and
+    report the loss and held-out PSNR, e.g.
+    ``python -m paper_2508_16121_gb300.train --steps 320 --batch 64 --size 256``."""
+    import argparse
+    ap = argparse.ArgumentParser(description="teacher-student training of the SVDLUT factor generator")
+    ap.add_argument("--steps", type=int, default=320)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--K", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--eval", action="store_true", help="held-out PSNR before and after")
+    ap.add_argument("--save", default=None, help="checkpoint path")
+    args = ap.parse_args(argv)
+    tr = Trainer(K=args.K, batch=args.batch, size=args.size, lr=args.lr)
+    if args.eval:
+        print("before:", evaluate(tr))
+    losses = tr.run(args.steps)
+    print(f"steps {args.steps}: loss first {losses[0]:.5f} last {losses[-1]:.5f}")
+    if args.eval:
+        print("after:", evaluate(tr))
+    if args.save:
+        tr.save(args.save)
+
+
+if __name__ == "__main__":
+    main()
