@@ -353,41 +353,6 @@ struct PartOut {
         part[(static_cast<size_t>(z) * N + i) * Kd + j] = v;
     }
 };
-// input gradient: rows m = input pixel (b, iy, ix), columns n = input channel,
-// reduction k = (o, ky, kx) over the output taps that read this pixel.
-struct DgradA {
-    const float *dz;
-    int N, S, So;
-    __device__ float operator()(int m, int k, int) const
-    {
-        const int b = m / (S * S), r = m - b * S * S, iy = r / S, ix = r - iy * S;
-        const int o = k / 9, tt = k - o * 9, ky = tt / 3, kx = tt - ky * 3;
-        const int ty = iy + 1 - ky, tx = ix + 1 - kx;
-        if ((ty | tx) < 0 || (ty & 1) || (tx & 1)) return 0.f;
-        const int oy = ty >> 1, ox = tx >> 1;
-        if (oy >= So || ox >= So) return 0.f;
-        return __ldg(dz + (static_cast<size_t>(b) * N + o) * So * So + oy * So + ox);
-    }
-};
-struct DgradB {  // B(k = (o, ky, kx), n = c) = w[o][c][ky][kx]
-    const float *w;
-    int C;
-    __device__ float operator()(int k, int c, int) const
-    {
-        const int o = k / 9, tt = k - o * 9;
-        return __ldg(w + (static_cast<size_t>(o) * C + c) * 9 + tt);
-    }
-};
-struct DgradOut {
-    float *dact;
-    int C, S;
-    __device__ void operator()(int m, int c, int, float v) const
-    {
-        const int b = m / (S * S), r = m - b * S * S;
-        dact[(static_cast<size_t>(b) * C + c) * S * S + r] = v;
-    }
-};
-
 // ---- forward convolution (implicit GEMM, split over K) ----
 // Rows m = output pixel (b, oy, ox), columns n = output channel, reduction
 // k = (c, ky, kx) in the order of the weight tensor [N][C][3][3].  CTA z of a
@@ -506,6 +471,132 @@ __global__ void __launch_bounds__(kGT) conv_fwd_kernel(const ConvFwd p)
                 const int n = wn + ni * 8 + 2 * t + (q & 1);
                 if (mm < p.M && n < p.N) pz[static_cast<size_t>(n) * p.M + mm] = acc[mi][ni][q];
             }
+}
+
+// ---- input gradient of the stride-2 3x3 convolution, by input parity ----
+// Input pixel (iy, ix) = (2 qy + py, 2 qx + px) only receives the taps with
+// iy + 1 - ky and ix + 1 - kx even: ky = 1 (output row qy) when py = 0, and
+// ky = 0 (row qy + 1) or ky = 2 (row qy) when py = 1; likewise along x.  Each
+// parity class (blockIdx.z = 2 py + px) is then a dense GEMM with rows
+// m = (b, qy, qx), columns n = input channel and reduction k = (tap, o) over
+// its 1, 2 or 4 taps x Cout: none of the zero taps of the full 3x3 im2col is
+// loaded or multiplied.  Operands are split into BF16 hi + lo parts (three
+// MMAs, as in mma_gemm_kernel<true, ...>).
+struct DgradPar {
+    const float *dz;  // [B][Cout][So][So]
+    const float *w;   // [Cout][Cin][3][3]
+    float *dact;      // [B][Cin][2 So][2 So]
+    int Cout, Cin, So, M;  // M = B So So rows per class
+};
+
+__global__ void __launch_bounds__(kGT) dgrad_kernel(const DgradPar p)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[2][64][40];
+    __shared__ __align__(16) __nv_bfloat16 Bs[2][64][40];
+    const int cls = blockIdx.z, py = cls >> 1, px = cls & 1, ntx = px ? 2 : 1;
+    const int Kd = (py ? 2 : 1) * ntx * p.Cout;
+    const int m0 = blockIdx.x * 64;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int g = lane >> 2, t = lane & 3;
+    const int lr = tid >> 1, lk = (tid & 1) * 16;  // loader: tile row and first k
+    const int m = m0 + lr, P = p.So * p.So;
+    const bool mvalid = m < p.M, nvalid = lr < p.Cin;
+    int b = 0, qy = 0, qx = 0;
+    if (mvalid) {
+        b = m / P;
+        const int rr = m - b * P;
+        qy = rr / p.So;
+        qx = rr - qy * p.So;
+    }
+    const float *dzb = p.dz + static_cast<size_t>(b) * p.Cout * P;
+    const float *wn_ = p.w + static_cast<size_t>(nvalid ? lr : 0) * 9;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    for (int k0 = 0; k0 < Kd; k0 += 32) {
+        const int k = k0 + lk;
+        int tap = k / p.Cout, o = k - tap * p.Cout;
+        float va[16], vb[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const bool kin = k + q < Kd;
+            const int ty = ntx == 2 ? tap >> 1 : tap, tx = ntx == 2 ? tap & 1 : 0;
+            const int ky = py ? (ty == 0 ? 0 : 2) : 1, kx = px ? (tx == 0 ? 0 : 2) : 1;
+            const int oy = qy + (py && ty == 0 ? 1 : 0), ox = qx + (px && tx == 0 ? 1 : 0);
+            const bool ok = mvalid && kin && oy < p.So && ox < p.So;
+            va[q] = ok ? __ldg(dzb + static_cast<size_t>(o) * P + oy * p.So + ox) : 0.f;
+            vb[q] = nvalid && kin ? __ldg(wn_ + static_cast<size_t>(o) * p.Cin * 9 + ky * 3 + kx) : 0.f;
+            if (++o == p.Cout) {
+                o = 0;
+                ++tap;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+            const __nv_bfloat162 ha = __floats2bfloat162_rn(va[q], va[q + 1]);
+            const __nv_bfloat162 hb = __floats2bfloat162_rn(vb[q], vb[q + 1]);
+            *reinterpret_cast<__nv_bfloat162 *>(&As[0][lr][lk + q]) = ha;
+            *reinterpret_cast<__nv_bfloat162 *>(&Bs[0][lr][lk + q]) = hb;
+            *reinterpret_cast<__nv_bfloat162 *>(&As[1][lr][lk + q]) =
+                __floats2bfloat162_rn(va[q] - __low2float(ha), va[q + 1] - __high2float(ha));
+            *reinterpret_cast<__nv_bfloat162 *>(&Bs[1][lr][lk + q]) =
+                __floats2bfloat162_rn(vb[q] - __low2float(hb), vb[q + 1] - __high2float(hb));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 32; kk += 16) {
+            uint32_t a[2][2][4], bb[2][4][2];
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi) {
+                    const int r = wm + mi * 16 + g;
+                    a[pp][mi][0] = *reinterpret_cast<const uint32_t *>(&As[pp][r][kk + 2 * t]);
+                    a[pp][mi][1] = *reinterpret_cast<const uint32_t *>(&As[pp][r + 8][kk + 2 * t]);
+                    a[pp][mi][2] = *reinterpret_cast<const uint32_t *>(&As[pp][r][kk + 8 + 2 * t]);
+                    a[pp][mi][3] = *reinterpret_cast<const uint32_t *>(&As[pp][r + 8][kk + 8 + 2 * t]);
+                }
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) {
+                    const int n = wn + ni * 8 + g;
+                    bb[pp][ni][0] = *reinterpret_cast<const uint32_t *>(&Bs[pp][n][kk + 2 * t]);
+                    bb[pp][ni][1] = *reinterpret_cast<const uint32_t *>(&Bs[pp][n][kk + 8 + 2 * t]);
+                }
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) {
+                    mma_bf16(acc[mi][ni], a[1][mi], bb[0][ni]);
+                    mma_bf16(acc[mi][ni], a[0][mi], bb[1][ni]);
+                    mma_bf16(acc[mi][ni], a[0][mi], bb[0][ni]);
+                }
+        }
+        __syncthreads();
+    }
+    const int S = 2 * p.So;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2) {
+            const int mm = m0 + wm + mi * 16 + g + 8 * q2;
+            if (mm >= p.M) continue;
+            const int bo = mm / P, rr = mm - bo * P, oy = rr / p.So, ox = rr - oy * p.So;
+            const size_t pix = static_cast<size_t>(2 * oy + py) * S + 2 * ox + px;
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+                for (int q1 = 0; q1 < 2; ++q1) {
+                    const int n = wn + ni * 8 + 2 * t + q1;
+                    if (n < p.Cin)
+                        p.dact[(static_cast<size_t>(bo) * p.Cin + n) * S * S + pix] = acc[mi][ni][2 * q2 + q1];
+                }
+        }
 }
 
 // Fixed-order sum over the NW warps of a block; every thread gets the total.
@@ -1037,9 +1128,9 @@ extern "C" svdlut_status svdlut_generator_backward(int K, const float *weights, 
         if (i == 0) break;
         // input gradient, then InstanceNorm + LeakyReLU backward of layer i-1
         float *dact = w + wl.dact;
-        st = gemm<true, true>(B * S * S, Cin, Cout * 9, 1, DgradA{dz, Cout, S, So}, DgradB{weights + L.conv_w[i], Cin},
-                  DgradOut{dact, Cin, S}, s);
-        if (st != SVDLUT_OK) return st;
+        dgrad_kernel<<<dim3((B * So * So + 63) / 64, 1, 4), kGT, 0, s>>>(
+            DgradPar{dz, weights + L.conv_w[i], dact, Cout, Cin, So, B * So * So});
+        SVDLUT_CUDA_TRY(cudaGetLastError());
         const int j = i - 1;
         float *dz_next = dz == w + wl.dz[0] ? w + wl.dz[1] : w + wl.dz[0];
         in_bwd_sums_kernel<<<B * Cin, 256, 0, s>>>(dact, w + wl.r[j], w + wl.mean[j], w + wl.rstd[j], S * S,
