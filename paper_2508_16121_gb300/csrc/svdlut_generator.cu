@@ -79,12 +79,13 @@ inline size_t act_size(int B, int i) { return static_cast<size_t>(B) * kCh[i + 1
 
 // Weight gradient of conv i: the sum over the batch's output pixels is cut
 // into chunks of wgrad_chunk_px pixels (one GEMM slice each, a multiple of the
-// 32-wide K step) so that output tiles x chunks cover the SMs about twice.
+// 32-wide K step) so that output tiles x chunks give about four resident
+// CTAs per SM.
 inline int wgrad_chunk_px(int B, int i)
 {
     const int pix = B * kSz[i + 1] * kSz[i + 1];
     const int tiles = ((kCh[i + 1] + 63) / 64) * ((kCh[i] * 9 + 1 + 63) / 64);
-    const int want = std::max(1, (2 * 152 + tiles - 1) / tiles);
+    const int want = std::max(1, (4 * 152 + tiles - 1) / tiles);
     const int px = (pix + want - 1) / want;
     return std::max(32, (px + 31) / 32 * 32);
 }
