@@ -95,6 +95,33 @@ svdlut_status svdlut_apply(const svdlut_dims *dims, const svdlut_params *params,
                            svdlut_stream_t stream);
 
 /*
+ * svdlut_apply_host -- svdlut_apply on images in HOST memory.
+ *  - Page-locked (pinned, cudaHostAlloc / cudaHostRegister) x_host and y_host
+ *    are mapped into the GPU's address space: the kernel reads and writes them
+ *    in place over the CPU-GPU link, no copies, ws unused (may be NULL).
+ *  - Otherwise each image is cut into row bands; the upload of a band, the
+ *    transform of the previous one and the download of the one before run
+ *    concurrently, on two copy streams owned by the library (created once per
+ *    device) and on `stream` for the transform.  The copy streams fork from
+ *    `stream` at the start and join it at the end.
+ * Either way the call is ordered on `stream` like svdlut_apply (and can be
+ * captured in a CUDA graph); y_host is complete when `stream` has reached the
+ * end of the call.
+ *   x_host, y_host  host memory, [B][3][H][W] of dtype, must not overlap
+ *   params          DEVICE pointers, as for svdlut_apply
+ *   ws, ws_bytes    pageable case: device workspace of
+ *                   svdlut_apply_host_workspace_size() bytes, 256-byte aligned
+ *                   (device copies of x and y)
+ * Errors: those of svdlut_apply; WORKSPACE when ws is needed and missing or
+ * too small.  Calls on one device are serialised on the host (the copy streams
+ * are shared).
+ */
+svdlut_status svdlut_apply_host(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
+                                svdlut_dtype dtype, const void *x_host, void *y_host, void *ws, size_t ws_bytes,
+                                svdlut_stream_t stream);
+size_t svdlut_apply_host_workspace_size(int B, int H, int W, svdlut_dtype dtype);
+
+/*
  * One image of a ragged batch for svdlut_apply_batched: its size, transform
  * sizes and parameters (the svdlut_params layouts without the batch axis),
  * and device pointers to its [3][H][W] input and output.

@@ -92,6 +92,53 @@ def apply(x, params, out=None, stream=None):
     return y[0] if squeeze else y
 
 
+_host_ws = {}
+
+
+def apply_host(x, params, out=None, stream=None):
+    """Fused apply on host images (svdlut_apply_host): x is a CPU tensor
+    [B,3,H,W] or [3,H,W] (float32 or uint8, contiguous), params are CUDA
+    tensors as for apply.  Pinned x and out are read and written in place by
+    the kernel over the CPU-GPU link; pageable ones go through banded copies
+    overlapped with the transform.  The result (a CPU tensor, pinned when
+    allocated here) is complete once `stream` (default: the current stream)
+    has reached the end of the call."""
+    torch = _torch()
+    squeeze = x.dim() == 3
+    xb = x.unsqueeze(0) if squeeze else x
+    if xb.dim() != 4 or xb.shape[1] != 3:
+        raise ValueError("x must be [B,3,H,W] or [3,H,W]")
+    if xb.is_cuda or not xb.is_contiguous():
+        raise ValueError("x must be a contiguous host tensor")
+    if xb.dtype == torch.float32:
+        dt = _lib.F32
+    elif xb.dtype == torch.uint8:
+        dt = _lib.U8
+    else:
+        raise ValueError("x must be float32 or uint8")
+    B, _, H, W = xb.shape
+    d = dims_of(params)
+    p = _param_struct(params, B, d)
+    y = torch.empty(xb.shape, dtype=xb.dtype, pin_memory=True) if out is None else (out.unsqueeze(0) if squeeze else out)
+    if y.shape != xb.shape or y.dtype != xb.dtype or y.is_cuda or not y.is_contiguous():
+        raise ValueError("out must be a host tensor matching x in shape and dtype")
+    lib = _lib.load()
+    sp = _stream_ptr(stream)
+    ws_ptr, ws_bytes = None, 0
+    if not (xb.is_pinned() and y.is_pinned()):  # pinned frames are used in place, no workspace
+        need = lib.svdlut_apply_host_workspace_size(B, H, W, dt)
+        dev = next(iter(params.values())).device
+        key = (str(dev), sp.value)  # one workspace per device and stream: calls on one stream are ordered
+        ws = _host_ws.get(key)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=dev)
+            _host_ws[key] = ws
+        ws_ptr, ws_bytes = ws.data_ptr(), ws.numel()
+    _lib.check(lib.svdlut_apply_host(ctypes.byref(d), ctypes.byref(p), B, H, W, dt, ctypes.c_void_p(xb.data_ptr()),
+                                     ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(ws_ptr), ws_bytes, sp))
+    return y[0] if squeeze else y
+
+
 def to_device(params, device="cuda"):
     """numpy / torch parameter dict -> contiguous float32 tensors on device."""
     torch = _torch()

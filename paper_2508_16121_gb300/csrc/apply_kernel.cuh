@@ -44,6 +44,7 @@ struct ImgDesc {
     const float *U, *S, *V, *lw, *gxy, *gxc, *gyc, *gw;
     int H, W;
     int D, R, K, Dsx, Dsy, Dsc;
+    int y_begin, y_end;  // rows processed: [y_begin, y_end) of the H-row image
     int strips;       // column strips of kTileW pixels
     int BH;           // block height (rows)
     int block_begin;  // first global block index of this image
@@ -225,7 +226,7 @@ __host__ __device__ inline int prologue_floats_n(int D, int R, int pairs)
 
 __device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, float *misc, int tmp_floats)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int D = d.D, R = d.R, Rp = padded_rank(R), DR = D * R, DRp = D * Rp, Dm1 = D - 1;
     // all nine tables' factors at once when they fit (one global round trip)
     const int pairs_at_once = prologue_floats_n(D, R, 3) <= tmp_floats ? 3 : 1;
@@ -304,8 +305,8 @@ __device__ __forceinline__ BlockGeom block_geom(const ImgDesc &d, int lb, int nv
     BlockGeom g;
     const int band = lb / d.strips, strip = lb - band * d.strips;
     g.x0 = strip * kTileW;
-    g.y0 = band * d.BH;
-    g.rows = min(d.BH, d.H - g.y0);
+    g.y0 = d.y_begin + band * d.BH;
+    g.rows = min(d.BH, d.y_end - g.y0);
     const int x1 = min(g.x0 + kTileW - 1, d.W - 1), y1 = g.y0 + g.rows - 1;
     int ixhi, iyhi;
     float unused;
@@ -545,10 +546,10 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         const int band = lb / d.strips, strip = lb - band * d.strips;
         int x;
         const int n = lane_px(d.W, strip * kTileW, x);
-        const int y = band * d.BH + row;
+        const int y = d.y_begin + band * d.BH + row;
         const size_t plane = static_cast<size_t>(d.H) * d.W;
         const T *src = static_cast<const T *>(d.x) + static_cast<size_t>(y) * d.W + x;
-        const bool ok = row < d.BH && y < d.H && n > 0;
+        const bool ok = row < d.BH && y < d.y_end && n > 0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if constexpr (kStride) dst[c] = ok ? PixIO<T>::load_s(src + c * plane, n) : Raw();

@@ -3,6 +3,8 @@
 
 #include <algorithm>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "apply_kernel.cuh"
 
@@ -47,15 +49,17 @@ template <int N>
 svdlut_status plan_uniform(LaunchArgs<N> &a, int sm_count, size_t smem_limit, size_t *smem_out)
 {
     const ImgDesc &e0 = a.img[0];
-    const int H = e0.H, W = e0.W, strips = (W + kTileW - 1) / kTileW;
-    const int max_bands = std::max(1, (H + kMinBlockH - 1) / kMinBlockH);
+    // rows to cover (a row range of the image for banded calls); grid
+    // spacing still follows the full image height H
+    const int H = e0.H, W = e0.W, rows = e0.y_end - e0.y_begin, strips = (W + kTileW - 1) / kTileW;
+    const int max_bands = std::max(1, (rows + kMinBlockH - 1) / kMinBlockH);
     int best = -1;
     double best_score = -1e30;
     const int nvx = span_bound(kTileW, W, e0.Dsx);
     const int fixed = lcell_floats(e0.D) + kMiscFloats;
     const int pro = prologue_floats_n(e0.D, e0.R, 1);  // required; all-pairs-at-once is optional
     for (int bands = 1; bands <= max_bands; ++bands) {
-        const int BH = (H + bands - 1) / bands;
+        const int BH = (rows + bands - 1) / bands;
         const int need = fixed + std::max(pro, block_floats(nvx, span_bound(BH, H, e0.Dsy), e0.Dsc, BH));
         if (sizeof(float) * static_cast<size_t>(need) > smem_limit) continue;
         const long long T = static_cast<long long>(a.n) * strips * bands;
@@ -72,8 +76,8 @@ svdlut_status plan_uniform(LaunchArgs<N> &a, int sm_count, size_t smem_limit, si
         return fail(SVDLUT_ERR_UNSUPPORTED,
                     "grid slices of a %dx%d block do not fit in shared memory (%zu bytes): grid vertices too "
                     "dense or D_t/rank too large", kTileW, kMinBlockH, smem_limit);
-    const int BH = (H + best - 1) / best;
-    const int bands = (H + BH - 1) / BH;
+    const int BH = (rows + best - 1) / best;
+    const int bands = (rows + BH - 1) / BH;
     for (int i = 0; i < a.n; ++i) {
         a.img[i].strips = strips;
         a.img[i].BH = BH;
@@ -87,20 +91,27 @@ svdlut_status plan_uniform(LaunchArgs<N> &a, int sm_count, size_t smem_limit, si
     return SVDLUT_OK;
 }
 
+// Opts kernel `fn` into max_smem bytes of dynamic shared memory once per
+// device.  Keyed by the kernel's host address: every translation unit that
+// launches a kernel template has its own instance of it.
+inline svdlut_status allow_smem_once(const void *fn, int max_smem, int device)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<int, const void *>> done;
+    std::lock_guard<std::mutex> g(mu);
+    for (const auto &e : done)
+        if (e.first == device && e.second == fn) return SVDLUT_OK;
+    SVDLUT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    done.emplace_back(device, fn);
+    return SVDLUT_OK;
+}
+
 template <typename T, int N, bool DX>
 svdlut_status launch_apply_t(LaunchArgs<N> &a, size_t smem, int sm_count, int max_smem, int device,
                              cudaStream_t s, int grid)
 {
-    static std::mutex mu;
-    static bool attr_set[64] = {};
-    {
-        std::lock_guard<std::mutex> g(mu);
-        if (!attr_set[device]) {
-            SVDLUT_CUDA_TRY(
-                cudaFuncSetAttribute(apply_kernel<T, N, DX>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-            attr_set[device] = true;
-        }
-    }
+    svdlut_status st = allow_smem_once(reinterpret_cast<const void *>(apply_kernel<T, N, DX>), max_smem, device);
+    if (st != SVDLUT_OK) return st;
     if (grid <= 0) grid = std::min(a.total_blocks, sm_count);
     grid = std::max(1, std::min(grid, a.total_blocks));
     apply_kernel<T, N, DX><<<grid, kThreads, smem, s>>>(a);

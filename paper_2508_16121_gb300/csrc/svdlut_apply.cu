@@ -53,6 +53,8 @@ ImgDesc make_desc(const svdlut_dims *d, const svdlut_params *p, int b, int H, in
     e.gw = p->grid_w ? p->grid_w + b * param_stride(d, 7) : nullptr;
     e.H = H;
     e.W = W;
+    e.y_begin = 0;
+    e.y_end = H;
     e.D = d->D_t;
     e.R = d->rank;
     e.K = d->K;
