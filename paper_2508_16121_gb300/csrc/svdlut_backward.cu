@@ -209,11 +209,19 @@ struct GridPlan {
     int BH, bands, nblk;   // per image
     int nvx, nvy, rpw, nvyw;  // maxima
     int blk_stride;        // floats per block partial
+    int bins;              // 1: yc through lane-private bins, 0: warp scatter (large Dsc)
 };
 
-__host__ __device__ inline int grid_warp_floats(int nvx, int nvyw, int Dsc)
+// Per-warp floats: the xy, xc and yc tables, then the lane-private yc bins
+// [3][Dsc][33] (one column per lane, padded so that a lane summing a row of
+// bins reads 32 different banks).
+__host__ __device__ inline int grid_table_floats(int nvx, int nvyw, int Dsc)
 {
     return (3 * nvyw * nvx + 3 * nvx * Dsc + 3 * nvyw * Dsc + 3) & ~3;
+}
+__host__ __device__ inline int grid_warp_floats(int nvx, int nvyw, int Dsc, int bins)
+{
+    return grid_table_floats(nvx, nvyw, Dsc) + (bins ? 3 * Dsc * 33 : 0);
 }
 
 __host__ __device__ inline int grid_block_floats(int nvx, int nvy, int Dsc)
@@ -251,11 +259,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     const int nvyw = min(min(wyhi + 1, a.Dsy - 1) - wylo + 1, gp.nvyw);
 
-    const int wf = grid_warp_floats(gp.nvx, gp.nvyw, Dsc);
+    const int wf = grid_warp_floats(gp.nvx, gp.nvyw, Dsc, gp.bins);
     float *wt = sm + warp * wf;
     float *txy = wt;                             // [nvyw][nvx][3]
     float *txc = txy + 3 * gp.nvyw * gp.nvx;     // [3][nvx][Dsc]
     float *tyc = txc + 3 * gp.nvx * Dsc;         // [3][nvyw][Dsc]
+    float *hb = wt + grid_table_floats(gp.nvx, gp.nvyw, Dsc);  // [3][Dsc][33] yc bins of this row
     for (int e = threadIdx.x; e < kWarps * wf; e += kThreads) sm[e] = 0.f;
     __syncthreads();
 
@@ -341,13 +350,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                                      {gy[c] * (1.f - dx) * ec}, {gy[c] * dx * ec}};
                     warp_scatter<1>(txc + c * gp.nvx * Dsc, act ? ixl[k] * Dsc + jc : -1, Dsc, 1, v);
                 }
-                {   // yc: corners (iy, j), (iy+1, j), (iy, j+1), (iy+1, j+1)
+                if (gp.bins) {
+                    // yc: the row (hence dy and the y-cell) is common to the warp, so
+                    // the intensity weights go to this lane's own bins (no conflicts)
+                    // and are spread over the corners (iy, iy+1) once per row
+                    hb[(c * Dsc + jc) * 33 + lane] += gy[c] * (1.f - ec);
+                    hb[(c * Dsc + jc + 1) * 33 + lane] += gy[c] * ec;
+                } else {  // yc: corners (iy, j), (iy+1, j), (iy, j+1), (iy+1, j+1)
                     float v[4][1] = {{gy[c] * (1.f - dy) * (1.f - ec)}, {gy[c] * dy * (1.f - ec)},
                                      {gy[c] * (1.f - dy) * ec}, {gy[c] * dy * ec}};
                     warp_scatter<1>(tyc + c * gp.nvyw * Dsc, act ? iyw * Dsc + jc : -1, Dsc, 1, v);
                 }
             }
         }
+        // yc bins of this row: lane-ordered sums, spread over rows iy, iy+1
+        __syncwarp();
+        for (int e = lane; gp.bins && e < 3 * Dsc; e += 32) {
+            float *col = hb + e * 33;
+            float sum = 0.f;
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) {
+                sum += col[l];
+                col[l] = 0.f;
+            }
+            const int c = e / Dsc, j = e - c * Dsc;
+            float *t0 = tyc + (c * gp.nvyw + iyw) * Dsc + j;
+            t0[0] = fmaf(1.f - dy, sum, t0[0]);
+            t0[Dsc] = fmaf(dy, sum, t0[Dsc]);
+        }
+        __syncwarp();
     }
     if (iyw_acc >= 0) flush_xy();
     // the warps' first vertex row relative to the block's
@@ -648,15 +679,17 @@ static svdlut_status plan_backward(const svdlut_dims *d, int B, int H, int W, in
     int best = -1;
     double best_score = -1e30;
     GridPlan bestgp{};
+    for (int bins = 1; bins >= 0 && best < 0; --bins)
     for (int bands = 1; bands <= max_bands; ++bands) {
         GridPlan gp{};
+        gp.bins = bins;
         gp.BH = (H + bands - 1) / bands;
         gp.bands = (H + gp.BH - 1) / gp.BH;
         gp.nvx = span_bound(kTileW, W, d->Dsx);
         gp.nvy = span_bound(gp.BH, H, d->Dsy);
         gp.rpw = (gp.BH + kWarps - 1) / kWarps;
         gp.nvyw = span_bound(gp.rpw, H, d->Dsy);
-        const size_t need = sizeof(float) * static_cast<size_t>(kWarps) * grid_warp_floats(gp.nvx, gp.nvyw, Dsc);
+        const size_t need = sizeof(float) * static_cast<size_t>(kWarps) * grid_warp_floats(gp.nvx, gp.nvyw, Dsc, bins);
         if (need + 256 > smem_limit) continue;  // + the kernel's static row offsets
         const long long T = static_cast<long long>(B) * strips * gp.bands;
         const double waves = std::ceil(static_cast<double>(T) / sm_count - 1e-9);
@@ -672,7 +705,8 @@ static svdlut_status plan_backward(const svdlut_dims *d, int B, int H, int W, in
     bestgp.nblk = strips * bestgp.bands;
     bestgp.blk_stride = grid_block_floats(bestgp.nvx, bestgp.nvy, Dsc);
     pl->gp = bestgp;
-    pl->grid_smem = sizeof(float) * static_cast<size_t>(kWarps) * grid_warp_floats(bestgp.nvx, bestgp.nvyw, Dsc);
+    pl->grid_smem =
+        sizeof(float) * static_cast<size_t>(kWarps) * grid_warp_floats(bestgp.nvx, bestgp.nvyw, Dsc, bestgp.bins);
     size_t off = 0;
     pl->off_lut = off;
     off = align256(off + sizeof(float) * static_cast<size_t>(B) * pl->P * 9 * D * D);
