@@ -144,17 +144,18 @@ __global__ void __launch_bounds__(kLutThreads, 1)
     float dysum[3] = {0.f, 0.f, 0.f};
     for (int u = grp; u < units; u += kLutWarps / 3) {
         const int row = r0 + u / a.strips, strip = u - (u / a.strips) * a.strips;
-        const int x = strip * kTileW + lane * 4;
-        const int n = min(4, a.W - x);
+        // pixel k of the lane: column x + 32 k (a warp-wide access covers 32
+        // adjacent pixels, whose cells often coincide: fewer scatter groups)
+        const int x = strip * kTileW + lane;
+        const int n = x < a.W ? min(4, (a.W - x + 31) >> 5) : 0;
         const size_t o = static_cast<size_t>(row) * a.W + x;
         float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa, g0 = pa, g1 = pa, g2 = pa;
         if (n > 0) {
-            const bool v = a.vec && n == 4;
-            pa = PixIO<float>::load(xb + A * plane + o, n, v);
-            pb = PixIO<float>::load(xb + Bx * plane + o, n, v);
-            g0 = PixIO<float>::load(gb + o, n, v);
-            g1 = PixIO<float>::load(gb + plane + o, n, v);
-            g2 = PixIO<float>::load(gb + 2 * plane + o, n, v);
+            pa = PixIO<float>::load_s(xb + A * plane + o, n);
+            pb = PixIO<float>::load_s(xb + Bx * plane + o, n);
+            g0 = PixIO<float>::load_s(gb + o, n);
+            g1 = PixIO<float>::load_s(gb + plane + o, n);
+            g2 = PixIO<float>::load_s(gb + 2 * plane + o, n);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
