@@ -142,6 +142,18 @@ typedef struct {
 } svdlut_launch_cfg;
 
 /*
+ * svdlut_apply_cfg -- svdlut_apply with a launch shape: cfg->ctas > 0 plans
+ * the work for and launches that many persistent CTAs (at most one per SM),
+ * leaving the other SMs to concurrent work on other streams, e.g. the factor
+ * generator of the next batch; cfg->block_px is not used (the blocks are
+ * planned for the CTA count).  cfg may be NULL (= svdlut_apply).
+ * Errors: those of svdlut_apply; INVALID_ARG for a negative CTA count.
+ */
+svdlut_status svdlut_apply_cfg(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
+                               svdlut_dtype dtype, const void *x, void *y, const svdlut_launch_cfg *cfg,
+                               svdlut_stream_t stream);
+
+/*
  * svdlut_apply_batched -- the fused transform of svdlut_apply (Eq. 10) over n
  * images of uneven sizes, each with its own transform, in one persistent
  * launch per 64 images.  imgs is a HOST array of n descriptors (read during the

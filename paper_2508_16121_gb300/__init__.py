@@ -61,11 +61,12 @@ def _stream_ptr(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def apply(x, params, out=None, stream=None):
+def apply(x, params, out=None, stream=None, ctas=None):
     """Fused SVDLUT apply (Eq. 10).  x: CUDA tensor [B,3,H,W] or [3,H,W],
     float32 or uint8, contiguous.  params: dict of float32 CUDA tensors with
     an optional leading batch axis (see include/svdlut.h).  Returns y with
-    x's shape and dtype."""
+    x's shape and dtype.  ctas: persistent CTAs to use (svdlut_apply_cfg;
+    default one per SM)."""
     torch = _torch()
     squeeze = x.dim() == 3
     xb = x.unsqueeze(0) if squeeze else x
@@ -86,9 +87,15 @@ def apply(x, params, out=None, stream=None):
     if y.shape != xb.shape or y.dtype != xb.dtype or not y.is_contiguous():
         raise ValueError("out must match x in shape and dtype")
     lib = _lib.load()
-    _lib.check(lib.svdlut_apply(ctypes.byref(d), ctypes.byref(p), B, H, W, dt,
-                                ctypes.c_void_p(xb.data_ptr()), ctypes.c_void_p(y.data_ptr()),
-                                _stream_ptr(stream)))
+    if ctas is None:
+        _lib.check(lib.svdlut_apply(ctypes.byref(d), ctypes.byref(p), B, H, W, dt,
+                                    ctypes.c_void_p(xb.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                    _stream_ptr(stream)))
+    else:
+        cfg = _lib.LaunchCfg(0, int(ctas))
+        _lib.check(lib.svdlut_apply_cfg(ctypes.byref(d), ctypes.byref(p), B, H, W, dt,
+                                        ctypes.c_void_p(xb.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                        ctypes.byref(cfg), _stream_ptr(stream)))
     return y[0] if squeeze else y
 
 

@@ -72,9 +72,27 @@ ImgDesc make_desc(const svdlut_dims *d, const svdlut_params *p, int b, int H, in
 
 using namespace svdlut;
 
+static svdlut_status apply_impl(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
+                                svdlut_dtype dtype, const void *x, void *y, int ctas, svdlut_stream_t stream);
+
 extern "C" svdlut_status svdlut_apply(const svdlut_dims *dims, const svdlut_params *params, int B, int H,
                                       int W, svdlut_dtype dtype, const void *x, void *y,
                                       svdlut_stream_t stream)
+{
+    return apply_impl(dims, params, B, H, W, dtype, x, y, 0, stream);
+}
+
+extern "C" svdlut_status svdlut_apply_cfg(const svdlut_dims *dims, const svdlut_params *params, int B, int H,
+                                          int W, svdlut_dtype dtype, const void *x, void *y,
+                                          const svdlut_launch_cfg *cfg, svdlut_stream_t stream)
+{
+    clear_error();
+    if (cfg && cfg->ctas < 0) return fail(SVDLUT_ERR_INVALID_ARG, "negative CTA count");
+    return apply_impl(dims, params, B, H, W, dtype, x, y, cfg ? cfg->ctas : 0, stream);
+}
+
+static svdlut_status apply_impl(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
+                                svdlut_dtype dtype, const void *x, void *y, int ctas, svdlut_stream_t stream)
 {
     clear_error();
     svdlut_status st = check_dims(dims);
@@ -92,14 +110,16 @@ extern "C" svdlut_status svdlut_apply(const svdlut_dims *dims, const svdlut_para
 
     DeviceInfo di;
     if ((st = device_info(&di)) != SVDLUT_OK) return st;
+    const int n_cta = ctas > 0 ? std::min(ctas, di.sm_count) : di.sm_count;  // persistent CTAs to plan for
     for (int b0 = 0; b0 < B; b0 += kPlainChunk) {
         LaunchArgs<kPlainChunk> a{};
         a.n = std::min(kPlainChunk, B - b0);
         for (int i = 0; i < a.n; ++i) a.img[i] = make_desc(dims, params, b0 + i, H, W, dtype, x, y);
         size_t smem = 0;
-        if ((st = plan_uniform(a, di.sm_count, static_cast<size_t>(di.max_smem_optin), &smem)) != SVDLUT_OK)
+        if ((st = plan_uniform(a, n_cta, static_cast<size_t>(di.max_smem_optin), &smem)) != SVDLUT_OK)
             return st;
-        if ((st = launch_apply(a, smem, dtype, reinterpret_cast<cudaStream_t>(stream), 0)) != SVDLUT_OK) return st;
+        if ((st = launch_apply(a, smem, dtype, reinterpret_cast<cudaStream_t>(stream), n_cta)) != SVDLUT_OK)
+            return st;
     }
     return SVDLUT_OK;
 }
