@@ -146,3 +146,18 @@ def test_4k_u8_sampled_rows(sv):
     ref = oracle.quantize_u8(oracle.forward(d, p, oracle.u8_to_unit(x8)))
     diff = np.abs(y8.astype(int) - ref.astype(int))
     assert diff.max() <= 1
+
+
+@pytest.mark.parametrize("ctas", [1, 7, 100, 152, 1000])
+def test_cta_cap_gives_identical_output(sv, ctas):
+    """svdlut_apply_cfg plans for a capped number of persistent CTAs; the
+    per-pixel arithmetic, hence every output bit, is unchanged."""
+    import torch
+    H, W = 300, 517
+    d = si.spatial_dims(H, W)
+    x, p = si.make_batch(si.config_seed(9), 2, H, W, d)
+    xt, pd = torch.from_numpy(x).cuda(), sv.to_device(p)
+    ref = sv.apply(xt, pd)
+    got = sv.apply(xt, pd, ctas=ctas)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
