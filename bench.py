@@ -159,7 +159,7 @@ class ClockSampler:
 
 def dist_init(backend=None):
     """One process per GPU under torchrun: (world, rank, local).  NCCL on a
-    GPU box; gloo when CUDA is absent (host-logic tests)."""
+    GPU machine; gloo when CUDA is absent (host-logic tests)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

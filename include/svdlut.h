@@ -36,7 +36,7 @@ typedef struct CUstream_st *svdlut_stream_t; /* same type as cudaStream_t */
 typedef enum {
     SVDLUT_OK = 0,
     SVDLUT_ERR_INVALID_ARG = 1, /* null pointer, bad size, misaligned pointer */
-    SVDLUT_ERR_UNSUPPORTED = 2, /* valid but beyond this build's limits      */
+    SVDLUT_ERR_UNSUPPORTED = 2, /* valid but beyond the library's size limits */
     SVDLUT_ERR_CUDA = 3,        /* a CUDA call or launch failed              */
     SVDLUT_ERR_WORKSPACE = 4,   /* workspace missing or too small            */
     SVDLUT_ERR_TIMEOUT = 5      /* a bounded device-side wait ran out        */

@@ -37,7 +37,7 @@ inline svdlut_status cuda_fail(cudaError_t e, const char *where)
         if (_e != cudaSuccess) return ::svdlut::cuda_fail(_e, #expr);  \
     } while (0)
 
-// ---- limits of this build ----
+// ---- size limits of the library ----
 constexpr int kMaxDt = 33;
 constexpr int kMaxK = 48;
 constexpr int kMaxDsc = 64;
