@@ -14,9 +14,11 @@
 //    channels: 3 float4 per cell and pair.
 //  - Per block: the grid slices of the block's footprint are summed over the
 //    grids that feed each output channel (grid k feeds channel k mod 3, Supp.
-//    Eq. 22) with their weights (Eq. 21); the xc slice is packed as
-//    (x, x+1) x (j, j+1) corners.
-//  - Per row: a warp interpolates the xy and yc slices along y for its row.
+//    Eq. 22) with their weights (Eq. 21); the xc slice is stored per x-cell
+//    and intensity cell in slope form (value, slope along intensity, and
+//    their differences to the next x-cell).
+//  - Per row: a warp interpolates the xy and yc slices along y for its row
+//    (yc as value and slope along intensity).
 //  - Per pixel: 9 LDS.128 for the three LUT pairs, 2 LDS.128 (xy), 3 LDS.128
 //    (xc) and 3 LDS.64 (yc).  Row data is loaded one row ahead, across block
 //    boundaries.
@@ -325,10 +327,12 @@ __device__ __forceinline__ BlockGeom block_geom(const ImgDesc &d, int lb, int nv
 //   fxy [3][nvy][nvx], fxc [3][nvx][Dsc], fyc [3][nvy][Dsc]   folded grid slices
 //   coli [kTileW] int, cold [kTileW]                           column cells
 //   rowi [bh] int, rowd [bh]                                    row cells
-//   pxc [3][nvx-1][Dsc] float4   xc corners (x, x+1) x (j, j+1); row stride Dsc
-//                                (one padding entry) to spread banks
+//   pxc [3][nvx-1][Dsc] float4   xc slope form of x-cell ix, intensity cell j
+//                                (see block_phase_b); row stride Dsc (one
+//                                padding entry) to spread banks
 //   per warp: rxy [nvx] float4 (xy interpolated along y for the warp's row),
-//             ryc [3][Dsc-1] float2 (yc interpolated along y, (j, j+1))
+//             ryc [3][Dsc-1] float2 (yc interpolated along y: value at j and
+//             slope to j + 1)
 struct BlockBufs {
     float *fxy, *fxc, *fyc;
     int *coli, *rowi;
