@@ -261,6 +261,17 @@ def run_ours(args, world, rank, local):
                                                          stream) / 1e3), 1)
         del xr_t, yr_t
 
+    # ---- the paper's own transform sizes (K=6 grids of 17^3) on the same 4K image ----
+    dp = si.paper_dims()
+    xq, pq = si.make_batch(si.config_seed(1) + 11, 1, H, W, dp)
+    xq_t, pq_t = torch.from_numpy(xq).to(dev), svdlut.to_device(pq, dev)
+    yq_t = torch.empty_like(xq_t)
+    paper_ms = time_calls(lambda: svdlut.apply(xq_t, pq_t, out=yq_t), args.steps, stream)
+    paper_cfg = {"value": round(H * W / 1e6 / (paper_ms / 1e3), 1), "unit": "Mpix/s", "ms": round(paper_ms, 5),
+                 "GB/s": round(algo_bytes_apply(H, W, dp, 4) / (paper_ms / 1e3) / 1e9, 1),
+                 "workload": "1x3840x2160 FP32, D_t=33 rank 8, K=6 grids 17x17x17"}
+    del xq_t, yq_t
+
     # ---- ragged batch: 16 images 480p..4K, one graph-captured launch vs 16 plain calls ----
     batched = run_batched_variant(svdlut, torch, dev, stream, args)
 
@@ -327,6 +338,7 @@ def run_ours(args, world, rank, local):
                                      "ms": round(u8_ms, 5),
                                      "GB/s": round(algo_bytes_apply(H, W, d, 1) / (u8_ms / 1e3) / 1e9, 1)},
                      "f32_plain_4k_by_regime_Mpix/s": regimes,
+                     "f32_plain_4k_paper_grids": paper_cfg,
                      "batched_16_ragged": batched,
                      "backward_8x1080p": backward,
                      "learned_4x4k": learned},

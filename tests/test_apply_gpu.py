@@ -51,7 +51,8 @@ def test_f32_spatial_dims(sv, HW):
 
 
 @pytest.mark.parametrize("d", [si.paper_dims(), si.Dims(2, 1, 3, 2, 2, 2), si.Dims(17, 8, 8, 9, 5, 33),
-                               si.Dims(33, 33, 0, 2, 2, 2), si.Dims(5, 3, 1, 3, 4, 2), si.Dims(33, 8, 48, 17, 17, 33)])
+                               si.Dims(33, 33, 0, 2, 2, 2), si.Dims(5, 3, 1, 3, 4, 2), si.Dims(33, 8, 48, 17, 17, 33),
+                               si.Dims(33, 33, 48, 9, 7, 64)])  # the largest sizes the ABI accepts
 def test_f32_dims_variants(sv, d):
     x, p = si.make_batch(77, 1, 70, 260, d)
     check_f32(sv, d, x, p)

@@ -68,7 +68,8 @@ def test_backward_matches_oracle_spatial_dims(sv, HW):
 
 
 @pytest.mark.parametrize("d", [si.paper_dims(), si.Dims(2, 1, 3, 2, 2, 2), si.Dims(17, 8, 8, 9, 5, 33),
-                               si.Dims(33, 33, 0, 2, 2, 2), si.Dims(9, 3, 7, 3, 4, 5)])
+                               si.Dims(33, 33, 0, 2, 2, 2), si.Dims(9, 3, 7, 3, 4, 5),
+                               si.Dims(33, 33, 48, 9, 7, 64)])  # largest sizes: yc through the warp scatter
 def test_backward_dims_variants(sv, d):
     x, p = si.make_batch(310, 2, 45, 140, d)
     dy = si.make_upstream(311, x.shape)

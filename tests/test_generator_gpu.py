@@ -143,3 +143,18 @@ def test_adam_and_mse(sv):
     loss = sv.mse(torch.from_numpy(y).cuda(), torch.from_numpy(t).cuda(), dy)
     assert abs(float(loss) - np.mean((y.astype(np.float64) - t) ** 2)) <= 1e-6
     assert np.abs(dy.cpu().numpy() - 2 * (y - t) / 5000).max() <= 1e-9
+
+
+def test_forward_on_4k_frames_matches_oracle(sv):
+    """The inference workload's input size: 2 x 3840x2160 frames, bilinear
+    downsample to the 256x256 thumbnail included."""
+    import torch
+    K = 8
+    blob = make_blob(K, 120)
+    x = np.stack([si.make_image(np.random.default_rng(130 + j), 2160, 3840) for j in range(2)])
+    gen = gpu_gen(sv, K, blob, B=2)
+    out = gen.forward(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    ref, _ = G.forward(blob, x, K)
+    for k in ref:
+        assert rel(out[k].cpu().numpy().astype(np.float64), ref[k]) <= 2e-2, k
