@@ -79,6 +79,7 @@ extern "C" svdlut_status svdlut_apply(const svdlut_dims *dims, const svdlut_para
                                       int W, svdlut_dtype dtype, const void *x, void *y,
                                       svdlut_stream_t stream)
 {
+    SVDLUT_TRACE("svdlut_apply");
     return apply_impl(dims, params, B, H, W, dtype, x, y, 0, stream);
 }
 
@@ -86,6 +87,7 @@ extern "C" svdlut_status svdlut_apply_cfg(const svdlut_dims *dims, const svdlut_
                                           int W, svdlut_dtype dtype, const void *x, void *y,
                                           const svdlut_launch_cfg *cfg, svdlut_stream_t stream)
 {
+    SVDLUT_TRACE("svdlut_apply_cfg");
     clear_error();
     if (cfg && cfg->ctas < 0) return fail(SVDLUT_ERR_INVALID_ARG, "negative CTA count");
     return apply_impl(dims, params, B, H, W, dtype, x, y, cfg ? cfg->ctas : 0, stream);

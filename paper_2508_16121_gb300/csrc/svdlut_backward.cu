@@ -754,6 +754,7 @@ extern "C" svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_p
                                          const svdlut_grads *grads, void *ws, size_t ws_bytes,
                                          svdlut_stream_t stream)
 {
+    SVDLUT_TRACE("svdlut_backward");
     clear_error();
     svdlut_status st = check_backward_args(dims, params, B, H, W, x, dy);
     if (st != SVDLUT_OK) return st;

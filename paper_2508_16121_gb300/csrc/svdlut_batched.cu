@@ -124,6 +124,7 @@ extern "C" svdlut_status svdlut_apply_batched(const svdlut_image *imgs, int n, s
                                               const svdlut_launch_cfg *cfg, void *ws, size_t ws_bytes,
                                               svdlut_stream_t stream)
 {
+    SVDLUT_TRACE("svdlut_apply_batched");
     clear_error();
     if (!imgs || n < 1) return fail(SVDLUT_ERR_INVALID_ARG, "imgs is NULL or n=%d < 1", n);
     if (dtype != SVDLUT_F32 && dtype != SVDLUT_U8) return fail(SVDLUT_ERR_INVALID_ARG, "unknown dtype %d", dtype);
@@ -141,6 +142,7 @@ extern "C" svdlut_status svdlut_autotune_batched(const svdlut_image *imgs, int n
                                                  size_t ws_bytes, svdlut_stream_t stream, int reps,
                                                  svdlut_launch_cfg *best, float *best_ms)
 {
+    SVDLUT_TRACE("svdlut_autotune_batched");
     clear_error();
     if (!best) return fail(SVDLUT_ERR_INVALID_ARG, "best is NULL");
     if (!imgs || n < 1) return fail(SVDLUT_ERR_INVALID_ARG, "imgs is NULL or n=%d < 1", n);

@@ -1038,6 +1038,7 @@ extern "C" svdlut_status svdlut_generator_forward(int K, const float *weights, i
                                                   const svdlut_param_buffers *out, int training, uint64_t seed,
                                                   void *ws, size_t ws_bytes, svdlut_stream_t stream)
 {
+    SVDLUT_TRACE("svdlut_generator_forward");
     clear_error();
     svdlut_status st = gen_check(K, weights, B, ws, ws_bytes);
     if (st != SVDLUT_OK) return st;
@@ -1084,6 +1085,7 @@ extern "C" svdlut_status svdlut_generator_backward(int K, const float *weights, 
                                                    float *dweights, int training, uint64_t seed, void *ws,
                                                    size_t ws_bytes, svdlut_stream_t stream)
 {
+    SVDLUT_TRACE("svdlut_generator_backward");
     clear_error();
     svdlut_status st = gen_check(K, weights, B, ws, ws_bytes);
     if (st != SVDLUT_OK) return st;
@@ -1150,6 +1152,7 @@ extern "C" svdlut_status svdlut_generator_adam(float *weights, const float *grad
                                                float lr, float beta1, float beta2, float eps, int step,
                                                svdlut_stream_t stream)
 {
+    SVDLUT_TRACE("svdlut_generator_adam");
     clear_error();
     if (!weights || !grads || !m || !v || n == 0 || step < 1)
         return fail(SVDLUT_ERR_INVALID_ARG, "adam: null buffer, n = 0 or step < 1");
@@ -1164,6 +1167,7 @@ extern "C" svdlut_status svdlut_generator_adam(float *weights, const float *grad
 extern "C" svdlut_status svdlut_mse(const float *y, const float *target, size_t n, float *dy, float *loss, void *ws,
                                     size_t ws_bytes, svdlut_stream_t stream)
 {
+    SVDLUT_TRACE("svdlut_mse");
     clear_error();
     if (!y || !target || !loss || n == 0) return fail(SVDLUT_ERR_INVALID_ARG, "mse: null buffer or n = 0");
     const int nb = std::min(blocks_for(n), 1024);

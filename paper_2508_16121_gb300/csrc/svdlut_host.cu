@@ -92,6 +92,7 @@ extern "C" svdlut_status svdlut_apply_host(const svdlut_dims *dims, const svdlut
                                            svdlut_dtype dtype, const void *x_host, void *y_host, void *ws,
                                            size_t ws_bytes, svdlut_stream_t stream)
 {
+    SVDLUT_TRACE("svdlut_apply_host");
     clear_error();
     svdlut_status st = check_dims(dims);
     if (st != SVDLUT_OK) return st;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdarg>
 #include <cstdint>
@@ -36,6 +37,16 @@ inline svdlut_status cuda_fail(cudaError_t e, const char *where)
         cudaError_t _e = (expr);                                       \
         if (_e != cudaSuccess) return ::svdlut::cuda_fail(_e, #expr);  \
     } while (0)
+
+// ---- tracing: an NVTX range around each public entry point (a no-op unless
+// a profiler such as Nsight Systems is attached) ----
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define SVDLUT_TRACE(name) ::svdlut::NvtxRange svdlut_trace_range_(name)
 
 // ---- size limits of the library ----
 constexpr int kMaxDt = 33;

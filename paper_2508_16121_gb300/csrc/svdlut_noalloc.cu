@@ -47,6 +47,7 @@ extern "C" svdlut_status svdlut_backward_noalloc(const svdlut_dims *dims, const 
                                                  int H, int W, const float *x, const float *dy, float *dx,
                                                  const svdlut_grads *grads, svdlut_stream_t stream)
 {
+    SVDLUT_TRACE("svdlut_backward_noalloc");
     svdlut::clear_error();
     const svdlut_grads g0{};
     const svdlut_grads &g = grads ? *grads : g0;
