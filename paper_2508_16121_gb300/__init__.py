@@ -267,9 +267,33 @@ class Batch:
                                             _stream_ptr(stream)))
         return self.outs
 
-    def autotune(self, reps=5, stream=None):
+    def tune_key(self):
+        """Key of this batch's launch-shape choice: GPU model, dtype and the
+        per-image sizes and transform dims."""
+        torch = _torch()
+        name = torch.cuda.get_device_name(self.xs[0].device)
+        def dims_str(p):
+            d = dims_of(p)
+            return ",".join(str(getattr(d, n)) for n, _ in _lib.Dims._fields_)
+        shapes = ";".join(f"{x.shape[1]}x{x.shape[2]}:{dims_str(p)}" for x, p in zip(self.xs, self.params))
+        return f"{name}|{'u8' if self.dtype == _lib.U8 else 'f32'}|{shapes}"
+
+    def autotune(self, reps=5, stream=None, cache=None):
         """Time a set of block sizes on this batch (native autotuner) and keep
-        the fastest; returns (block_px, ms)."""
+        the fastest; returns (block_px, ms).  cache: path of a JSON file of
+        earlier choices keyed by tune_key() (default: $SVDLUT_AUTOTUNE_CACHE,
+        none if unset); a hit skips the timing and returns (block_px, None)."""
+        import json
+        import os
+        path = cache if cache is not None else os.environ.get("SVDLUT_AUTOTUNE_CACHE")
+        key = self.tune_key()
+        table = {}
+        if path and os.path.exists(path):
+            with open(path) as f:
+                table = json.load(f)
+            if key in table:
+                self.cfg = _lib.LaunchCfg(int(table[key]["block_px"]), int(table[key].get("ctas", 0)))
+                return self.cfg.block_px, None
         lib = _lib.load()
         best = _lib.LaunchCfg()
         ms = ctypes.c_float()
@@ -277,6 +301,12 @@ class Batch:
                                                ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
                                                _stream_ptr(stream), reps, ctypes.byref(best), ctypes.byref(ms)))
         self.cfg = best
+        if path:
+            table[key] = {"block_px": int(best.block_px), "ctas": int(best.ctas), "ms": float(ms.value)}
+            tmp = path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, path)
         return best.block_px, ms.value
 
 

@@ -148,3 +148,23 @@ def test_sixteen_ragged_images_benchmark_workload(sv):
     for (x, d, p), y in zip(items, ys):
         ref = sv.apply(torch.from_numpy(x).cuda(), sv.to_device(p)).cpu().numpy()
         assert np.abs(y - ref).max() <= 1e-6
+
+
+def test_autotune_cache_round_trip(sv, tmp_path):
+    """A tuned launch shape is stored under (GPU, dtype, sizes) and reused
+    without timing; the output is unchanged."""
+    import torch
+    items = si.make_ragged(seed=77, n=3, sizes=((640, 480), (1280, 720), (640, 480)))
+    xs = [torch.from_numpy(x).cuda() for x, _, _ in items]
+    ps = [sv.to_device(p) for _, _, p in items]
+    cache = str(tmp_path / "tune.json")
+    b1 = sv.Batch(xs, ps)
+    px1, ms1 = b1.autotune(reps=2, cache=cache)
+    assert ms1 is not None
+    y1 = [y.clone() for y in b1.run()]
+    b2 = sv.Batch(xs, ps)
+    px2, ms2 = b2.autotune(reps=2, cache=cache)
+    assert ms2 is None and px2 == px1
+    torch.cuda.synchronize()
+    for a, b in zip(y1, b2.run()):
+        assert torch.equal(a, b)
