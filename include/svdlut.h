@@ -311,6 +311,18 @@ svdlut_status svdlut_backward_noalloc(const svdlut_dims *dims, const svdlut_para
 /* Message of the last error raised on this thread ("" if none). */
 const char *svdlut_last_error(void);
 
+/*
+ * svdlut_check_report -- index-check status of a library built with
+ * -DSVDLUT_CHECK_BOUNDS (a debugging build in which the transform kernels
+ * test every shared-memory gather index, count the ones out of range and
+ * replace them by 0 instead of faulting).  Waits for the device, copies
+ * out[0] = failures, out[1] = site (1 LUT cell, 2 xc slice, 3 yc slice,
+ * 4 xy slice), out[2] = index and out[3] = limit of the first failure, and
+ * clears them.  The paper has no counterpart.  Returns UNSUPPORTED (out
+ * zeroed) in the normal build.
+ */
+svdlut_status svdlut_check_report(uint32_t out[4]);
+
 /* Library version, e.g. "svdlut 0.1.0 sm_103a". */
 const char *svdlut_version(void);
 

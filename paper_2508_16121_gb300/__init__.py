@@ -146,6 +146,19 @@ def apply_host(x, params, out=None, stream=None):
     return y[0] if squeeze else y
 
 
+def check_report():
+    """Index-check status of a library built with -DSVDLUT_CHECK_BOUNDS:
+    dict(failures, site, index, limit) of the first failure since the last
+    call (and clears it); None for the normal build."""
+    lib = _lib.load()
+    out = (ctypes.c_uint32 * 4)()
+    st = lib.svdlut_check_report(out)
+    if st == 2:  # SVDLUT_ERR_UNSUPPORTED: normal build
+        return None
+    _lib.check(st)
+    return {"failures": out[0], "site": out[1], "index": out[2], "limit": out[3]}
+
+
 def to_device(params, device="cuda"):
     """numpy / torch parameter dict -> contiguous float32 tensors on device."""
     torch = _torch()

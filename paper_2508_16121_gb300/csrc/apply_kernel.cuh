@@ -62,8 +62,35 @@ struct LaunchArgs {
     int lcell_floats;    // floats reserved for the cell table
     int scratch_floats;  // floats of the block buffers / prologue temporaries
     unsigned int *queue;  // non-null: blocks are taken from this counter (must be 0 at launch)
+    unsigned int *check;  // index-check status (builds with SVDLUT_CHECK_BOUNDS), else null
     ImgDesc img[N];
 };
+
+// ---- optional index checks ----
+// Built with -DSVDLUT_CHECK_BOUNDS, every shared-memory gather index of the
+// kernel is tested against its table size; an index out of range is counted
+// in the status words (count, site, index, limit of the first one) and
+// replaced by 0, so the access stays inside the table.  Otherwise the checks
+// compile to nothing.
+enum CheckSite : unsigned int { kChkLut = 1, kChkPxc = 2, kChkRyc = 3, kChkRxy = 4 };
+
+__device__ __forceinline__ int checked_index(unsigned int *st, unsigned int site, int idx, int limit)
+{
+#ifdef SVDLUT_CHECK_BOUNDS
+    if (idx >= 0 && idx < limit) return idx;
+    if (st && atomicAdd(st, 1u) == 0u) {
+        st[1] = site;
+        st[2] = static_cast<unsigned int>(idx);
+        st[3] = static_cast<unsigned int>(limit);
+    }
+    return 0;
+#else
+    (void)st;
+    (void)site;
+    (void)limit;
+    return idx;
+#endif
+}
 
 // Spatial cell of pixel index x on an axis of n pixels and Ds vertices
 // (x' = x/(n-1), u = x' (Ds-1), Supp. Eqs. 17-18), computed exactly in
@@ -658,12 +685,18 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                         jc[c] = cell_of(p[c], fS1, fS2, ec[c]);
                     }
                     float y0 = bias0, y1 = bias1, y2 = bias2;
-                    lut_pair(lcell + ic[0] * D3 + ic[1] * 3, dc[0], dc[1], y0, y1, y2);
-                    lut_pair(lcell + nc3 + ic[0] * D3 + ic[2] * 3, dc[0], dc[2], y0, y1, y2);
-                    lut_pair(lcell + 2 * nc3 + ic[1] * D3 + ic[2] * 3, dc[1], dc[2], y0, y1, y2);
+                    const int lut_lim = 3 * nc3 - 2;  // each cell reads 3 float4
+                    lut_pair(lcell + checked_index(a.check, kChkLut, ic[0] * D3 + ic[1] * 3, lut_lim), dc[0],
+                             dc[1], y0, y1, y2);
+                    lut_pair(lcell + checked_index(a.check, kChkLut, nc3 + ic[0] * D3 + ic[2] * 3, lut_lim), dc[0],
+                             dc[2], y0, y1, y2);
+                    lut_pair(lcell + checked_index(a.check, kChkLut, 2 * nc3 + ic[1] * D3 + ic[2] * 3, lut_lim),
+                             dc[1], dc[2], y0, y1, y2);
                     // xy slicing: row-interpolated vertices, lerp along x
-                    const float4 r0 = xy_fast ? (ixl[k] == ixl[0] ? xa : xb) : b.rxy[ixl[k]];
-                    const float4 r1 = xy_fast ? (ixl[k] == ixl[0] ? xb : xc) : b.rxy[ixl[k] + 1];
+                    const float4 r0 =
+                        xy_fast ? (ixl[k] == ixl[0] ? xa : xb) : b.rxy[checked_index(a.check, kChkRxy, ixl[k], g.nvx)];
+                    const float4 r1 = xy_fast ? (ixl[k] == ixl[0] ? xb : xc)
+                                              : b.rxy[checked_index(a.check, kChkRxy, ixl[k] + 1, g.nvx)];
                     const float dx = dxk[k];
                     y0 += fmaf(r1.x - r0.x, dx, r0.x);
                     y1 += fmaf(r1.y - r0.y, dx, r0.y);
@@ -672,8 +705,8 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                     // xc + yc slicing share the intensity cell of channel c
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const float4 q = b.pxc[c * xcs + ixl[k] * Dsc + jc[c]];
-                        const float2 qy = b.ryc[c * Dc1 + jc[c]];
+                        const float4 q = b.pxc[checked_index(a.check, kChkPxc, c * xcs + ixl[k] * Dsc + jc[c], 3 * xcs)];
+                        const float2 qy = b.ryc[checked_index(a.check, kChkRyc, c * Dc1 + jc[c], 3 * Dc1)];
                         const float s0 = fmaf(q.z, dx, q.x) + qy.x;  // value at j
                         const float sl = fmaf(q.w, dx, q.y) + qy.y;  // slope to j + 1
                         out[c][k] = fmaf(sl, ec[c], yy[c] + s0);
@@ -708,7 +741,8 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
 #pragma unroll
                     for (int pr = 0; pr < 3; ++pr) {
                         const int A = pr == 2 ? 1 : 0, Bx = pr == 0 ? 1 : 2;
-                        const float4 *q = lcell + pr * nc3 + ic[A] * D3 + ic[Bx] * 3;
+                        const float4 *q =
+                            lcell + checked_index(a.check, kChkLut, pr * nc3 + ic[A] * D3 + ic[Bx] * 3, 3 * nc3 - 2);
                         const float4 q0 = q[0], q1 = q[1], q2 = q[2];
                         // b = (q0.w, q1.x, q1.y), c = (q1.z, q1.w, q2.x), d = (q2.y, q2.z, q2.w)
                         const float da = dc[A], db = dc[Bx];
@@ -722,8 +756,8 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                     const float dx = dxk[k];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const float4 q = b.pxc[c * xcs + ixl[k] * Dsc + jc[c]];
-                        const float2 qy = b.ryc[c * Dc1 + jc[c]];
+                        const float4 q = b.pxc[checked_index(a.check, kChkPxc, c * xcs + ixl[k] * Dsc + jc[c], 3 * xcs)];
+                        const float2 qy = b.ryc[checked_index(a.check, kChkRyc, c * Dc1 + jc[c], 3 * Dc1)];
                         const float sl = fmaf(q.w, dx, q.y) + qy.y;  // slope to j + 1
                         gp[c] = fmaf(gy[c] * fS1, sl, gp[c]);
                         outd[c][k] = (xv[c] >= 0.f && xv[c] <= 1.f) ? gp[c] : 0.f;

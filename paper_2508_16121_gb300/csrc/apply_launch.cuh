@@ -112,6 +112,7 @@ svdlut_status launch_apply_t(LaunchArgs<N> &a, size_t smem, int sm_count, int ma
 {
     svdlut_status st = allow_smem_once(reinterpret_cast<const void *>(apply_kernel<T, N, DX>), max_smem, device);
     if (st != SVDLUT_OK) return st;
+    if ((st = check_buffer(&a.check)) != SVDLUT_OK) return st;
     if (grid <= 0) grid = std::min(a.total_blocks, sm_count);
     grid = std::max(1, std::min(grid, a.total_blocks));
     apply_kernel<T, N, DX><<<grid, kThreads, smem, s>>>(a);

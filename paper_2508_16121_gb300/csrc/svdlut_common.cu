@@ -55,7 +55,51 @@ svdlut_status device_info(DeviceInfo *out)
     return SVDLUT_OK;
 }
 
+#ifdef SVDLUT_CHECK_BOUNDS
+// [0] failures, [1] site, [2] index, [3] limit of the first failure
+static __device__ unsigned int g_check_words[4];
+#endif
+
+svdlut_status check_buffer(unsigned int **out)
+{
+#ifdef SVDLUT_CHECK_BOUNDS
+    static std::mutex mu;
+    static unsigned int *addr[64] = {};
+    int dev = 0;
+    SVDLUT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(SVDLUT_ERR_UNSUPPORTED, "device index %d", dev);
+    std::lock_guard<std::mutex> g(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        SVDLUT_CUDA_TRY(cudaGetSymbolAddress(&p, g_check_words));
+        addr[dev] = static_cast<unsigned int *>(p);
+    }
+    *out = addr[dev];
+#else
+    *out = nullptr;
+#endif
+    return SVDLUT_OK;
+}
+
 }  // namespace svdlut
+
+extern "C" svdlut_status svdlut_check_report(uint32_t out[4])
+{
+    svdlut::clear_error();
+    if (!out) return svdlut::fail(SVDLUT_ERR_INVALID_ARG, "out is NULL");
+#ifdef SVDLUT_CHECK_BOUNDS
+    unsigned int h[4] = {0, 0, 0, 0};
+    SVDLUT_CUDA_TRY(cudaDeviceSynchronize());
+    SVDLUT_CUDA_TRY(cudaMemcpyFromSymbol(h, svdlut::g_check_words, sizeof h));
+    const unsigned int zero[4] = {0, 0, 0, 0};
+    SVDLUT_CUDA_TRY(cudaMemcpyToSymbol(svdlut::g_check_words, zero, sizeof zero));
+    for (int i = 0; i < 4; ++i) out[i] = h[i];
+    return SVDLUT_OK;
+#else
+    for (int i = 0; i < 4; ++i) out[i] = 0;
+    return svdlut::fail(SVDLUT_ERR_UNSUPPORTED, "library built without SVDLUT_CHECK_BOUNDS");
+#endif
+}
 
 extern "C" const char *svdlut_last_error(void) { return svdlut::g_err; }
 

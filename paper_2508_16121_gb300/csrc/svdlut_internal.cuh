@@ -64,6 +64,10 @@ struct DeviceInfo {
 };
 svdlut_status device_info(DeviceInfo *out);
 
+// Device status words of the kernels' index checks for the current device
+// (builds with SVDLUT_CHECK_BOUNDS; null otherwise).
+svdlut_status check_buffer(unsigned int **out);
+
 inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 }  // namespace svdlut

@@ -96,3 +96,10 @@ def test_dims_inference_from_shapes():
     p = si.make_params(np.random.default_rng(0), d)
     got = svdlut.dims_of({k: np.asarray(v) for k, v in p.items()})
     assert (got.D_t, got.rank, got.K, got.Dsx, got.Dsy, got.Dsc) == d.as_tuple()
+
+
+def test_check_report_is_unsupported_in_the_normal_build(lib):
+    import ctypes
+    out = (ctypes.c_uint32 * 4)(7, 7, 7, 7)
+    assert lib.svdlut_check_report(out) == 2  # SVDLUT_ERR_UNSUPPORTED
+    assert list(out) == [0, 0, 0, 0]
