@@ -55,6 +55,7 @@ def _load():
             i = ctypes.c_int
             lib.oracle_forward.argtypes = [ip, i, i, i] + [dp] * 10 + [i]
             lib.oracle_forward_separable.argtypes = [ip, i, i, i] + [dp] * 10
+            lib.oracle_forward_original.argtypes = [ip, i, i, i] + [dp] * 11 + [i]
             lib.oracle_backward.argtypes = [ip, i, i, i] + [dp] * 19
             lib.oracle_lut_from_svd.argtypes = [i, i, dp, dp, dp, dp]
             lib.oracle_quantize_u8.argtypes = [dp, ctypes.c_void_p, ctypes.c_size_t]
@@ -110,6 +111,23 @@ def forward(dims, params, x, nthreads: int = 0, separable: bool = False):
         lib.oracle_forward_separable(_dims(dims), B, H, W, *args, _ptr(xb), _ptr(y))
     else:
         lib.oracle_forward(_dims(dims), B, H, W, *args, _ptr(xb), _ptr(y), int(nthreads))
+    return y[0] if squeeze else y
+
+
+def forward_original(dims, params, fusion, x, nthreads: int = 0):
+    """The paper's original structure in FP64 (Eqs. 7, 8, 5): K spatial maps,
+    the (K+3)->3 1x1 fusion conv, then the 2D LUT transform of the fused
+    image.  fusion: [3 (K+3) + 3] or [B][3 (K+3) + 3] (weights [3][K+3], then
+    biases [3])."""
+    squeeze = np.asarray(x).ndim == 3
+    p, xb = _batched(params, x)
+    B, _, H, W = xb.shape
+    f = _d(fusion)
+    if f.ndim == 1:
+        f = np.ascontiguousarray(np.broadcast_to(f, (B, f.shape[0])))
+    y = np.empty_like(xb)
+    _load().oracle_forward_original(_dims(dims), B, H, W, *[_ptr(p[k]) for k in PARAM_NAMES], _ptr(f),
+                                    _ptr(xb), _ptr(y), int(nthreads))
     return y[0] if squeeze else y
 
 

@@ -183,6 +183,74 @@ int oracle_forward(const int *dims, int B, int H, int W,
     return 0;
 }
 
+/* The paper's original (unfused) structure, the "1x1 conv" model of Table 6:
+ *   f_s[k] = w_xy psi_xy + w_xc psi_xc + w_yc psi_yc + b_k        (Eq. 7, K maps)
+ *   Xbar_c = sum_i Wf[c][i] X_i + sum_k Wf[c][3+k] f_s[k] + bf[c]  (Eq. 8, 1x1 conv)
+ *   Y_c    = w_rg phi_rg(Xbar) + w_rb phi_rb(Xbar) + w_gb phi_gb(Xbar) + b^c   (Eq. 5)
+ * The slices read the clamped input intensity of channel k mod 3; the conv
+ * takes the input as given; the LUT lookup clamps Xbar to [0,1] (reading R6).
+ * fusion: [B][3][K+3] weights then [B][3] biases, i.e. [B][3 (K+3) + 3].
+ * Grid arguments may be NULL when K == 0. */
+int oracle_forward_original(const int *dims, int B, int H, int W,
+                            const double *U, const double *S, const double *V, const double *lut_w,
+                            const double *g_xy, const double *g_xc, const double *g_yc,
+                            const double *grid_w, const double *fusion, const double *x, double *y,
+                            int nthreads)
+{
+    size_t plane = (size_t)H * W;
+    const int K = dims[2], nf = 3 * (K + 3) + 3;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    for (int b = 0; b < B; ++b) {
+        img_params q = params_of(dims, b, U, S, V, lut_w, g_xy, g_xc, g_yc, grid_w);
+        double *T = build_tables(&q);
+        const double *xb = x + (size_t)b * 3 * plane;
+        const double *Wf = fusion + (size_t)b * nf, *bf = Wf + 3 * (K + 3);
+        double *yb = y + (size_t)b * 3 * plane;
+        int D = q.D;
+#pragma omp parallel for schedule(static)
+        for (int row = 0; row < H; ++row) {
+            double *fs = (double *)malloc(sizeof(double) * (K > 0 ? K : 1));
+            for (int col = 0; col < W; ++col) {
+                size_t o = (size_t)row * W + col;
+                double xin[3], p[3], xs = coord(col, W), ys = coord(row, H);
+                for (int c = 0; c < 3; ++c) {
+                    xin[c] = xb[c * plane + o];
+                    p[c] = clamp01(xin[c]);
+                }
+                for (int k = 0; k < K; ++k) {
+                    int c = k % 3;
+                    const double *w = q.gw + k * 4;
+                    fs[k] = w[0] * bilinear(q.gxy + (size_t)k * q.Dsy * q.Dsx, q.Dsx, q.Dsy, q.Dsx, ys, xs)
+                          + w[1] * bilinear(q.gxc + (size_t)k * q.Dsx * q.Dsc, q.Dsc, q.Dsx, q.Dsc, xs, p[c])
+                          + w[2] * bilinear(q.gyc + (size_t)k * q.Dsy * q.Dsc, q.Dsc, q.Dsy, q.Dsc, ys, p[c])
+                          + w[3];
+                }
+                double xbar[3];
+                for (int c = 0; c < 3; ++c) {
+                    double v = bf[c];
+                    for (int i = 0; i < 3; ++i) v += Wf[c * (K + 3) + i] * xin[i];
+                    for (int k = 0; k < K; ++k) v += Wf[c * (K + 3) + 3 + k] * fs[k];
+                    xbar[c] = clamp01(v);
+                }
+                for (int c = 0; c < 3; ++c) {
+                    double Phi = q.lw[c * 4 + 3];
+                    for (int pr = 0; pr < 3; ++pr)
+                        Phi += q.lw[c * 4 + pr] * bilinear(T + (size_t)(c * 3 + pr) * D * D, D, D, D,
+                                                           xbar[AX_A[pr]], xbar[AX_B[pr]]);
+                    yb[c * plane + o] = Phi;
+                }
+            }
+            free(fs);
+        }
+        free(T);
+    }
+    return 0;
+}
+
 /* Forward of the LUT part only through the separable form
  * I_bi(U S V^T; a, b) = sum_r s_r I_1d(u_r; a) I_1d(v_r; b),
  * never materialising T.  Independent second route used to cross-check the
