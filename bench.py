@@ -272,6 +272,27 @@ def run_ours(args, world, rank, local):
                  "workload": "1x3840x2160 FP32, D_t=33 rank 8, K=6 grids 17x17x17"}
     del xq_t, yq_t
 
+    # ---- the paper's original, unfused structure (maps and fused image through HBM) ----
+    original = {}
+    for name, dd, (xx, pp_) in (("1/8-res K=8", d, (sets[0][0], sets[0][1])), ("paper K=6 17^3", dp, (None, None))):
+        if xx is None:
+            xx, pp_ = torch.from_numpy(xq).to(dev), svdlut.to_device(pq, dev)
+        frng = np.random.default_rng(si.config_seed(1) + 13)
+        Wf = frng.normal(0, 0.15, (3, dd.K + 3))
+        Wf[np.arange(3), np.arange(3)] += 1.0
+        fus = torch.tensor(np.concatenate([Wf.ravel(), np.zeros(3)]), dtype=torch.float32, device=dev)
+        ws_o = torch.empty(svdlut.original_workspace_bytes(pp_, 1, H, W), dtype=torch.uint8, device=dev)
+        yo = torch.empty_like(xx)
+        t_o = time_calls(lambda: svdlut.apply_original(xx, pp_, fus, out=yo, workspace=ws_o), max(3, args.steps // 4),
+                         stream)
+        t_f = time_calls(lambda: svdlut.apply(xx, pp_, out=yo), max(3, args.steps // 4), stream)
+        bytes_o = H * W * (60 + 8 * dd.K)  # X read twice, K maps written and read, Xbar written and read, Y written
+        original[name] = {"original_ms": round(t_o, 4), "fused_ms": round(t_f, 4),
+                          "fused_speedup": round(t_o / t_f, 2),
+                          "original_GB/s": round(bytes_o / (t_o / 1e3) / 1e9, 1),
+                          "original_bytes_per_px": 60 + 8 * dd.K}
+        del ws_o, yo
+
     # ---- ragged batch: 16 images 480p..4K, one graph-captured launch vs 16 plain calls ----
     batched = run_batched_variant(svdlut, torch, dev, stream, args)
 
@@ -339,6 +360,7 @@ def run_ours(args, world, rank, local):
                                      "GB/s": round(algo_bytes_apply(H, W, d, 1) / (u8_ms / 1e3) / 1e9, 1)},
                      "f32_plain_4k_by_regime_Mpix/s": regimes,
                      "f32_plain_4k_paper_grids": paper_cfg,
+                     "original_unfused_structure_4k": original,
                      "batched_16_ragged": batched,
                      "backward_8x1080p": backward,
                      "learned_4x4k": learned},

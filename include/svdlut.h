@@ -312,6 +312,25 @@ svdlut_status svdlut_backward_noalloc(const svdlut_dims *dims, const svdlut_para
 const char *svdlut_last_error(void);
 
 /*
+ * svdlut_apply_original -- the paper's original, unfused structure (the "1x1
+ * conv" model of Table 6; Eqs. 7, 8 and 5), kept for comparison with the fused
+ * transform: K spatial maps f_s[k] = w_xy psi_xy + w_xc psi_xc + w_yc psi_yc +
+ * b_k are written to the workspace, then Xbar = 1x1 conv (K+3 -> 3) of
+ * concat(x, f_s), then y = the 2D LUT transform of Xbar (inputs clamped to
+ * [0,1] for the lookups, as in svdlut_apply).
+ *   fusion   [B][3 (K+3) + 3] device floats: weights [3 out][K+3 in] (input
+ *            channels r, g, b, then the K maps), then biases [3]
+ *   x, y     [B][3][H][W] float device arrays, must not overlap
+ *   ws       device workspace of svdlut_apply_original_workspace_size()
+ *            bytes, 256-byte aligned (f_s and Xbar)
+ * Errors: those of svdlut_apply; WORKSPACE when ws is missing or too small.
+ */
+svdlut_status svdlut_apply_original(const svdlut_dims *dims, const svdlut_params *params, const float *fusion,
+                                    int B, int H, int W, const float *x, float *y, void *ws, size_t ws_bytes,
+                                    svdlut_stream_t stream);
+size_t svdlut_apply_original_workspace_size(const svdlut_dims *dims, int B, int H, int W);
+
+/*
  * svdlut_check_report -- index-check status of a library built with
  * -DSVDLUT_CHECK_BOUNDS (a debugging build in which the transform kernels
  * test every shared-memory gather index, count the ones out of range and

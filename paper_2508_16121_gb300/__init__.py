@@ -146,6 +146,42 @@ def apply_host(x, params, out=None, stream=None):
     return y[0] if squeeze else y
 
 
+def original_workspace_bytes(params, B, H, W):
+    """Device workspace of apply_original for B images of H x W."""
+    return int(_lib.load().svdlut_apply_original_workspace_size(ctypes.byref(dims_of(params)), B, H, W))
+
+
+def apply_original(x, params, fusion, out=None, workspace=None, stream=None):
+    """The paper's original, unfused structure (svdlut_apply_original): K
+    spatial maps and the fused image go through HBM.  x: float32 CUDA tensor
+    [B,3,H,W] or [3,H,W]; fusion: CUDA tensor [3 (K+3) + 3] or
+    [B, 3 (K+3) + 3] (1x1 conv weights [3][K+3], then biases [3])."""
+    torch = _torch()
+    squeeze = x.dim() == 3
+    xb = x.unsqueeze(0) if squeeze else x
+    if xb.dim() != 4 or xb.shape[1] != 3 or xb.dtype != torch.float32 or not xb.is_cuda or not xb.is_contiguous():
+        raise ValueError("x must be a contiguous float32 CUDA tensor [B,3,H,W] or [3,H,W]")
+    B, _, H, W = xb.shape
+    d = dims_of(params)
+    p = _param_struct(params, B, d)
+    nf = 3 * (d.K + 3) + 3
+    f = fusion.reshape(-1, nf)
+    if f.shape[0] == 1 and B > 1:
+        f = f.expand(B, nf)
+    f = f.to(torch.float32).contiguous()
+    if f.shape != (B, nf) or not f.is_cuda:
+        raise ValueError(f"fusion must hold {nf} floats per image on the GPU")
+    y = torch.empty_like(xb) if out is None else (out.unsqueeze(0) if squeeze else out)
+    lib = _lib.load()
+    need = lib.svdlut_apply_original_workspace_size(ctypes.byref(d), B, H, W)
+    ws = workspace if workspace is not None and workspace.numel() >= need else \
+        torch.empty(need, dtype=torch.uint8, device=xb.device)
+    _lib.check(lib.svdlut_apply_original(ctypes.byref(d), ctypes.byref(p), ctypes.c_void_p(f.data_ptr()), B, H, W,
+                                         ctypes.c_void_p(xb.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+    return y[0] if squeeze else y
+
+
 def check_report():
     """Index-check status of a library built with -DSVDLUT_CHECK_BOUNDS:
     dict(failures, site, index, limit) of the first failure since the last

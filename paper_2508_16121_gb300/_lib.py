@@ -106,6 +106,11 @@ def _declare(lib):
     lib.svdlut_backward_noalloc.argtypes = [P(Dims), P(Params), c_int, c_int, c_int, c_void_p, c_void_p,
                                             c_void_p, P(Grads), c_void_p]
     lib.svdlut_backward_noalloc.restype = c_int
+    lib.svdlut_apply_original.argtypes = [P(Dims), P(Params), c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
+                                          c_void_p, c_size_t, c_void_p]
+    lib.svdlut_apply_original.restype = c_int
+    lib.svdlut_apply_original_workspace_size.argtypes = [P(Dims), c_int, c_int, c_int]
+    lib.svdlut_apply_original_workspace_size.restype = c_size_t
     lib.svdlut_check_report.argtypes = [c_void_p]
     lib.svdlut_check_report.restype = c_int
     lib.svdlut_apply_cfg.argtypes = [P(Dims), P(Params), c_int, c_int, c_int, c_int, c_void_p, c_void_p,
@@ -135,4 +140,4 @@ def check(status: int):
 EXPORTED = ["svdlut_apply", "svdlut_apply_batched", "svdlut_batched_workspace_size", "svdlut_autotune_batched",
             "svdlut_generator_param_count", "svdlut_generator_workspace_size", "svdlut_generator_forward",
             "svdlut_generator_backward", "svdlut_generator_adam", "svdlut_mse", "svdlut_backward", "svdlut_backward_workspace_size", "svdlut_backward_noalloc",
-            "svdlut_apply_cfg", "svdlut_check_report", "svdlut_apply_host", "svdlut_apply_host_workspace_size", "svdlut_last_error", "svdlut_version"]
+            "svdlut_apply_cfg", "svdlut_apply_original", "svdlut_apply_original_workspace_size", "svdlut_check_report", "svdlut_apply_host", "svdlut_apply_host_workspace_size", "svdlut_last_error", "svdlut_version"]
