@@ -56,6 +56,9 @@ def _load():
             lib.oracle_forward.argtypes = [ip, i, i, i] + [dp] * 10 + [i]
             lib.oracle_forward_separable.argtypes = [ip, i, i, i] + [dp] * 10
             lib.oracle_forward_original.argtypes = [ip, i, i, i] + [dp] * 11 + [i]
+            lib.oracle_lut3d_apply.argtypes = [i, i, i, i, dp, dp, dp]
+            lib.oracle_lut3d_fit2d.argtypes = [i, dp, dp, dp, dp]
+            lib.oracle_lut3d_fit2d.restype = ctypes.c_double
             lib.oracle_backward.argtypes = [ip, i, i, i] + [dp] * 19
             lib.oracle_lut_from_svd.argtypes = [i, i, dp, dp, dp, dp]
             lib.oracle_quantize_u8.argtypes = [dp, ctypes.c_void_p, ctypes.c_size_t]
@@ -129,6 +132,33 @@ def forward_original(dims, params, fusion, x, nthreads: int = 0):
     _load().oracle_forward_original(_dims(dims), B, H, W, *[_ptr(p[k]) for k in PARAM_NAMES], _ptr(f),
                                     _ptr(xb), _ptr(y), int(nthreads))
     return y[0] if squeeze else y
+
+
+def lut3d_apply(lut3d, x):
+    """Trilinear 3D LUT transform (Eq. 3) in FP64.  lut3d: [3][D][D][D] or
+    [B][3][D][D][D] (axes r, g, b per output channel); x: [3][H][W] or
+    [B][3][H][W]."""
+    squeeze = np.asarray(x).ndim == 3
+    xb = _d(x)
+    t = _d(lut3d)
+    if xb.ndim == 3:
+        xb = xb[None]
+    if t.ndim == 4:
+        t = np.ascontiguousarray(np.broadcast_to(t, (xb.shape[0],) + t.shape))
+    B, _, H, W = xb.shape
+    y = np.empty_like(xb)
+    _load().oracle_lut3d_apply(t.shape[-1], B, H, W, _ptr(t), _ptr(xb), _ptr(y))
+    return y[0] if squeeze else y
+
+
+def lut3d_fit2d(t):
+    """Best least-squares fit of one [D][D][D] table by A[i][j] + B[i][k] +
+    C[j][k] (second-order ANOVA projection); returns (A, B, C, rms residual)."""
+    t = _d(t)
+    D = t.shape[0]
+    A, Bt, C = np.empty((D, D)), np.empty((D, D)), np.empty((D, D))
+    rms = _load().oracle_lut3d_fit2d(D, _ptr(t), _ptr(A), _ptr(Bt), _ptr(C))
+    return A, Bt, C, rms
 
 
 def backward(dims, params, x, dy):

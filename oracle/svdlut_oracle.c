@@ -251,6 +251,107 @@ int oracle_forward_original(const int *dims, int B, int H, int W,
     return 0;
 }
 
+/* ---- 3D LUT (Eq. 3) and its best decomposition into 2D LUTs (Eq. 4) ----
+ * lut3d: [D][D][D] per output channel, axes (r, g, b); trilinear lookup with
+ * the cell rule of Supp. Eq. 13 on each axis. */
+static double trilinear(const double *t, int D, double pr, double pg, double pb)
+{
+    int i, j, k;
+    double a, b, c;
+    cell(pr, D, &i, &a);
+    cell(pg, D, &j, &b);
+    cell(pb, D, &k, &c);
+    double v = 0.0;
+    for (int di = 0; di < 2; ++di)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int dk = 0; dk < 2; ++dk) {
+                double w = (di ? a : 1.0 - a) * (dj ? b : 1.0 - b) * (dk ? c : 1.0 - c);
+                v += w * t[((size_t)(i + di) * D + (j + dj)) * D + (k + dk)];
+            }
+    return v;
+}
+
+/* y = I_tri(clamp(x), t^c_rgb) for every channel c.  lut3d: [B][3 c][D][D][D]. */
+int oracle_lut3d_apply(int D, int B, int H, int W, const double *lut3d, const double *x, double *y)
+{
+    size_t plane = (size_t)H * W, nl = (size_t)D * D * D;
+    for (int b = 0; b < B; ++b) {
+        const double *xb = x + (size_t)b * 3 * plane;
+        double *yb = y + (size_t)b * 3 * plane;
+#pragma omp parallel for schedule(static)
+        for (int row = 0; row < H; ++row)
+            for (int col = 0; col < W; ++col) {
+                size_t o = (size_t)row * W + col;
+                double p[3];
+                for (int c = 0; c < 3; ++c) p[c] = clamp01(xb[c * plane + o]);
+                for (int c = 0; c < 3; ++c)
+                    yb[c * plane + o] = trilinear(lut3d + ((size_t)b * 3 + c) * nl, D, p[0], p[1], p[2]);
+            }
+    }
+    return 0;
+}
+
+/* Least-squares fit, over the D^3 vertices, of one 3D table t[i][j][k] by a
+ * sum of 2D tables A[i][j] + Bt[i][k] + C[j][k] (the hypothesis of Eq. 4 with
+ * the weights and bias absorbed).  The sums of functions of two indices form
+ * a linear space whose orthogonal projection is the second-order ANOVA
+ * expansion:
+ *   fit = m_ij. + m_i.k + m_.jk - m_i.. - m_.j. - m_..k + m_...
+ * (m: means over the dotted indices); it is split as A = m_ij.,
+ * Bt = m_i.k - m_i.., C = m_.jk - m_.j. - m_..k + m_... .  Returns the RMS
+ * of the residual (the three-way interaction). */
+double oracle_lut3d_fit2d(int D, const double *t, double *A, double *Bt, double *C)
+{
+    size_t n2 = (size_t)D * D;
+    double *mij = (double *)calloc(n2, sizeof(double)), *mik = (double *)calloc(n2, sizeof(double)),
+           *mjk = (double *)calloc(n2, sizeof(double)), *mi = (double *)calloc(D, sizeof(double)),
+           *mj = (double *)calloc(D, sizeof(double)), *mk = (double *)calloc(D, sizeof(double));
+    double m = 0.0;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j)
+            for (int k = 0; k < D; ++k) {
+                double v = t[((size_t)i * D + j) * D + k];
+                mij[i * D + j] += v;
+                mik[i * D + k] += v;
+                mjk[j * D + k] += v;
+                mi[i] += v;
+                mj[j] += v;
+                mk[k] += v;
+                m += v;
+            }
+    for (size_t e = 0; e < n2; ++e) {
+        mij[e] /= D;
+        mik[e] /= D;
+        mjk[e] /= D;
+    }
+    for (int i = 0; i < D; ++i) {
+        mi[i] /= (double)D * D;
+        mj[i] /= (double)D * D;
+        mk[i] /= (double)D * D;
+    }
+    m /= (double)D * D * D;
+    for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) {
+            A[a * D + b] = mij[a * D + b];
+            Bt[a * D + b] = mik[a * D + b] - mi[a];
+            C[a * D + b] = mjk[a * D + b] - mj[a] - mk[b] + m;
+        }
+    double ss = 0.0;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j)
+            for (int k = 0; k < D; ++k) {
+                double r = t[((size_t)i * D + j) * D + k] - A[i * D + j] - Bt[i * D + k] - C[j * D + k];
+                ss += r * r;
+            }
+    free(mij);
+    free(mik);
+    free(mjk);
+    free(mi);
+    free(mj);
+    free(mk);
+    return sqrt(ss / ((double)D * D * D));
+}
+
 /* Forward of the LUT part only through the separable form
  * I_bi(U S V^T; a, b) = sum_r s_r I_1d(u_r; a) I_1d(v_r; b),
  * never materialising T.  Independent second route used to cross-check the

@@ -199,6 +199,37 @@ GEN_M, GEN_HIDDEN = 8, 8
 GEN_CH = (3, 8, 16, 32, 64, 64)
 
 
+def make_lut3d(rng: np.random.Generator, D: int = 33, kind: str = "photo") -> np.ndarray:
+    """Synthetic 3D LUT [3 out][D r][D g][D b] on the vertex grid.
+    identity: out_c = in_c.  photo: a seeded photo-style grade (per-channel
+    gamma, near-identity colour matrix, saturation about the luma, and a
+    split-toning term r*g*b that no sum of 2D tables can express), clipped to
+    [0,1].  smooth: identity plus a few seeded low-frequency 3D cosines."""
+    v = np.linspace(0.0, 1.0, D)
+    r, g, b = np.meshgrid(v, v, v, indexing="ij")
+    rgb = np.stack([r, g, b])
+    if kind == "identity":
+        return rgb.copy()
+    if kind == "photo":
+        gam = rng.uniform(0.8, 1.25, 3)
+        x = rgb ** gam[:, None, None, None]
+        M = np.eye(3) + rng.uniform(-0.08, 0.08, (3, 3))
+        x = np.einsum("cd,dijk->cijk", M, x)
+        lum = 0.299 * x[0] + 0.587 * x[1] + 0.114 * x[2]
+        x = lum + rng.uniform(0.8, 1.3) * (x - lum)
+        x = x + rng.uniform(-0.3, 0.3, 3)[:, None, None, None] * (r * g * b)
+        return np.clip(x, 0.0, 1.0)
+    if kind == "smooth":
+        x = rgb.copy()
+        for _ in range(4):
+            f = rng.integers(1, 3, 3)
+            ph = rng.uniform(0, 2 * np.pi, 3)
+            a = rng.uniform(-0.05, 0.05, 3)
+            x += a[:, None, None, None] * np.cos(np.pi * (f[0] * r + f[1] * g + f[2] * b) + ph[:, None, None, None])
+        return x
+    raise ValueError(kind)
+
+
 def generator_shapes(K: int):
     """(name, shape) of the generator's weights in the flat FP32 layout
     documented with svdlut_generator_forward (include/svdlut.h)."""
