@@ -293,6 +293,9 @@ def run_ours(args, world, rank, local):
                           "original_bytes_per_px": 60 + 8 * dd.K}
         del ws_o, yo
 
+    # ---- the 3D LUT of Eq. 3 against its best 2D-LUT fit (Eq. 4) on the same 4K image ----
+    lut3d = run_lut3d_variant(svdlut, torch, dev, stream, args, sets[0][0])
+
     # ---- ragged batch: 16 images 480p..4K, one graph-captured launch vs 16 plain calls ----
     batched = run_batched_variant(svdlut, torch, dev, stream, args)
 
@@ -361,6 +364,7 @@ def run_ours(args, world, rank, local):
                      "f32_plain_4k_by_regime_Mpix/s": regimes,
                      "f32_plain_4k_paper_grids": paper_cfg,
                      "original_unfused_structure_4k": original,
+                     "lut3d_vs_2d_fit_4k": lut3d,
                      "batched_16_ragged": batched,
                      "backward_8x1080p": backward,
                      "learned_4x4k": learned},
@@ -381,6 +385,40 @@ def time_calls(fn, steps, stream, warmup=3):
     b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / steps
+
+
+def run_lut3d_variant(svdlut, torch, dev, stream, args, x):
+    """3D LUT transform vs the 2D transform of its least-squares 2D fit, full
+    rank and truncated to rank 8 (Eq. 9), for a photo-style and a smooth 33^3
+    LUT: speed, fit RMS on the vertex grid and RMS difference on the image."""
+    H, W = x.shape[-2], x.shape[-1]
+    steps = max(3, args.steps // 4)
+    out = {}
+    y3, y2 = torch.empty_like(x), torch.empty_like(x)
+    for kind in ("photo", "smooth"):
+        rng = np.random.default_rng(si.config_seed(1) + 17)
+        lut = torch.tensor(si.make_lut3d(rng, 33, kind), dtype=torch.float32, device=dev)[None]
+        ws = torch.empty(svdlut._lib.load().svdlut_lut3d_workspace_size(33, 1), dtype=torch.uint8, device=dev)
+        t3 = time_calls(lambda: svdlut.lut3d_apply(x, lut, out=y3, workspace=ws), steps, stream)
+        tf = time_calls(lambda: svdlut.lut3d_fit2d(lut), steps, stream)
+        tables, rms = svdlut.lut3d_fit2d(lut)
+        pf = svdlut.fit_params(tables)
+        t2 = time_calls(lambda: svdlut.apply(x, pf, out=y2), steps, stream)
+        full_rmse = float(torch.sqrt(torch.mean((y2 - y3) ** 2)))
+        # rank-8 truncation of each fitted table (host SVD: analysis only)
+        u, sv_, vt = np.linalg.svd(tables[0].double().cpu().numpy())
+        p8 = dict(pf, U=torch.tensor(u[..., :8], dtype=torch.float32, device=dev)[None].contiguous(),
+                  S=torch.tensor(sv_[..., :8], dtype=torch.float32, device=dev)[None].contiguous(),
+                  V=torch.tensor(np.swapaxes(vt, -1, -2)[..., :8], dtype=torch.float32, device=dev)[None].contiguous())
+        t8 = time_calls(lambda: svdlut.apply(x, p8, out=y2), steps, stream)
+        r8_rmse = float(torch.sqrt(torch.mean((y2 - y3) ** 2)))
+        out[kind] = {"lut3d_ms": round(t3, 4), "lut3d_Mpix/s": round(H * W / 1e6 / (t3 / 1e3), 1),
+                     "lut3d_GB/s": round(H * W * 24 / (t3 / 1e3) / 1e9, 1),
+                     "fit2d_ms": round(tf, 4), "fit2d_full_rank_ms": round(t2, 4), "fit2d_rank8_ms": round(t8, 4),
+                     "fit_rms_vertex_grid": [round(float(v), 6) for v in rms[0]],
+                     "image_rmse_full_rank_vs_3d": round(full_rmse, 6), "image_rmse_rank8_vs_3d": round(r8_rmse, 6)}
+    out["workload"] = f"1x{W}x{H} FP32, 33^3 LUTs (seeded photo-style grade and smooth cosine LUT), no grids"
+    return out
 
 
 def run_batched_variant(svdlut, torch, dev, stream, args):

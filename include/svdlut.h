@@ -331,6 +331,37 @@ svdlut_status svdlut_apply_original(const svdlut_dims *dims, const svdlut_params
 size_t svdlut_apply_original_workspace_size(const svdlut_dims *dims, int B, int H, int W);
 
 /*
+ * svdlut_lut3d_apply -- the 3D LUT transform the paper starts from (Eq. 3):
+ * y_c = trilinear interpolation, at the clamped (r, g, b) of each pixel, of
+ * the table t^c over the D x D x D vertex grid, for B images of H x W.
+ *   lut3d  [B][3 c][D][D][D] device floats, index [r][g][b]
+ *   x, y   [B][3][H][W] float device arrays
+ *   ws     device workspace of svdlut_lut3d_workspace_size(D, B) bytes,
+ *          16-byte aligned (the tables repacked as one float4 per vertex)
+ * 2 <= D <= 33.  Errors: INVALID_ARG for null or misaligned pointers, bad
+ * sizes; WORKSPACE when ws is missing or too small.
+ */
+svdlut_status svdlut_lut3d_apply(int D, const float *lut3d, int B, int H, int W, const float *x, float *y,
+                                 void *ws, size_t ws_bytes, svdlut_stream_t stream);
+size_t svdlut_lut3d_workspace_size(int D, int B);
+
+/*
+ * svdlut_lut3d_fit2d -- the best approximation of each 3D table by a sum of
+ * 2D tables, the hypothesis behind the 2D LUT (Eq. 4): the least-squares fit
+ * over the vertex grid, t[i][j][k] ~ A[i][j] + Bt[i][k] + C[j][k], which is
+ * the second-order ANOVA projection (m: means over the dotted indices)
+ *   A = m_ij.,  Bt = m_i.k - m_i..,  C = m_.jk - m_.j. - m_..k + m_... .
+ *   lut3d   [B][3 c][D][D][D] device floats
+ *   tables  [B][3 c][3 pair (A, Bt, C)][D][D] device floats, written: this
+ *           is the U array of svdlut_params for rank = D with S = 1, V = the
+ *           identity and lut_w = (1, 1, 1, 0), so svdlut_apply can run the fit
+ *   rms     [B][3] device floats, written: RMS of the residual over the grid
+ * 2 <= D <= 33.  Errors: INVALID_ARG for null pointers or bad sizes.
+ */
+svdlut_status svdlut_lut3d_fit2d(int D, const float *lut3d, int B, float *tables, float *rms,
+                                 svdlut_stream_t stream);
+
+/*
  * svdlut_check_report -- index-check status of a library built with
  * -DSVDLUT_CHECK_BOUNDS (a debugging build in which the transform kernels
  * test every shared-memory gather index, count the ones out of range and

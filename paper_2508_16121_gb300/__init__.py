@@ -182,6 +182,70 @@ def apply_original(x, params, fusion, out=None, workspace=None, stream=None):
     return y[0] if squeeze else y
 
 
+def _lut3d_tensor(lut3d):
+    torch = _torch()
+    t = lut3d.unsqueeze(0) if lut3d.dim() == 4 else lut3d
+    if (t.dim() != 5 or t.shape[1] != 3 or not (t.shape[2] == t.shape[3] == t.shape[4])
+            or t.dtype != torch.float32 or not t.is_cuda):
+        raise ValueError("lut3d must be a float32 CUDA tensor [B,3,D,D,D] or [3,D,D,D]")
+    return t.contiguous()
+
+
+def lut3d_apply(x, lut3d, out=None, workspace=None, stream=None):
+    """3D LUT transform (Eq. 3, svdlut_lut3d_apply): trilinear lookup of
+    lut3d [B,3,D,D,D] (or [3,D,D,D] shared by the batch), index [r][g][b],
+    at every pixel of x (float32 CUDA [B,3,H,W] or [3,H,W])."""
+    torch = _torch()
+    squeeze = x.dim() == 3
+    xb = x.unsqueeze(0) if squeeze else x
+    if xb.dim() != 4 or xb.shape[1] != 3 or xb.dtype != torch.float32 or not xb.is_cuda or not xb.is_contiguous():
+        raise ValueError("x must be a contiguous float32 CUDA tensor [B,3,H,W] or [3,H,W]")
+    B, _, H, W = xb.shape
+    t = _lut3d_tensor(lut3d)
+    if t.shape[0] == 1 and B > 1:
+        t = t.expand(B, *t.shape[1:]).contiguous()
+    if t.shape[0] != B:
+        raise ValueError(f"lut3d holds {t.shape[0]} tables for {B} images")
+    D = t.shape[-1]
+    y = torch.empty_like(xb) if out is None else (out.unsqueeze(0) if squeeze else out)
+    lib = _lib.load()
+    need = lib.svdlut_lut3d_workspace_size(D, B)
+    ws = workspace if workspace is not None and workspace.numel() >= need else \
+        torch.empty(need, dtype=torch.uint8, device=xb.device)
+    _lib.check(lib.svdlut_lut3d_apply(D, ctypes.c_void_p(t.data_ptr()), B, H, W, ctypes.c_void_p(xb.data_ptr()),
+                                      ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                      _stream_ptr(stream)))
+    return y[0] if squeeze else y
+
+
+def lut3d_fit2d(lut3d, stream=None):
+    """Least-squares fit of each 3D table by A[r][g] + Bt[r][b] + C[g][b]
+    (the hypothesis of Eq. 4; svdlut_lut3d_fit2d).  Returns (tables
+    [B,3,3,D,D] in pair order (A, Bt, C), rms [B,3])."""
+    torch = _torch()
+    t = _lut3d_tensor(lut3d)
+    B, D = t.shape[0], t.shape[-1]
+    tables = torch.empty(B, 3, 3, D, D, dtype=torch.float32, device=t.device)
+    rms = torch.empty(B, 3, dtype=torch.float32, device=t.device)
+    _lib.check(_lib.load().svdlut_lut3d_fit2d(D, ctypes.c_void_p(t.data_ptr()), B, ctypes.c_void_p(tables.data_ptr()),
+                                              ctypes.c_void_p(rms.data_ptr()), _stream_ptr(stream)))
+    return tables, rms
+
+
+def fit_params(tables):
+    """svdlut parameters that run 2D tables [B,3,3,D,D] (e.g. from
+    lut3d_fit2d) through apply at full rank: U = the tables, S = 1, V = I,
+    lut_w = (1, 1, 1, 0), no grids."""
+    torch = _torch()
+    B, D = tables.shape[0], tables.shape[-1]
+    dev = tables.device
+    V = torch.eye(D, dtype=torch.float32, device=dev).expand(B, 3, 3, D, D).contiguous()
+    lut_w = torch.tensor([1.0, 1.0, 1.0, 0.0], device=dev).expand(B, 3, 4).contiguous()
+    none = torch.empty(B, 0, 2, 2, device=dev)
+    return dict(U=tables.contiguous(), S=torch.ones(B, 3, 3, D, device=dev), V=V, lut_w=lut_w,
+                g_xy=none, g_xc=none, g_yc=none, grid_w=torch.empty(B, 0, 4, device=dev))
+
+
 def check_report():
     """Index-check status of a library built with -DSVDLUT_CHECK_BOUNDS:
     dict(failures, site, index, limit) of the first failure since the last

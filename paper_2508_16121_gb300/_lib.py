@@ -121,6 +121,13 @@ def _declare(lib):
     lib.svdlut_apply_host.restype = c_int
     lib.svdlut_apply_host_workspace_size.argtypes = [c_int, c_int, c_int, c_int]
     lib.svdlut_apply_host_workspace_size.restype = c_size_t
+    lib.svdlut_lut3d_apply.argtypes = [c_int, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_size_t,
+                                       c_void_p]
+    lib.svdlut_lut3d_apply.restype = c_int
+    lib.svdlut_lut3d_workspace_size.argtypes = [c_int, c_int]
+    lib.svdlut_lut3d_workspace_size.restype = c_size_t
+    lib.svdlut_lut3d_fit2d.argtypes = [c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p]
+    lib.svdlut_lut3d_fit2d.restype = c_int
     for name, argtypes in _EXTRA.items():
         if hasattr(lib, name):
             f = getattr(lib, name)
@@ -140,4 +147,5 @@ def check(status: int):
 EXPORTED = ["svdlut_apply", "svdlut_apply_batched", "svdlut_batched_workspace_size", "svdlut_autotune_batched",
             "svdlut_generator_param_count", "svdlut_generator_workspace_size", "svdlut_generator_forward",
             "svdlut_generator_backward", "svdlut_generator_adam", "svdlut_mse", "svdlut_backward", "svdlut_backward_workspace_size", "svdlut_backward_noalloc",
-            "svdlut_apply_cfg", "svdlut_apply_original", "svdlut_apply_original_workspace_size", "svdlut_check_report", "svdlut_apply_host", "svdlut_apply_host_workspace_size", "svdlut_last_error", "svdlut_version"]
+            "svdlut_apply_cfg", "svdlut_apply_original", "svdlut_apply_original_workspace_size", "svdlut_check_report", "svdlut_apply_host", "svdlut_apply_host_workspace_size",
+            "svdlut_lut3d_apply", "svdlut_lut3d_workspace_size", "svdlut_lut3d_fit2d", "svdlut_last_error", "svdlut_version"]
