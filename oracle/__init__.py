@@ -63,6 +63,7 @@ def _load():
             lib.oracle_lut_from_svd.argtypes = [i, i, dp, dp, dp, dp]
             lib.oracle_quantize_u8.argtypes = [dp, ctypes.c_void_p, ctypes.c_size_t]
             lib.oracle_u8_to_unit.argtypes = [ctypes.c_void_p, dp, ctypes.c_size_t]
+            lib.oracle_u16_to_unit.argtypes = [ctypes.c_void_p, dp, ctypes.c_size_t]
             _lib = lib
     return _lib
 
@@ -185,6 +186,46 @@ def u8_to_unit(v):
     out = np.empty(v.shape, dtype=np.float64)
     _load().oracle_u8_to_unit(v.ctypes.data, _ptr(out), v.size)
     return out
+
+
+def u16_to_unit(v):
+    v = np.ascontiguousarray(v, dtype=np.uint16)
+    out = np.empty(v.shape, dtype=np.float64)
+    _load().oracle_u16_to_unit(v.ctypes.data, _ptr(out), v.size)
+    return out
+
+
+# Pixel formats of the I/O variants: planar [..][3][H][W] ("f32", "u8",
+# "u16") or interleaved [..][H][W][3] ("u8_hwc", "u16_hwc").
+PIXEL_FORMATS = ("f32", "u8", "u16", "u8_hwc", "u16_hwc")
+
+
+def decode(v, fmt):
+    """Pixels of format fmt -> planar FP64 in [0,1]: 8-bit codes v/255,
+    16-bit codes v/65535 (the 16-bit inputs of Sec. 5.1), float as is."""
+    if fmt not in PIXEL_FORMATS:
+        raise ValueError(fmt)
+    if fmt == "f32":
+        return _d(v)
+    x = u8_to_unit(v) if fmt.startswith("u8") else u16_to_unit(v)
+    if fmt.endswith("_hwc"):
+        x = np.moveaxis(x, -1, -3)
+    return np.ascontiguousarray(x)
+
+
+def encode(y, fmt):
+    """Planar FP64 result -> format fmt ("f32": as is; 8-bit: quantize_u8)."""
+    if fmt == "f32":
+        return _d(y)
+    if fmt not in ("u8", "u8_hwc"):
+        raise ValueError(f"no output encoding {fmt}")
+    q = quantize_u8(y)
+    return np.ascontiguousarray(np.moveaxis(q, -3, -1)) if fmt == "u8_hwc" else q
+
+
+def forward_io(dims, params, v, in_fmt, out_fmt, nthreads: int = 0):
+    """The forward (Eq. 10) between pixel formats: decode, transform, encode."""
+    return encode(forward(dims, params, decode(v, in_fmt), nthreads=nthreads), out_fmt)
 
 
 def quantize_u8(y):

@@ -546,6 +546,12 @@ void oracle_u8_to_unit(const uint8_t *v, double *out, size_t n)
     for (size_t i = 0; i < n; ++i) out[i] = (double)v[i] / 255.0;
 }
 
+/* 16-bit input (the 16-bit photos of Sec. 5.1): p = v / 65535. */
+void oracle_u16_to_unit(const uint16_t *v, double *out, size_t n)
+{
+    for (size_t i = 0; i < n; ++i) out[i] = (double)v[i] / 65535.0;
+}
+
 /* 8-bit output: round-half-even of clamp(Y,0,1)*255, decided in FP32 (the
  * precision the kernel computes Y in). */
 void oracle_quantize_u8(const double *y, uint8_t *out, size_t n)

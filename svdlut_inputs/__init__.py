@@ -101,6 +101,22 @@ def to_u8(img: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(np.rint(np.clip(img, 0, 1) * 255.0).astype(np.uint8))
 
 
+def to_u16(img: np.ndarray) -> np.ndarray:
+    """16-bit version of a [0,1] image: round(x*65535)."""
+    return np.round(np.clip(img, 0.0, 1.0) * 65535.0).astype(np.uint16)
+
+
+def make_image_u16(rng: np.random.Generator, H: int, W: int, mode: str = "mix") -> np.ndarray:
+    """Planar 16-bit codes [3][H][W] standing in for the 16-bit photo inputs
+    (linear light, so most codes are dark): make_image raised to 2.2."""
+    return to_u16(make_image(rng, H, W, mode=mode).astype(np.float64) ** 2.2)
+
+
+def to_hwc(img: np.ndarray) -> np.ndarray:
+    """Interleaved copy [..][H][W][3] of a planar image [..][3][H][W]."""
+    return np.ascontiguousarray(np.moveaxis(img, -3, -1))
+
+
 def identity_params(d: Dims, dtype=np.float64) -> dict:
     """Factors whose transform is the identity, with all grid terms off.
 
