@@ -293,6 +293,9 @@ def run_ours(args, world, rank, local):
                           "original_bytes_per_px": 60 + 8 * dd.K}
         del ws_o, yo
 
+    # ---- 16-bit and interleaved pixel formats on the same 4K frame ----
+    io_formats = run_io_variant(svdlut, torch, dev, stream, args, sets[0][0], sets[0][1], d)
+
     # ---- the 3D LUT of Eq. 3 against its best 2D-LUT fit (Eq. 4) on the same 4K image ----
     lut3d = run_lut3d_variant(svdlut, torch, dev, stream, args, sets[0][0])
 
@@ -349,7 +352,7 @@ def run_ours(args, world, rank, local):
                    "l2": f"rotating {N_SETS} input/output sets ({N_SETS * bytes_launch / 1e6:.0f} MB) > 129 MB L2"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
-                     "kernel": "apply_kernel<float, 16, false>", "bytes_per_launch": bytes_launch,
+                     "kernel": "apply_kernel<Io<InF32, OutF32>, 16, false>", "bytes_per_launch": bytes_launch,
                      "kernel_ms": round(kern_ms, 5), "peak_source": peak_src,
                      "kernel_sources_sha256_16": kernel_hash()},
         "e2e": {"value": round(job_throughput(world, mpix, e2e_ms), 1), "unit": "Mpix/s",
@@ -364,6 +367,7 @@ def run_ours(args, world, rank, local):
                      "f32_plain_4k_by_regime_Mpix/s": regimes,
                      "f32_plain_4k_paper_grids": paper_cfg,
                      "original_unfused_structure_4k": original,
+                     "io_formats_4k": io_formats,
                      "lut3d_vs_2d_fit_4k": lut3d,
                      "batched_16_ragged": batched,
                      "backward_8x1080p": backward,
@@ -385,6 +389,29 @@ def time_calls(fn, steps, stream, warmup=3):
     b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / steps
+
+
+def run_io_variant(svdlut, torch, dev, stream, args, x, p, d):
+    """svdlut_apply_io on the 4K frame: 16-bit planar and interleaved inputs
+    to 8-bit (and float) outputs, interleaved 8-bit in and out."""
+    H, W = x.shape[-2], x.shape[-1]
+    steps = max(3, args.steps // 2)
+    grids = algo_bytes_apply(H, W, d, 0)  # the parameter and grid bytes alone
+    xh = x.cpu().numpy().reshape(-1, 3, H, W)
+    v16, v8 = si.to_u16(xh), si.to_u8(xh)
+    dv = lambda a: torch.from_numpy(a).to(dev)  # noqa: E731
+    cases = {"u16->u8": (dv(v16), "u16", "u8", 9), "u16->f32": (dv(v16), "u16", "f32", 18),
+             "u16_hwc->u8_hwc": (dv(si.to_hwc(v16)), "u16_hwc", "u8_hwc", 9),
+             "u8_hwc->u8_hwc": (dv(si.to_hwc(v8)), "u8_hwc", "u8_hwc", 6)}
+    out = {}
+    for name, (xin, fi, fo, bpp) in cases.items():
+        y = svdlut.apply_io(xin, p, fi, fo)
+        ms = time_calls(lambda: svdlut.apply_io(xin, p, fi, fo, out=y), steps, stream)
+        out[name] = {"value": round(H * W / 1e6 / (ms / 1e3), 1), "unit": "Mpix/s", "ms": round(ms, 5),
+                     "GB/s": round((H * W * bpp + grids) / (ms / 1e3) / 1e9, 1), "io_bytes_per_px": bpp}
+        del y
+    out["workload"] = f"1x{W}x{H}, D_t=33 rank 8, K=8 grids at 1/8 res; inputs = the headline frame quantised"
+    return out
 
 
 def run_lut3d_variant(svdlut, torch, dev, stream, args, x):

@@ -331,6 +331,36 @@ svdlut_status svdlut_apply_original(const svdlut_dims *dims, const svdlut_params
 size_t svdlut_apply_original_workspace_size(const svdlut_dims *dims, int B, int H, int W);
 
 /*
+ * Pixel formats of svdlut_apply_io.  Planar formats are [B][3][H][W],
+ * interleaved (HWC) ones [B][H][W][3] with channels (r, g, b) per pixel.
+ * Integer inputs map code v to v / 255 (8-bit) or v / 65535 (16-bit);
+ * 8-bit outputs are rint(clamp(Y, 0, 1) * 255) as for SVDLUT_U8.  The
+ * 16-bit inputs are those of the tone-mapping and PPR10K tasks (Sec. 5.1).
+ */
+typedef enum {
+    SVDLUT_PIX_F32 = 0,     /* planar float                    */
+    SVDLUT_PIX_U8 = 1,      /* planar 8-bit                    */
+    SVDLUT_PIX_U16 = 2,     /* planar 16-bit (input only)      */
+    SVDLUT_PIX_U8_HWC = 3,  /* interleaved 8-bit               */
+    SVDLUT_PIX_U16_HWC = 4  /* interleaved 16-bit (input only) */
+} svdlut_pixfmt;
+
+/*
+ * svdlut_apply_io -- svdlut_apply between pixel formats: the same transform
+ * (Eq. 10, Supp. Eq. 22) with the input decoded and the output encoded inside
+ * the kernel.  Supported (input -> output) pairs:
+ *   F32 -> F32, U8 -> U8 (as svdlut_apply), U16 -> U8, U16 -> F32,
+ *   U8_HWC -> U8_HWC, U16_HWC -> U8_HWC.
+ * x and y are device arrays of B images of H x W in their formats and must not
+ * overlap; float arrays 4-byte aligned, 16-bit arrays 2-byte aligned.  W % 4
+ * == 0 with 16-byte aligned arrays enables the vector path.  Errors: those of
+ * svdlut_apply; UNSUPPORTED for any other pair of formats.
+ */
+svdlut_status svdlut_apply_io(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
+                              svdlut_pixfmt in_fmt, const void *x, svdlut_pixfmt out_fmt, void *y,
+                              svdlut_stream_t stream);
+
+/*
  * svdlut_lut3d_apply -- the 3D LUT transform the paper starts from (Eq. 3):
  * y_c = trilinear interpolation, at the clamped (r, g, b) of each pixel, of
  * the table t^c over the D x D x D vertex grid, for B images of H x W.

@@ -99,6 +99,56 @@ def apply(x, params, out=None, stream=None, ctas=None):
     return y[0] if squeeze else y
 
 
+# pixel formats of apply_io (svdlut_pixfmt): code, element dtypes, interleaved?
+PIXEL_FORMATS = {"f32": (0, ("float32",), False), "u8": (1, ("uint8",), False),
+                 "u16": (2, ("uint16", "int16"), False), "u8_hwc": (3, ("uint8",), True),
+                 "u16_hwc": (4, ("uint16", "int16"), True)}
+
+
+def _pix_tensor(t, fmt, what):
+    torch = _torch()
+    if fmt not in PIXEL_FORMATS:
+        raise ValueError(f"unknown pixel format {fmt!r}")
+    _, dts, hwc = PIXEL_FORMATS[fmt]
+    single = t.dim() == 3
+    tb = t.unsqueeze(0) if single else t
+    if tb.dim() != 4 or tb.shape[3 if hwc else 1] != 3:
+        raise ValueError(f"{what} must be {'[B,H,W,3]' if hwc else '[B,3,H,W]'} (or without B) for {fmt}")
+    if str(tb.dtype).replace("torch.", "") not in dts or not tb.is_cuda or not tb.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous CUDA tensor of {' or '.join(dts)} for {fmt}")
+    H, W = (tb.shape[1], tb.shape[2]) if hwc else (tb.shape[2], tb.shape[3])
+    return tb, single, H, W
+
+
+def apply_io(x, params, in_format, out_format, out=None, stream=None):
+    """The fused transform between pixel formats (svdlut_apply_io): 16-bit
+    ("u16", "u16_hwc") and 8-bit inputs are decoded and 8-bit outputs
+    encoded inside the kernel.  Formats: "f32", "u8", "u16" planar
+    [B,3,H,W]; "u8_hwc", "u16_hwc" interleaved [B,H,W,3].  Supported pairs:
+    u16->u8, u16->f32, u8_hwc->u8_hwc, u16_hwc->u8_hwc (and f32->f32,
+    u8->u8 as apply)."""
+    torch = _torch()
+    xb, single, H, W = _pix_tensor(x, in_format, "x")
+    B = xb.shape[0]
+    hwc_out = PIXEL_FORMATS.get(out_format, (0, (), False))[2]
+    if out is None:
+        if out_format not in ("f32", "u8", "u8_hwc"):
+            raise ValueError(f"no output encoding {out_format!r}")
+        dt = torch.float32 if out_format == "f32" else torch.uint8
+        out = torch.empty((B, H, W, 3) if hwc_out else (B, 3, H, W), dtype=dt, device=xb.device)
+        yb = out
+    else:
+        yb, _, Ho, Wo = _pix_tensor(out, out_format, "out")
+        if (yb.shape[0], Ho, Wo) != (B, H, W):
+            raise ValueError("out must hold the same images as x")
+    d = dims_of(params)
+    p = _param_struct(params, B, d)
+    _lib.check(_lib.load().svdlut_apply_io(ctypes.byref(d), ctypes.byref(p), B, H, W, PIXEL_FORMATS[in_format][0],
+                                           ctypes.c_void_p(xb.data_ptr()), PIXEL_FORMATS[out_format][0],
+                                           ctypes.c_void_p(yb.data_ptr()), _stream_ptr(stream)))
+    return yb[0] if single else yb
+
+
 _host_ws = {}
 
 

@@ -51,7 +51,7 @@ struct ImgDesc {
     int BH;           // block height (rows)
     int block_begin;  // first global block index of this image
     float rW1, rH1;   // 1/(W-1), 1/(H-1); 0 when W or H is 1
-    int vec;         // 16-byte (f32) / 4-byte (u8) vector I/O allowed
+    int vec;         // whole-lane vector loads and stores allowed (W % 4 == 0, aligned images)
 };
 
 template <int N>
@@ -221,6 +221,262 @@ struct PixIO<uint8_t> {
         if (n > 3) p[3] = w >> 24;
     }
 };
+
+// ---- pixel formats of the transform's input and output ----
+// A lane handles 4 pixels of a tile row: columns lane + 32 k (k < n) when the
+// input format has kStride (planar float: each warp-wide access covers 32
+// adjacent pixels), else columns lane * 4 + k.  `off` is the offset y * W + x
+// of the lane's first pixel, at(base, off) its address, `plane` = H * W.
+// load(at(..), plane, ..) fills Raw r[3] with the lane's pixels; unpack() turns them into the channel values (r, g, b) of the
+// 4 pixels.  kVecAlign: the alignment that makes the whole-lane vector access
+// legal (with W % 4 == 0).
+struct InF32 {  // planar float [3][H][W]
+    using Raw = float4;  // one per channel
+    static constexpr bool kStride = true;
+    static constexpr size_t kPixelBytes = 12, kVecAlign = 4;
+    static __device__ __forceinline__ const void *at(const void *base, size_t off)
+    {
+        return static_cast<const float *>(base) + off;
+    }
+    static __device__ __forceinline__ void load(const void *q, size_t plane, int n, bool, Raw *r)
+    {
+        const float *p = static_cast<const float *>(q);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = PixIO<float>::load_s(p + c * plane, n);
+    }
+    static __device__ __forceinline__ void unpack(const Raw *r, float4 (&v)[3])
+    {
+        v[0] = r[0];
+        v[1] = r[1];
+        v[2] = r[2];
+    }
+};
+
+struct InU8 {  // planar 8-bit [3][H][W], value v / 255
+    using Raw = unsigned int;  // one per channel, byte k = pixel k
+    static constexpr bool kStride = false;
+    static constexpr size_t kPixelBytes = 3, kVecAlign = 4;
+    static __device__ __forceinline__ const void *at(const void *base, size_t off)
+    {
+        return static_cast<const uint8_t *>(base) + off;
+    }
+    static __device__ __forceinline__ void load(const void *q, size_t plane, int n, bool vec, Raw *r)
+    {
+        const uint8_t *p = static_cast<const uint8_t *>(q);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = PixIO<uint8_t>::load(p + c * plane, n, vec);
+    }
+    static __device__ __forceinline__ void unpack(const Raw *r, float4 (&v)[3])
+    {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = PixIO<uint8_t>::to_float(r[c]);
+    }
+};
+
+// 16-bit code in a 32-bit word (half h) placed in the mantissa of 2^23, minus
+// 2^23: the exact integer as a float (no I2F).
+__device__ __forceinline__ float half_value(unsigned int w, int h)
+{
+    return __int_as_float(__byte_perm(w, 0x4B000000u, h ? 0x7432 : 0x7410)) - 8388608.0f;
+}
+
+// 2 bytes x 4 pixels at p (scalar below 4 pixels or when unaligned)
+__device__ __forceinline__ uint2 load_u16x4(const uint16_t *p, int n, bool vec)
+{
+    if (vec && n == 4) return __ldcs(reinterpret_cast<const uint2 *>(p));
+    unsigned int h[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k < n) h[k] = __ldcs(reinterpret_cast<const unsigned short *>(p + k));
+    return make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+}
+
+struct InU16 {  // planar 16-bit [3][H][W], value v / 65535
+    using Raw = uint2;  // one per channel: pixels (0, 1) and (2, 3)
+    static constexpr bool kStride = false;
+    static constexpr size_t kPixelBytes = 6, kVecAlign = 8;
+    static __device__ __forceinline__ const void *at(const void *base, size_t off)
+    {
+        return static_cast<const uint16_t *>(base) + off;
+    }
+    static __device__ __forceinline__ void load(const void *q, size_t plane, int n, bool vec, Raw *r)
+    {
+        const uint16_t *p = static_cast<const uint16_t *>(q);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = load_u16x4(p + c * plane, n, vec);
+    }
+    static __device__ __forceinline__ void unpack(const Raw *r, float4 (&v)[3])
+    {
+        const float k = 1.0f / 65535.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            v[c] = make_float4(half_value(r[c].x, 0) * k, half_value(r[c].x, 1) * k, half_value(r[c].y, 0) * k,
+                               half_value(r[c].y, 1) * k);
+    }
+};
+
+// byte b (0..3) of w as a float in [0, 255] (no I2F)
+__device__ __forceinline__ float byte_value(unsigned int w, int b)
+{
+    return __int_as_float(__byte_perm(w, 0x4B000000u, 0x7440 + b)) - 8388608.0f;
+}
+
+struct InU8Hwc {  // interleaved 8-bit [H][W][3], value v / 255
+    // 12 bytes of 4 pixels: r0 g0 b0 r1 | g1 b1 r2 g2 | b2 r3 g3 b3
+    using Raw = unsigned int;
+    static constexpr bool kStride = false;
+    static constexpr size_t kPixelBytes = 3, kVecAlign = 4;
+    static __device__ __forceinline__ const void *at(const void *base, size_t off)
+    {
+        return static_cast<const uint8_t *>(base) + 3 * off;
+    }
+    static __device__ __forceinline__ void load(const void *q, size_t, int n, bool vec, Raw *r)
+    {
+        const uint8_t *p = static_cast<const uint8_t *>(q);
+        if (vec && n == 4) {
+            const unsigned int *w = reinterpret_cast<const unsigned int *>(p);
+            r[0] = __ldcs(w);
+            r[1] = __ldcs(w + 1);
+            r[2] = __ldcs(w + 2);
+            return;
+        }
+        unsigned int w[3] = {0u, 0u, 0u};
+#pragma unroll
+        for (int i = 0; i < 12; ++i)
+            if (i < 3 * n) w[i >> 2] |= static_cast<unsigned int>(p[i]) << (8 * (i & 3));
+        r[0] = w[0];
+        r[1] = w[1];
+        r[2] = w[2];
+    }
+    static __device__ __forceinline__ void unpack(const Raw *r, float4 (&v)[3])
+    {
+        const float k = 1.0f / 255.0f;
+        v[0] = make_float4(byte_value(r[0], 0) * k, byte_value(r[0], 3) * k, byte_value(r[1], 2) * k,
+                           byte_value(r[2], 1) * k);
+        v[1] = make_float4(byte_value(r[0], 1) * k, byte_value(r[1], 0) * k, byte_value(r[1], 3) * k,
+                           byte_value(r[2], 2) * k);
+        v[2] = make_float4(byte_value(r[0], 2) * k, byte_value(r[1], 1) * k, byte_value(r[2], 0) * k,
+                           byte_value(r[2], 3) * k);
+    }
+};
+
+struct InU16Hwc {  // interleaved 16-bit [H][W][3], value v / 65535
+    // 24 bytes of 4 pixels as 6 words: (r0 g0) (b0 r1) | (g1 b1) (r2 g2) | (b2 r3) (g3 b3)
+    using Raw = uint2;
+    static constexpr bool kStride = false;
+    static constexpr size_t kPixelBytes = 6, kVecAlign = 8;
+    static __device__ __forceinline__ const void *at(const void *base, size_t off)
+    {
+        return static_cast<const uint16_t *>(base) + 3 * off;
+    }
+    static __device__ __forceinline__ void load(const void *q, size_t, int n, bool vec, Raw *r)
+    {
+        const uint16_t *p = static_cast<const uint16_t *>(q);
+        if (vec && n == 4) {
+            const uint2 *w = reinterpret_cast<const uint2 *>(p);
+            r[0] = __ldcs(w);
+            r[1] = __ldcs(w + 1);
+            r[2] = __ldcs(w + 2);
+            return;
+        }
+        unsigned int w[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int i = 0; i < 12; ++i)
+            if (i < 3 * n) w[i >> 1] |= static_cast<unsigned int>(__ldcs(reinterpret_cast<const unsigned short *>(p + i)))
+                                        << (16 * (i & 1));
+        r[0] = make_uint2(w[0], w[1]);
+        r[1] = make_uint2(w[2], w[3]);
+        r[2] = make_uint2(w[4], w[5]);
+    }
+    static __device__ __forceinline__ void unpack(const Raw *r, float4 (&v)[3])
+    {
+        const float k = 1.0f / 65535.0f;
+        v[0] = make_float4(half_value(r[0].x, 0) * k, half_value(r[0].y, 1) * k, half_value(r[1].y, 0) * k,
+                           half_value(r[2].x, 1) * k);
+        v[1] = make_float4(half_value(r[0].x, 1) * k, half_value(r[1].x, 0) * k, half_value(r[1].y, 1) * k,
+                           half_value(r[2].y, 0) * k);
+        v[2] = make_float4(half_value(r[0].y, 0) * k, half_value(r[1].x, 1) * k, half_value(r[2].x, 0) * k,
+                           half_value(r[2].y, 1) * k);
+    }
+};
+
+// Outputs: o[c][k] = channel c of the lane's pixel k.  STRIDE: the lane
+// mapping of the input format.
+struct OutF32 {  // planar float
+    static constexpr size_t kPixelBytes = 12, kVecAlign = 16;
+    template <bool STRIDE>
+    static __device__ __forceinline__ void store(void *base, size_t plane, size_t off, const float (&o)[3][4], int n,
+                                                 bool vec)
+    {
+        float *p = static_cast<float *>(base) + off;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 v = make_float4(o[c][0], o[c][1], o[c][2], o[c][3]);
+            if constexpr (STRIDE) PixIO<float>::store_s(p + c * plane, v, n);
+            else PixIO<float>::store(p + c * plane, v, n, vec);
+        }
+    }
+};
+
+struct OutU8 {  // planar 8-bit, rint(clamp(y, 0, 1) * 255)
+    static constexpr size_t kPixelBytes = 3, kVecAlign = 4;
+    template <bool STRIDE>
+    static __device__ __forceinline__ void store(void *base, size_t plane, size_t off, const float (&o)[3][4], int n,
+                                                 bool vec)
+    {
+        static_assert(!STRIDE, "8-bit output needs adjacent pixels per lane");
+        uint8_t *p = static_cast<uint8_t *>(base) + off;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            PixIO<uint8_t>::store(p + c * plane, make_float4(o[c][0], o[c][1], o[c][2], o[c][3]), n, vec);
+    }
+};
+
+// bytes (a, b, c, d) -> one word, each the low byte of its argument
+__device__ __forceinline__ unsigned int pack4(unsigned int a, unsigned int b, unsigned int c, unsigned int d)
+{
+    return __byte_perm(__byte_perm(a, b, 0x0040), __byte_perm(c, d, 0x0040), 0x5410);
+}
+
+struct OutU8Hwc {  // interleaved 8-bit, rint(clamp(y, 0, 1) * 255)
+    static constexpr size_t kPixelBytes = 3, kVecAlign = 4;
+    template <bool STRIDE>
+    static __device__ __forceinline__ void store(void *base, size_t, size_t off, const float (&o)[3][4], int n,
+                                                 bool vec)
+    {
+        static_assert(!STRIDE, "8-bit output needs adjacent pixels per lane");
+        uint8_t *p = static_cast<uint8_t *>(base) + 3 * off;
+        unsigned int q[3][4];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[c][k] = quant_u8_bits(o[c][k]);
+        const unsigned int w0 = pack4(q[0][0], q[1][0], q[2][0], q[0][1]);
+        const unsigned int w1 = pack4(q[1][1], q[2][1], q[0][2], q[1][2]);
+        const unsigned int w2 = pack4(q[2][2], q[0][3], q[1][3], q[2][3]);
+        if (vec && n == 4) {
+            unsigned int *w = reinterpret_cast<unsigned int *>(p);
+            __stcs(w, w0);
+            __stcs(w + 1, w1);
+            __stcs(w + 2, w2);
+            return;
+        }
+        const unsigned int w[3] = {w0, w1, w2};
+#pragma unroll
+        for (int i = 0; i < 12; ++i)
+            if (i < 3 * n) p[i] = static_cast<uint8_t>(w[i >> 2] >> (8 * (i & 3)));
+    }
+};
+
+template <class IN, class OUT>
+struct Io {
+    using In = IN;
+    using Out = OUT;
+    static_assert(!IN::kStride || std::is_same<OUT, OutF32>::value, "strided lanes need float output");
+};
+
+using IoF32 = Io<InF32, OutF32>;
+using IoU8 = Io<InU8, OutU8>;
 
 __device__ __forceinline__ float get(const float4 &v, int k)
 {
@@ -527,7 +783,7 @@ __device__ __forceinline__ void lut_pair(const float4 *__restrict__ q, float da,
 // d delta_alpha) per output channel (weights already folded in); the xc / yc
 // terms add (Dsc-1) (s1 - s0) for their channel; zero where the input was
 // clamped (outside [0,1]).
-template <typename T, int N, bool DX>
+template <class IO, int N, bool DX>
 __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constant__ LaunchArgs<N> a)
 {
     extern __shared__ __align__(16) float smem[];
@@ -552,12 +808,15 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
     }
     if (blk >= b_end) return;
 
-    using Raw = typename PixIO<T>::Raw;
+    using In = typename IO::In;
+    using Out = typename IO::Out;
+    using Raw = typename In::Raw;
+    static_assert(!DX || std::is_same<IO, IoF32>::value, "the adjoint takes float images");
     // Pixel k of a lane in a 128-pixel tile row: column lane + 32 k for float
     // images (each warp-wide access covers 32 adjacent pixels, so lanes of a
-    // coherent region gather the same table cells), lane * 4 + k for 8-bit
-    // images (one 32-bit load or store per lane and plane).
-    constexpr bool kStride = std::is_same<T, float>::value;
+    // coherent region gather the same table cells), lane * 4 + k for integer
+    // images (one 32- or 64-bit access per lane and plane or word).
+    constexpr bool kStride = In::kStride;
     auto lane_px = [&](int W, int x0, int &x) {
         x = x0 + (kStride ? lane : lane * 4);
         if (kStride) return x < W ? min(4, (W - x + 31) >> 5) : 0;
@@ -579,12 +838,12 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         const int n = lane_px(d.W, strip * kTileW, x);
         const int y = d.y_begin + band * d.BH + row;
         const size_t plane = static_cast<size_t>(d.H) * d.W;
-        const T *src = static_cast<const T *>(d.x) + static_cast<size_t>(y) * d.W + x;
         const bool ok = row < d.BH && y < d.y_end && n > 0;
+        if (ok) {
+            In::load(In::at(d.x, static_cast<size_t>(y) * d.W + x), plane, n, d.vec, dst);
+        } else {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if constexpr (kStride) dst[c] = ok ? PixIO<T>::load_s(src + c * plane, n) : Raw();
-            else dst[c] = ok ? PixIO<T>::load(src + c * plane, n, d.vec) : Raw();
+            for (int c = 0; c < 3; ++c) dst[c] = Raw();
         }
         if constexpr (DX) {
             const float *g = d.dy + static_cast<size_t>(y) * d.W + x;
@@ -634,20 +893,20 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         }
         const int xcs = (g.nvx - 1) * Dsc;  // float4 per channel of pxc
         const size_t plane = static_cast<size_t>(d.H) * d.W;
-        T *dst = static_cast<T *>(d.y);
-        // this lane's pixels in row 0 of the block (input, and dy for the adjoint)
-        const T *xrow = static_cast<const T *>(d.x) + static_cast<size_t>(g.y0) * d.W + xbase;
-        const float *grow = DX ? d.dy + static_cast<size_t>(g.y0) * d.W + xbase : nullptr;
+        // offset of this lane's pixels in row 0 of the block (input, and dy for the adjoint)
+        const size_t off0 = static_cast<size_t>(g.y0) * d.W + xbase;
+        const void *xrow = In::at(d.x, off0);
+        const float *grow = DX ? d.dy + off0 : nullptr;
 #pragma unroll 1
         for (int row = warp; row < g.rows; row += kWarps) {
             // next row of this warp, possibly in the next block
             if (row + kWarps < g.rows) {
                 const size_t ro = static_cast<size_t>(row + kWarps) * d.W;
+                if (n > 0) {
+                    In::load(In::at(xrow, ro), plane, n, d.vec, nxt);
+                } else {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (n <= 0) nxt[c] = Raw();
-                    else if constexpr (kStride) nxt[c] = PixIO<T>::load_s(xrow + ro + c * plane, n);
-                    else nxt[c] = PixIO<T>::load(xrow + ro + c * plane, n, d.vec);
+                    for (int c = 0; c < 3; ++c) nxt[c] = Raw();
                 }
                 if constexpr (DX) {
 #pragma unroll
@@ -660,7 +919,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
             const int y = g.y0 + row;
             warp_row_tables(g, b, Dsc, row);
             __syncwarp();
-            if (n > 0 && !DX) {
+            if (!DX && n > 0) {
                 // adjacent pixels (8-bit images) usually span at most two x-cells: 3 vertices
                 const bool xy_fast = !kStride && ixl[3] - ixl[0] <= 1;
                 float4 xa, xb, xc;
@@ -669,9 +928,9 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                     xb = b.rxy[ixl[0] + 1];
                     xc = b.rxy[min(ixl[0] + 2, g.nvx - 1)];
                 }
-                const float4 pr = PixIO<T>::to_float(cur[0]);
-                const float4 pg = PixIO<T>::to_float(cur[1]);
-                const float4 pb = PixIO<T>::to_float(cur[2]);
+                float4 pv[3];
+                In::unpack(cur, pv);
+                const float4 pr = pv[0], pg = pv[1], pb = pv[2];
                 float out[3][4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -712,23 +971,15 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                         out[c][k] = fmaf(sl, ec[c], yy[c] + s0);
                     }
                 }
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                {
-                    T *o = dst + c * plane + static_cast<size_t>(y) * d.W + xbase;
-                    const float4 v = make_float4(out[c][0], out[c][1], out[c][2], out[c][3]);
-                    if constexpr (kStride) PixIO<T>::store_s(o, v, n);
-                    else PixIO<T>::store(o, v, n, d.vec);
-                }
+                Out::template store<kStride>(d.y, plane, static_cast<size_t>(y) * d.W + xbase, out, n, d.vec);
             }
-            if (n > 0 && DX) {
+            if constexpr (DX) {
+            if (n > 0) {
                 float outd[3][4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    float xv[3] = {get(PixIO<T>::to_float(cur[0]), k), get(PixIO<T>::to_float(cur[1]), k),
-                                   get(PixIO<T>::to_float(cur[2]), k)};
-                    const float gy[3] = {get(PixIO<T>::to_float(cur[3]), k), get(PixIO<T>::to_float(cur[4]), k),
-                                         get(PixIO<T>::to_float(cur[5]), k)};
+                    float xv[3] = {get(cur[0], k), get(cur[1], k), get(cur[2], k)};
+                    const float gy[3] = {get(cur[3], k), get(cur[4], k), get(cur[5], k)};
                     float p[3], dc[3], ec[3], gp[3] = {0.f, 0.f, 0.f};
                     int ic[3], jc[3];
 #pragma unroll
@@ -767,6 +1018,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                 for (int c = 0; c < 3; ++c)
                     PixIO<float>::store_s(reinterpret_cast<float *>(d.y) + c * plane + static_cast<size_t>(y) * d.W + xbase,
                                           make_float4(outd[c][0], outd[c][1], outd[c][2], outd[c][3]), n);
+            }
             }
             __syncwarp();  // row tables are rewritten for the next row
 #pragma unroll

@@ -17,6 +17,10 @@ svdlut_status check_params(const svdlut_dims *d, const svdlut_params *p);
 size_t param_stride(const svdlut_dims *d, int which);
 ImgDesc make_desc(const svdlut_dims *d, const svdlut_params *p, int b, int H, int W, svdlut_dtype dt,
                   const void *x, void *y);
+// x_px_bytes / y_px_bytes: bytes of one pixel (all three channels) of the
+// input / output format; x_align / y_align: alignment of its vector access
+ImgDesc make_desc_io(const svdlut_dims *d, const svdlut_params *p, int b, int H, int W, const void *x,
+                     size_t x_px_bytes, size_t x_align, void *y, size_t y_px_bytes, size_t y_align);
 
 // Shared-memory bytes of args a for block heights up to bh_max; the
 // all-nine-tables prologue is enabled when it fits.  Sets lcell/scratch sizes.
@@ -106,16 +110,16 @@ inline svdlut_status allow_smem_once(const void *fn, int max_smem, int device)
     return SVDLUT_OK;
 }
 
-template <typename T, int N, bool DX>
+template <class IO, int N, bool DX>
 svdlut_status launch_apply_t(LaunchArgs<N> &a, size_t smem, int sm_count, int max_smem, int device,
                              cudaStream_t s, int grid)
 {
-    svdlut_status st = allow_smem_once(reinterpret_cast<const void *>(apply_kernel<T, N, DX>), max_smem, device);
+    svdlut_status st = allow_smem_once(reinterpret_cast<const void *>(apply_kernel<IO, N, DX>), max_smem, device);
     if (st != SVDLUT_OK) return st;
     if ((st = check_buffer(&a.check)) != SVDLUT_OK) return st;
     if (grid <= 0) grid = std::min(a.total_blocks, sm_count);
     grid = std::max(1, std::min(grid, a.total_blocks));
-    apply_kernel<T, N, DX><<<grid, kThreads, smem, s>>>(a);
+    apply_kernel<IO, N, DX><<<grid, kThreads, smem, s>>>(a);
     SVDLUT_CUDA_TRY(cudaGetLastError());
     return SVDLUT_OK;
 }
@@ -130,10 +134,10 @@ svdlut_status launch_apply(LaunchArgs<N> &a, size_t smem, svdlut_dtype dt, cudaS
     DeviceInfo di;
     svdlut_status st = device_info(&di);
     if (st != SVDLUT_OK) return st;
-    if (dx_mode) return launch_apply_t<float, N, true>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid);
+    if (dx_mode) return launch_apply_t<IoF32, N, true>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid);
     return dt == SVDLUT_F32
-               ? launch_apply_t<float, N, false>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid)
-               : launch_apply_t<uint8_t, N, false>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid);
+               ? launch_apply_t<IoF32, N, false>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid)
+               : launch_apply_t<IoU8, N, false>(a, smem, di.sm_count, di.max_smem_optin, di.device, s, grid);
 }
 
 }  // namespace svdlut

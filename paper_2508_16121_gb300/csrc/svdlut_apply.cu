@@ -35,14 +35,13 @@ size_t param_stride(const svdlut_dims *d, int which)
     }
 }
 
-ImgDesc make_desc(const svdlut_dims *d, const svdlut_params *p, int b, int H, int W, svdlut_dtype dt,
-                  const void *x, void *y)
+ImgDesc make_desc_io(const svdlut_dims *d, const svdlut_params *p, int b, int H, int W, const void *x,
+                     size_t x_px_bytes, size_t x_align, void *y, size_t y_px_bytes, size_t y_align)
 {
     ImgDesc e{};
-    const size_t es = dt == SVDLUT_F32 ? 4 : 1;
-    const size_t img = static_cast<size_t>(3) * H * W * es;
-    e.x = static_cast<const char *>(x) + b * img;
-    e.y = static_cast<char *>(y) + b * img;
+    const size_t px = static_cast<size_t>(H) * W;
+    e.x = static_cast<const char *>(x) + b * px * x_px_bytes;
+    e.y = static_cast<char *>(y) + b * px * y_px_bytes;
     e.U = p->U + b * param_stride(d, 0);
     e.S = p->S + b * param_stride(d, 1);
     e.V = p->V + b * param_stride(d, 2);
@@ -63,9 +62,15 @@ ImgDesc make_desc(const svdlut_dims *d, const svdlut_params *p, int b, int H, in
     e.Dsc = d->Dsc;
     e.rW1 = W > 1 ? 1.0f / static_cast<float>(W - 1) : 0.f;
     e.rH1 = H > 1 ? 1.0f / static_cast<float>(H - 1) : 0.f;
-    const size_t va = dt == SVDLUT_F32 ? 16 : 4;
-    e.vec = (W % 4 == 0) && aligned(e.x, va) && aligned(e.y, va);
+    e.vec = (W % 4 == 0) && aligned(e.x, x_align) && aligned(e.y, y_align);
     return e;
+}
+
+ImgDesc make_desc(const svdlut_dims *d, const svdlut_params *p, int b, int H, int W, svdlut_dtype dt,
+                  const void *x, void *y)
+{
+    const size_t es = dt == SVDLUT_F32 ? 4 : 1, va = dt == SVDLUT_F32 ? 16 : 4;
+    return make_desc_io(d, p, b, H, W, x, 3 * es, va, y, 3 * es, va);
 }
 
 }  // namespace svdlut

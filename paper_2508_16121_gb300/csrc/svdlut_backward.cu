@@ -4,7 +4,7 @@
 // and prints no derivative; everything here is the exact derivative of the
 // forward map of Eq. 10 / Supp. Eqs. 12-22.  Passes (all on the caller's
 // stream, no atomics, every sum in a fixed order -> bitwise repeatable):
-//   1. dx      : apply_kernel<float, N, true> (slopes of the same cells).
+//   1. dx      : apply_kernel<IoF32, N, true> (slopes of the same cells).
 //   2. lut     : lut_grad_kernel scatters dy * bilinear weights into
 //                warp-private tables G_p[i][j][c] (one LUT pair, all three
 //                output channels per warp: one key match per pixel and pair),

@@ -1,0 +1,131 @@
+"""GPU parity of the transform between pixel formats (svdlut_apply_io): the
+16-bit inputs of the tone-mapping and PPR10K tasks (Sec. 5.1) and
+interleaved 8-bit frames, against the oracle's decode / transform / encode,
+and against the planar float and 8-bit paths (decoding inside the kernel
+must not change a single bit)."""
+import numpy as np
+import pytest
+
+import oracle
+import svdlut_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5  # float outputs, max-abs against FP64
+
+
+@pytest.fixture(scope="module")
+def sv():
+    import torch
+    import paper_2508_16121_gb300 as svdlut
+    from paper_2508_16121_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return svdlut
+
+
+def _case(seed, B, H, W, d=None):
+    d = d or si.spatial_dims(H, W)
+    rng = np.random.default_rng(seed)
+    v = np.stack([si.make_image_u16(rng, H, W) for _ in range(B)])
+    _, p = si.make_batch(seed, B, H, W, d)
+    return d, v, p
+
+
+def _cuda(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _lsb_check(y, ref):
+    diff = np.abs(y.astype(int) - ref.astype(int))
+    assert diff.max() <= 1
+    assert (diff > 0).mean() < 1e-3
+
+
+SIZES = [(1, 1, 1), (2, 37, 130), (1, 67, 257), (1, 64, 128), (1, 3, 5)]
+
+
+@pytest.mark.parametrize("B,H,W", SIZES)
+def test_u16_to_u8(sv, B, H, W):
+    d, v, p = _case(40 + H + W, B, H, W)
+    y = sv.apply_io(_cuda(v), sv.to_device(p), "u16", "u8").cpu().numpy()
+    _lsb_check(y, oracle.forward_io(d, p, v, "u16", "u8"))
+
+
+@pytest.mark.parametrize("B,H,W", SIZES)
+def test_u16_to_f32_and_bitwise_equal_to_the_float_path(sv, B, H, W):
+    d, v, p = _case(50 + H + W, B, H, W)
+    pd = sv.to_device(p)
+    y = sv.apply_io(_cuda(v), pd, "u16", "f32").cpu().numpy()
+    assert np.abs(y - oracle.forward_io(d, p, v, "u16", "f32")).max() <= TOL
+    # the kernel decodes v as float(v) * float(1/65535): the float path on those inputs
+    xf = v.astype(np.float32) * (np.float32(1.0) / np.float32(65535.0))
+    yf = sv.apply(_cuda(xf), pd).cpu().numpy()
+    assert np.array_equal(y, yf)
+
+
+@pytest.mark.parametrize("B,H,W", SIZES)
+def test_u8_hwc_equals_planar_u8(sv, B, H, W):
+    d = si.spatial_dims(H, W)
+    x, p = si.make_batch(60 + H + W, B, H, W, d)
+    x8 = si.to_u8(x)
+    pd = sv.to_device(p)
+    y = sv.apply_io(_cuda(si.to_hwc(x8)), pd, "u8_hwc", "u8_hwc").cpu().numpy()
+    y_planar = sv.apply(_cuda(x8), pd).cpu().numpy()
+    assert np.array_equal(y, si.to_hwc(y_planar))
+    _lsb_check(y, oracle.forward_io(d, p, si.to_hwc(x8), "u8_hwc", "u8_hwc"))
+
+
+@pytest.mark.parametrize("B,H,W", SIZES)
+def test_u16_hwc_equals_planar_u16(sv, B, H, W):
+    d, v, p = _case(70 + H + W, B, H, W)
+    pd = sv.to_device(p)
+    y = sv.apply_io(_cuda(si.to_hwc(v)), pd, "u16_hwc", "u8_hwc").cpu().numpy()
+    y_planar = sv.apply_io(_cuda(v), pd, "u16", "u8").cpu().numpy()
+    assert np.array_equal(y, si.to_hwc(y_planar))
+    _lsb_check(y, oracle.forward_io(d, p, si.to_hwc(v), "u16_hwc", "u8_hwc"))
+
+
+def test_paper_dims_and_unaligned_views(sv):
+    """K=6 grids of 17^3 on a 4-aligned width, and the same images at an odd
+    element offset (scalar path): identical results."""
+    import torch
+    B, H, W = 2, 40, 96
+    d, v, p = _case(80, B, H, W, si.paper_dims())
+    pd = sv.to_device(p)
+    y = sv.apply_io(_cuda(v), pd, "u16", "u8")
+    buf = torch.zeros(v.size + 1, dtype=torch.uint16, device="cuda")
+    xv = buf[1:].view(v.shape)
+    xv.copy_(_cuda(v))
+    out = torch.zeros(B * 3 * H * W + 1, dtype=torch.uint8, device="cuda")
+    yv = out[1:].view(B, 3, H, W)
+    sv.apply_io(xv, pd, "u16", "u8", out=yv)
+    assert torch.equal(y, yv)
+    _lsb_check(y.cpu().numpy(), oracle.forward_io(d, p, v, "u16", "u8"))
+    hv = torch.zeros(v.size + 1, dtype=torch.uint16, device="cuda")[1:].view(B, H, W, 3)
+    hv.copy_(_cuda(si.to_hwc(v)))
+    yh = sv.apply_io(hv, pd, "u16_hwc", "u8_hwc")
+    assert torch.equal(yh, y.permute(0, 2, 3, 1))
+
+
+def test_4k_u16_to_u8_frame(sv):
+    H, W = 2160, 3840
+    d, v, p = _case(si.config_seed(1), 1, H, W)
+    y = sv.apply_io(_cuda(v), sv.to_device(p), "u16", "u8").cpu().numpy()
+    _lsb_check(y, oracle.forward_io(d, p, v, "u16", "u8"))
+
+
+def test_unsupported_pairs_and_bad_formats(sv):
+    import torch
+    from paper_2508_16121_gb300._lib import SvdlutError
+    d = si.spatial_dims(8, 8)
+    _, p = si.make_batch(1, 1, 8, 8, d)
+    pd = sv.to_device(p)
+    x8 = torch.zeros(1, 3, 8, 8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(SvdlutError):
+        sv.apply_io(x8, pd, "u8", "f32", out=torch.empty(1, 3, 8, 8, device="cuda"))
+    with pytest.raises(ValueError):
+        sv.apply_io(x8, pd, "u8", "u16")
+    with pytest.raises(ValueError):
+        sv.apply_io(x8, pd, "u16", "u8")  # wrong element type for u16
