@@ -7,7 +7,8 @@ its Python binding) never calls it, and it shares no code with it.
 ``svdlut_oracle.c`` holds the arithmetic (Eq. 9 reconstruction, Supp.
 Eqs. 12-22 transform and slicing, and their adjoint); this module compiles
 it with gcc and marshals numpy arrays.  ``generator.py`` holds the FP64
-oracle of the learned factor generator (Supp. Tables 8-12).
+oracle of the learned factor generator (Supp. Tables 8-12), ``cie94.py`` the
+colour-difference term of the training loss (Eq. 11).
 
 Parity status: forward and adjoint are pinned (tests/test_oracle_*.py);
 the generator's numeric outputs are "parity unpinned" beyond the paper's
