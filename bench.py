@@ -604,6 +604,13 @@ def run_learned_variant(svdlut, torch, dev, stream, args):
     b_.record(stream)
     torch.cuda.synchronize()
     t_tr = a_.elapsed_time(b_) / n_tr
+    # the loss terms of that step alone: MSE, then CIE94 added into the same gradient
+    xb, ytb = tr.pair(1)
+    yb = svdlut.apply(xb, tr.student.forward(xb))
+    dyb, ws_l = torch.empty_like(yb), torch.empty(4096, dtype=torch.uint8, device=dev)
+    t_mse = time_calls(lambda: svdlut.mse(yb, ytb, dyb, ws=ws_l), steps, stream)
+    t_cie = time_calls(lambda: svdlut.cie94(yb, ytb, svdlut.CIE94_WEIGHT, dy=dyb, accumulate=True, ws=ws_l),
+                       steps, stream)
     return {"workload": "4 x 3840x2160 FP32, K=8 grids 17^3, D_t=33 rank 8",
             "generator_plus_apply_graph": {"value": round(mpix / (t_l / 1e3), 1), "unit": "Mpix/s",
                                            "ms": round(t_l, 4)},
@@ -621,6 +628,9 @@ def run_learned_variant(svdlut, torch, dev, stream, args):
                                          "CTAs on the rest)",
                                   "speedup_vs_plain_graph": round(t_p / t_pipe, 3)},
             "train_step_ms_batch64_256px": round(t_tr, 3),
+            "train_loss": "MSE + 0.005 CIE94 (Eq. 11 without LPIPS)",
+            "loss_terms_ms_batch64_256px": {"mse_and_grad": round(t_mse, 4), "cie94_and_grad": round(t_cie, 4),
+                                            "cie94_Mpix/s": round(64 * 256 * 256 / 1e6 / (t_cie / 1e3), 1)},
             "train_pairs_per_s": round(64 / (t_tr / 1e3), 1)}
 
 

@@ -284,6 +284,22 @@ svdlut_status svdlut_mse(const float *y, const float *target, size_t n, float *d
                          size_t ws_bytes, svdlut_stream_t stream);
 
 /*
+ * svdlut_cie94 -- the colour-difference term of the training loss (Eq. 11,
+ * weight lambda_c = 0.005 in the paper): *loss = mean over the B*H*W pixels
+ * of the CIE94 difference between y and the reference `target` in CIELAB:
+ *   sRGB decoding (IEC 61966-2-1) of the raw values, XYZ by the matrix of the
+ *   sRGB primaries and the D65 white (0.3127, 0.3290), CIELAB relative to
+ *   that white, CIE94 with kL = kC = kH = 1, K1 = 0.045, K2 = 0.015 and
+ *   S_C, S_H from the reference's chroma.
+ * If dy is not NULL, weight * d(*loss)/dy is written to dy (accumulate = 0)
+ * or added to it (accumulate != 0); the gradient is 0 where the difference
+ * is 0.  y, target, dy: [B][3][H][W] float device arrays; loss: one device
+ * float; ws: at least 4096 bytes of device scratch.  Deterministic.
+ */
+svdlut_status svdlut_cie94(const float *y, const float *target, int B, int H, int W, float weight, float *dy,
+                           int accumulate, float *loss, void *ws, size_t ws_bytes, svdlut_stream_t stream);
+
+/*
  * svdlut_backward_noalloc -- svdlut_backward for callers that cannot allocate
  * device memory.  The paper has no counterpart; this is a library service.
  *

@@ -554,6 +554,32 @@ def adam_step(weights, grads, m, v, step, lr=1e-4, beta1=0.9, beta2=0.999, eps=1
                                          lr, beta1, beta2, eps, int(step), _stream_ptr(stream)))
 
 
+CIE94_WEIGHT = 0.005  # lambda_c of the training loss (Eq. 11)
+
+
+def cie94(y, target, weight=1.0, dy=None, accumulate=False, ws=None, stream=None):
+    """Colour-difference term of the loss (svdlut_cie94): mean CIE94 Delta E
+    between y and the reference target, float32 CUDA [B,3,H,W] or [3,H,W]
+    sRGB images, as a 0-d CUDA tensor; if dy is given, weight times the
+    gradient is written into it (added to it with accumulate=True)."""
+    torch = _torch()
+    yb = y.unsqueeze(0) if y.dim() == 3 else y
+    tb = target.unsqueeze(0) if target.dim() == 3 else target
+    for t, what in ((yb, "y"), (tb, "target")):
+        if t.dim() != 4 or t.shape[1] != 3 or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{what} must be a contiguous float32 CUDA tensor [B,3,H,W] or [3,H,W]")
+    if yb.shape != tb.shape or (dy is not None and (dy.numel() != yb.numel() or not dy.is_contiguous())):
+        raise ValueError("y, target and dy must have the same shape")
+    B, _, H, W = yb.shape
+    loss = torch.empty((), dtype=torch.float32, device=y.device)
+    ws = ws if ws is not None else torch.empty(4096, dtype=torch.uint8, device=y.device)
+    _lib.check(_lib.load().svdlut_cie94(ctypes.c_void_p(yb.data_ptr()), ctypes.c_void_p(tb.data_ptr()), B, H, W,
+                                        float(weight), ctypes.c_void_p(dy.data_ptr()) if dy is not None else None,
+                                        int(bool(accumulate)), ctypes.c_void_p(loss.data_ptr()),
+                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+    return loss
+
+
 def mse(y, target, dy=None, ws=None, stream=None):
     """MSE loss (0-d CUDA tensor) and, into dy if given, its gradient."""
     torch = _torch()

@@ -121,6 +121,9 @@ def _declare(lib):
     lib.svdlut_apply_host.restype = c_int
     lib.svdlut_apply_host_workspace_size.argtypes = [c_int, c_int, c_int, c_int]
     lib.svdlut_apply_host_workspace_size.restype = c_size_t
+    lib.svdlut_cie94.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, ctypes.c_float, c_void_p, c_int, c_void_p,
+                                 c_void_p, c_size_t, c_void_p]
+    lib.svdlut_cie94.restype = c_int
     lib.svdlut_apply_io.argtypes = [P(Dims), P(Params), c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p,
                                     c_void_p]
     lib.svdlut_apply_io.restype = c_int
@@ -151,4 +154,4 @@ EXPORTED = ["svdlut_apply", "svdlut_apply_batched", "svdlut_batched_workspace_si
             "svdlut_generator_param_count", "svdlut_generator_workspace_size", "svdlut_generator_forward",
             "svdlut_generator_backward", "svdlut_generator_adam", "svdlut_mse", "svdlut_backward", "svdlut_backward_workspace_size", "svdlut_backward_noalloc",
             "svdlut_apply_cfg", "svdlut_apply_original", "svdlut_apply_original_workspace_size", "svdlut_check_report", "svdlut_apply_host", "svdlut_apply_host_workspace_size",
-            "svdlut_apply_io", "svdlut_lut3d_apply", "svdlut_lut3d_workspace_size", "svdlut_lut3d_fit2d", "svdlut_last_error", "svdlut_version"]
+            "svdlut_apply_io", "svdlut_cie94", "svdlut_lut3d_apply", "svdlut_lut3d_workspace_size", "svdlut_lut3d_fit2d", "svdlut_last_error", "svdlut_version"]

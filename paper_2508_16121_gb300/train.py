@@ -5,9 +5,11 @@ Adam (Sec. 4.2; loss Eq. 11, whose MSE term is used here).  Its photo datasets
 are not available, so the training pairs are made by the transform itself:
 a frozen, seeded teacher generator (identity-biased output layer, final
 weights N(0, teacher_scale)) predicts image-dependent parameters, svdlut_apply
-renders the target.  Every step runs in the library's kernels:
+renders the target.  The loss is Eq. 11 without its LPIPS term: MSE plus
+lambda_c = 0.005 times the CIE94 colour difference.  Every step runs in the
+library's kernels:
   student forward (svdlut_generator_forward, dropout on)
-  -> svdlut_apply -> svdlut_mse (loss and dy)
+  -> svdlut_apply -> svdlut_mse + svdlut_cie94 (loss and dy)
   -> svdlut_backward (parameter gradients)
   -> svdlut_generator_backward -> svdlut_generator_adam.
 Data and dropout are seeded per step, so a run resumed from a checkpoint
@@ -22,7 +24,7 @@ import numpy as np
 
 import svdlut_inputs as si
 
-from . import Generator, PARAM_NAMES, adam_step, apply, backward, mse
+from . import CIE94_WEIGHT, Generator, PARAM_NAMES, adam_step, apply, backward, cie94, mse
 
 
 def _torch():
@@ -32,9 +34,10 @@ def _torch():
 
 class Trainer:
     def __init__(self, K=8, batch=64, size=256, lr=1e-3, seed=0, teacher_seed=1, teacher_scale=0.1,
-                 data_seed=2, device="cuda"):
+                 data_seed=2, device="cuda", cie94_weight=CIE94_WEIGHT):
         torch = _torch()
         self.K, self.batch, self.size, self.lr = K, batch, size, lr
+        self.cie94_weight = float(cie94_weight)
         self.device = torch.device(device)
         self.data_seed = data_seed
         w0 = si.generator_init(K, np.random.default_rng(seed), 0.0)
@@ -68,6 +71,8 @@ class Trainer:
         sp = self.student.forward(x, training=True, seed=self.step)
         y = apply(x, sp)
         loss = mse(y, yt, self.dy)
+        if self.cie94_weight:
+            loss = loss + self.cie94_weight * cie94(y, yt, self.cie94_weight, dy=self.dy, accumulate=True)
         g = backward(x, sp, self.dy, want=tuple("d" + n for n in PARAM_NAMES), workspace=self.bwd_ws)
         self.student.backward({n: g["d" + n] for n in PARAM_NAMES}, dweights=self.dw)
         adam_step(self.student.weights, self.dw, self.m, self.v, self.step, lr=self.lr)
@@ -85,7 +90,7 @@ class Trainer:
     def save(self, path):
         torch = _torch()
         torch.save({"K": self.K, "batch": self.batch, "size": self.size, "lr": self.lr, "step": self.step,
-                    "data_seed": self.data_seed, "weights": self.student.weights.cpu(), "m": self.m.cpu(),
+                    "data_seed": self.data_seed, "cie94_weight": self.cie94_weight, "weights": self.student.weights.cpu(), "m": self.m.cpu(),
                     "v": self.v.cpu(), "teacher": self.teacher.weights.cpu(), "version": 1}, path)
 
     def load(self, path):
@@ -98,6 +103,7 @@ class Trainer:
         self.m.copy_(ck["m"].to(self.device))
         self.v.copy_(ck["v"].to(self.device))
         self.step, self.lr, self.data_seed = ck["step"], ck["lr"], ck["data_seed"]
+        self.cie94_weight = ck.get("cie94_weight", self.cie94_weight)
 
 
 def psnr(y, t):
@@ -141,10 +147,11 @@ def main(argv=None):
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--K", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--cie94", type=float, default=CIE94_WEIGHT, help="weight of the CIE94 term (0: MSE only)")
     ap.add_argument("--eval", action="store_true", help="held-out PSNR before and after")
     ap.add_argument("--save", default=None, help="checkpoint path")
     args = ap.parse_args(argv)
-    tr = Trainer(K=args.K, batch=args.batch, size=args.size, lr=args.lr)
+    tr = Trainer(K=args.K, batch=args.batch, size=args.size, lr=args.lr, cie94_weight=args.cie94)
     if args.eval:
         print("before:", evaluate(tr))
     losses = tr.run(args.steps)
