@@ -105,7 +105,10 @@ __host__ __device__ __forceinline__ void spatial_cell(int x, int n, int Ds, floa
         return;
     }
     const long long num = static_cast<long long>(x) * (Ds - 1);
-    long long q = num / (n - 1);
+    // exact integer quotient; 32-bit division whenever the numerator fits
+    long long q = num <= 0xffffffffLL ? static_cast<long long>(static_cast<unsigned int>(num) /
+                                                              static_cast<unsigned int>(n - 1))
+                                      : num / (n - 1);
     if (q > Ds - 2) q = Ds - 2;
     i = static_cast<int>(q);
     d = static_cast<float>(num - q * (n - 1)) * rn1;
@@ -498,27 +501,51 @@ __device__ __forceinline__ int cell_of(float p, float fDm1, float fDm2, float &f
 }
 
 // ---- LUT prologue: Eq. 9 reconstruction, Eq. 5 weight fold, cell coefficients ----
-// Factor rows are padded to an odd stride so that lanes reading different
-// rows hit different banks.
-__host__ __device__ inline int padded_rank(int R) { return R | 1; }
+// Factor rows are padded with zeros to Rp floats, a multiple of 4 with Rp / 4
+// odd: rows are read as float4, and the lanes of a quarter warp reading
+// consecutive rows hit different 16-byte bank groups.
+__host__ __device__ inline int padded_rank(int R)
+{
+    const int q = (R + 3) / 4;
+    return 4 * (q | 1);
+}
 
 // Shared-memory floats of the prologue temporaries: factors of all nine
 // tables at once (pairs = 3) or of one pair at a time (pairs = 1).
 __host__ __device__ inline int prologue_floats_n(int D, int R, int pairs)
 {
-    return (((2 * 3 * pairs * D * (R | 1)) + 3) & ~3) + D * D * 4;
+    return 2 * 3 * pairs * D * padded_rank(R) + D * D * 4;
 }
+
+// 16- and 4-byte asynchronous global -> shared copies (cp.async; L2 only for
+// 16 bytes) and the wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    const unsigned int s = static_cast<unsigned int>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    const unsigned int s = static_cast<unsigned int>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 __device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, float *misc, int tmp_floats)
 {
     const int tid = threadIdx.x;
-    const int D = d.D, R = d.R, Rp = padded_rank(R), DR = D * R, DRp = D * Rp, Dm1 = D - 1;
+    const int D = d.D, R = d.R, Rp = padded_rank(R), R4 = (R + 3) / 4, DR = D * R, DRp = D * Rp, Dm1 = D - 1;
     // all nine tables' factors at once when they fit (one global round trip)
     const int pairs_at_once = prologue_floats_n(D, R, 3) <= tmp_floats ? 3 : 1;
     const int nf = 3 * pairs_at_once;  // (c, p) tables held
     float *sU = tmp;                   // [nf][D][Rp] = U * S * w
     float *sV = tmp + nf * DRp;        // [nf][D][Rp]
-    float4 *vt = reinterpret_cast<float4 *>(tmp + ((2 * nf * DRp + 3) & ~3));  // [D][D]
+    float4 *vt = reinterpret_cast<float4 *>(tmp + 2 * nf * DRp);  // [D][D]
 
     // grid weights and summed biases
     for (int e = tid; e < d.K * 4; e += kThreads) misc[e] = __ldg(d.gw + e);
@@ -528,17 +555,61 @@ __device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, f
         misc[kMaxK * 4 + tid] = b;
     }
     const int nc = Dm1 * D;  // padded cells per pair
+    const int nrow = nf * D;  // factor rows held (of U, and of V)
+    const bool fast = (R & 3) == 0 && aligned16(d.U) && aligned16(d.V);
     for (int p = 0; p < 3; ++p) {
-        if (pairs_at_once == 1 || p == 0) {
-            // slot <-> (c, p): slot = c * 3 + p when all pairs are held, else c
-#pragma unroll 4
-            for (int e = tid; e < nf * DR; e += kThreads) {
-                const int slot = e / DR, ir = e - slot * DR, i = ir / R, r = ir - i * R;
+        if ((pairs_at_once == 1 || p == 0) && fast) {
+            // slot <-> (c, p): slot = c * 3 + p when all pairs are held, else c.
+            // U and V rows (16-byte chunks), S and the pair weights go to
+            // shared memory as asynchronous copies (one round trip); S and
+            // the weights sit in the vt area until U is scaled by them.
+            float *sS = reinterpret_cast<float *>(vt), *sW = sS + nf * R;
+            for (int e = tid; e < nrow * R4; e += kThreads) {
+                const int row = e / R4, q = e - row * R4, slot = row / D, i = row - slot * D;
                 const int c = slot / pairs_at_once, pp = pairs_at_once == 3 ? slot - c * 3 : p;
                 const int cp = c * 3 + pp;
-                sU[slot * DRp + i * Rp + r] =
-                    __ldg(d.U + cp * DR + ir) * __ldg(d.S + cp * R + r) * __ldg(d.lw + c * 4 + pp);
-                sV[slot * DRp + i * Rp + r] = __ldg(d.V + cp * DR + ir);
+                cp_async16(sU + slot * DRp + i * Rp + 4 * q, d.U + cp * DR + i * R + 4 * q);
+                cp_async16(sV + slot * DRp + i * Rp + 4 * q, d.V + cp * DR + i * R + 4 * q);
+            }
+            for (int e = tid; e < nf * (R + 1); e += kThreads) {
+                const int slot = e / (R + 1), r = e - slot * (R + 1);
+                const int c = slot / pairs_at_once, pp = pairs_at_once == 3 ? slot - c * 3 : p;
+                if (r < R) cp_async4(sS + slot * R + r, d.S + (c * 3 + pp) * R + r);
+                else cp_async4(sW + slot, d.lw + c * 4 + pp);
+            }
+            cp_async_wait_all();
+            __syncthreads();
+            for (int e = tid; e < nrow * R; e += kThreads) {
+                const int row = e / R, r = e - row * R, slot = row / D;
+                sU[row * Rp + r] = sU[row * Rp + r] * sS[slot * R + r] * sW[slot];  // (U S) w, as below
+            }
+            __syncthreads();
+        } else if (pairs_at_once == 1 || p == 0) {
+            // general case (rank not a multiple of 4 or unaligned factors):
+            // element e = (slot, i, r) with r < Rp, padding zeroed; the loads
+            // of kLoadBatch elements are issued before any of their stores.
+            constexpr int kLoadBatch = 4;
+            for (int e0 = tid; e0 < nrow * Rp; e0 += kLoadBatch * kThreads) {
+                float u[kLoadBatch], v[kLoadBatch];
+#pragma unroll
+                for (int q = 0; q < kLoadBatch; ++q) {
+                    const int e = e0 + q * kThreads;
+                    const int row = e / Rp, r = e - row * Rp, slot = row / D, i = row - slot * D;
+                    const int c = slot / pairs_at_once, pp = pairs_at_once == 3 ? slot - c * 3 : p;
+                    const int cp = c * 3 + pp;
+                    const bool ok = e < nrow * Rp && r < R;
+                    u[q] = ok ? __ldg(d.U + cp * DR + i * R + r) * __ldg(d.S + cp * R + r) * __ldg(d.lw + c * 4 + pp)
+                              : 0.f;
+                    v[q] = ok ? __ldg(d.V + cp * DR + i * R + r) : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < kLoadBatch; ++q) {
+                    const int e = e0 + q * kThreads;
+                    if (e < nrow * Rp) {
+                        sU[e] = u[q];
+                        sV[e] = v[q];
+                    }
+                }
             }
             __syncthreads();
         }
@@ -548,14 +619,20 @@ __device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, f
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const int slot = pairs_at_once == 3 ? c * 3 + p : c;
-                const float *u = sU + slot * DRp + i * Rp;
-                const float *v = sV + slot * DRp + j * Rp;
+                const float4 *u = reinterpret_cast<const float4 *>(sU + slot * DRp + i * Rp);
+                const float4 *v = reinterpret_cast<const float4 *>(sV + slot * DRp + j * Rp);
                 float a = 0.f;
-                if (R == 8) {
+                if (R4 == 2) {
 #pragma unroll
-                    for (int r = 0; r < 8; ++r) a = fmaf(u[r], v[r], a);
+                    for (int q = 0; q < 2; ++q) {
+                        const float4 x = u[q], y = v[q];
+                        a = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, a))));
+                    }
                 } else {
-                    for (int r = 0; r < R; ++r) a = fmaf(u[r], v[r], a);
+                    for (int q = 0; q < R4; ++q) {
+                        const float4 x = u[q], y = v[q];
+                        a = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, a))));
+                    }
                 }
                 acc[c] = a;
             }
@@ -657,51 +734,84 @@ __device__ __forceinline__ BlockBufs block_bufs(float *scratch, int nvx, int nvy
     return b;
 }
 
-// sum_{k = c, c+3, ... < K} w_k[which] * src[k * kstride]: the grids feeding one
-// output channel (Supp. Eq. 22), weighted (Eq. 21).  Terms are taken four at a
-// time with all four loads issued before their FMAs.
-__device__ __forceinline__ float fold_k(const float *src, size_t kstride, int c, int K, const float *misc, int which)
-{
-    float s = 0.f;
-    for (int k0 = c; k0 < K; k0 += 12) {
-        float v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int k = k0 + 3 * q;
-            v[q] = k < K ? __ldg(src + k * kstride) : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int k = k0 + 3 * q;
-            if (k < K) s = fmaf(misc[k * 4 + which], v[q], s);
-        }
-    }
-    return s;
-}
-
 // Block setup, phase A: grid slices of the block footprint folded per output
-// channel (sum over grids k = c mod 3 with their weights); column and row
-// cell tables.
+// channel (sum over grids k = c mod 3 of w_k times grid k: Supp. Eqs. 21-22);
+// column and row cell tables.
 __device__ inline void block_phase_a(const ImgDesc &d, const BlockGeom &g, const BlockBufs &b, const float *misc)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int nvx = g.nvx, nvy = g.nvy, Dsc = d.Dsc, K = d.K;
     const size_t kxy = static_cast<size_t>(d.Dsy) * d.Dsx, kxc = static_cast<size_t>(d.Dsx) * Dsc,
                  kyc = static_cast<size_t>(d.Dsy) * Dsc;
-    for (int r = warp; r < 3 * nvy; r += kWarps) {
-        const int c = r / nvy, iyl = r - c * nvy;
-        const float *src = d.gxy + static_cast<size_t>(g.iylo + iyl) * d.Dsx + g.ixlo;
-        for (int ixl = lane; ixl < nvx; ixl += 32) b.fxy[r * nvx + ixl] = fold_k(src + ixl, kxy, c, K, misc, 0);
-    }
-    for (int r = warp; r < 3 * nvx; r += kWarps) {
-        const int c = r / nvx, ixl = r - c * nvx;
-        const float *src = d.gxc + static_cast<size_t>(g.ixlo + ixl) * Dsc;
-        for (int j = lane; j < Dsc; j += 32) b.fxc[r * Dsc + j] = fold_k(src + j, kxc, c, K, misc, 1);
-    }
-    for (int r = warp; r < 3 * nvy; r += kWarps) {
-        const int c = r / nvy, iyl = r - c * nvy;
-        const float *src = d.gyc + static_cast<size_t>(g.iylo + iyl) * Dsc;
-        for (int j = lane; j < Dsc; j += 32) b.fyc[r * Dsc + j] = fold_k(src + j, kyc, c, K, misc, 2);
+    // One index space over the three folded slices (xy, then xc, then yc;
+    // each [3 c][rows][cols], consecutive elements adjacent in memory); every
+    // thread takes kFoldBatch elements at a time and issues all their loads
+    // before the first FMA, so the slices cost a few memory round trips.
+    const int nxy = 3 * nvy * nvx, nxc = 3 * nvx * Dsc, nyc = 3 * nvy * Dsc, ntot = nxy + nxc + nyc;
+    if (K > 0) {
+        // element e -> its first grid value's address and its channel c (by
+        // comparison: one division per element)
+        auto locate = [&](int e, int &c, size_t &kst) -> const float * {
+            if (e < nxy) {
+                const int r = e / nvx, ixl = e - r * nvx;
+                c = r >= nvy ? (r >= 2 * nvy ? 2 : 1) : 0;
+                kst = kxy;
+                return d.gxy + static_cast<size_t>(g.iylo + r - c * nvy) * d.Dsx + g.ixlo + ixl;
+            }
+            if (e < nxy + nxc) {
+                const int f = e - nxy, r = f / Dsc, j = f - r * Dsc;
+                c = r >= nvx ? (r >= 2 * nvx ? 2 : 1) : 0;
+                kst = kxc;
+                return d.gxc + static_cast<size_t>(g.ixlo + r - c * nvx) * Dsc + j;
+            }
+            const int f = e - nxy - nxc, r = f / Dsc, j = f - r * Dsc;
+            c = r >= nvy ? (r >= 2 * nvy ? 2 : 1) : 0;
+            kst = kyc;
+            return d.gyc + static_cast<size_t>(g.iylo + r - c * nvy) * Dsc + j;
+        };
+        // kFoldBatch elements per thread at a time, their first kFoldTerms
+        // grids (K <= 9: all of them) loaded before the first FMA
+        constexpr int kFoldBatch = 8, kFoldTerms = 3;
+        for (int e0 = tid; e0 < ntot; e0 += kFoldBatch * kThreads) {
+            int ch[kFoldBatch];
+            float v[kFoldBatch][kFoldTerms];
+#pragma unroll
+            for (int q = 0; q < kFoldBatch; ++q) {
+                const int e = e0 + q * kThreads;
+                int c = 0;
+                size_t kst = 0;
+                const float *sp = e < ntot ? locate(e, c, kst) : nullptr;
+                ch[q] = c;
+#pragma unroll
+                for (int t = 0; t < kFoldTerms; ++t) {
+                    const int k = c + 3 * t;
+                    v[q][t] = sp && k < K ? __ldg(sp + k * kst) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kFoldBatch; ++q) {
+                const int e = e0 + q * kThreads;
+                if (e >= ntot) continue;
+                const int which = e < nxy ? 0 : (e < nxy + nxc ? 1 : 2);
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < kFoldTerms; ++t) {
+                    const int k = ch[q] + 3 * t;
+                    if (k < K) acc = fmaf(misc[k * 4 + which], v[q][t], acc);
+                }
+                if (K > 3 * kFoldTerms) {  // grids beyond the third of a channel
+                    int c;
+                    size_t kst;
+                    const float *sp = locate(e, c, kst);
+                    for (int k = c + 3 * kFoldTerms; k < K; k += 3) acc = fmaf(misc[k * 4 + which], __ldg(sp + k * kst), acc);
+                }
+                float *dst = e < nxy ? b.fxy + e : (e < nxy + nxc ? b.fxc + (e - nxy) : b.fyc + (e - nxy - nxc));
+                *dst = acc;
+            }
+        }
+    } else {
+        for (int e = tid; e < ntot; e += kThreads)
+            (e < nxy ? b.fxy + e : (e < nxy + nxc ? b.fxc + (e - nxy) : b.fyc + (e - nxy - nxc)))[0] = 0.f;
     }
     if (tid < kTileW) {
         int ix;

@@ -162,3 +162,26 @@ def test_cta_cap_gives_identical_output(sv, ctas):
     got = sv.apply(xt, pd, ctas=ctas)
     torch.cuda.synchronize()
     assert torch.equal(got, ref)
+
+
+def test_unaligned_factors_give_identical_output(sv):
+    """Factors at 16-byte aligned addresses are copied to shared memory
+    asynchronously; any other 4-byte aligned address takes the general
+    loader.  Both compute (U S) w the same way: every output bit agrees."""
+    import torch
+    H, W = 120, 200
+    d = si.spatial_dims(H, W)
+    x, p = si.make_batch(si.config_seed(10), 2, H, W, d)
+    xt, pd = torch.from_numpy(x).cuda(), sv.to_device(p)
+    ref = sv.apply(xt, pd)
+    shifted = dict(pd)
+    for n in ("U", "V"):
+        buf = torch.zeros(pd[n].numel() + 1, dtype=torch.float32, device="cuda")
+        view = buf[1:].view(pd[n].shape)
+        view.copy_(pd[n])
+        shifted[n] = view
+    got = sv.apply(xt, shifted)
+    torch.cuda.synchronize()
+    assert shifted["U"].data_ptr() % 16 != 0
+    assert torch.equal(got, ref)
+    assert np.abs(got.cpu().numpy().astype(np.float64) - oracle.forward(d, p, x)).max() <= TOL
