@@ -964,7 +964,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
 
     Raw cur[NP], nxt[NP];
     int cur_im = -1;
-    load_row(blk, warp, cur);
+    bool first = true;
     for (;;) {
         const int im = find_image(blk);
         const ImgDesc &d = a.img[im];
@@ -972,6 +972,10 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
             __syncthreads();
             build_luts(d, lcell, scratch, misc, a.scratch_floats);
             cur_im = im;
+        }
+        if (first) {  // the first row's pixels, requested after the factor copies
+            load_row(blk, warp, cur);
+            first = false;
         }
         const BlockGeom g = block_geom(d, blk - d.block_begin, a.nvx_max, a.nvy_max);
         const BlockBufs b = block_bufs(scratch, g.nvx, g.nvy, d.Dsc, a.bh_max);
