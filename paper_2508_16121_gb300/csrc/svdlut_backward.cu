@@ -15,6 +15,9 @@
 //                through T = U diag(S) V^T (Eq. 9) to dU, dS, dV, dlut_w;
 //                grid_reduce_kernel + grid_finalize_kernel give dg_* and dgrid_w.
 #include <algorithm>
+#include <mutex>
+#include <utility>
+#include <vector>
 #include <cmath>
 
 #include "apply_kernel.cuh"
@@ -658,12 +661,20 @@ static size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255);
 
 // Lets kernel f use dynamic shared memory up to the opt-in limit minus its
 // static shared memory.
-static svdlut_status allow_dynamic_smem(const void *f, int max_optin)
+// Opts kernel f into the largest dynamic shared memory its static shared
+// memory leaves, once per device (calls from several threads are serialised).
+static svdlut_status allow_dynamic_smem(const void *f, int max_optin, int device)
 {
+    static std::mutex mu;
+    static std::vector<std::pair<int, const void *>> done;
+    std::lock_guard<std::mutex> g(mu);
+    for (const auto &e : done)
+        if (e.first == device && e.second == f) return SVDLUT_OK;
     cudaFuncAttributes fa;
     SVDLUT_CUDA_TRY(cudaFuncGetAttributes(&fa, f));
     SVDLUT_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          max_optin - static_cast<int>(fa.sharedSizeBytes)));
+    done.emplace_back(device, f);
     return SVDLUT_OK;
 }
 
@@ -820,17 +831,15 @@ extern "C" svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_p
     a.strips = (W + kTileW - 1) / kTileW;
     a.vec = (W % 4 == 0) && aligned(x, 16) && aligned(dy, 16);
 
-    static bool attr_done[64] = {};
-    if (!attr_done[di.device]) {
-        if ((st = allow_dynamic_smem(reinterpret_cast<const void *>(lut_grad_kernel), di.max_smem_optin)) != SVDLUT_OK)
-            return st;
-        if ((st = allow_dynamic_smem(reinterpret_cast<const void *>(grid_grad_kernel), di.max_smem_optin)) != SVDLUT_OK)
-            return st;
-        if ((st = allow_dynamic_smem(reinterpret_cast<const void *>(lut_finalize_kernel), di.max_smem_optin)) !=
-            SVDLUT_OK)
-            return st;
-        attr_done[di.device] = true;
-    }
+    if ((st = allow_dynamic_smem(reinterpret_cast<const void *>(lut_grad_kernel), di.max_smem_optin, di.device)) !=
+        SVDLUT_OK)
+        return st;
+    if ((st = allow_dynamic_smem(reinterpret_cast<const void *>(grid_grad_kernel), di.max_smem_optin, di.device)) !=
+        SVDLUT_OK)
+        return st;
+    if ((st = allow_dynamic_smem(reinterpret_cast<const void *>(lut_finalize_kernel), di.max_smem_optin,
+                                 di.device)) != SVDLUT_OK)
+        return st;
     if (pl.grid_smem + 256 > static_cast<size_t>(di.max_smem_optin) || pl.lut_smem > static_cast<size_t>(di.max_smem_optin))
         return fail(SVDLUT_ERR_UNSUPPORTED, "adjoint tables do not fit in shared memory");
     // 2. LUT pass (also produces the dy channel sums used by every bias)

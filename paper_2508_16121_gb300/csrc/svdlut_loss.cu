@@ -14,6 +14,7 @@
 // Delta E = 0.  The sum is reduced per block and then over blocks in a fixed
 // order (deterministic).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "svdlut_internal.cuh"
@@ -192,10 +193,12 @@ extern "C" svdlut_status svdlut_cie94(const float *y, const float *target, int B
     static const ColourConsts k = colour_consts();
     const size_t plane = static_cast<size_t>(H) * W, n = plane * B;
     // one resident wave: as many blocks per SM as the registers allow
-    static int per_sm = 0;
+    static std::atomic<int> cached_per_sm{0};
+    int per_sm = cached_per_sm.load();
     if (per_sm == 0) {
         SVDLUT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cie94_kernel, kLossThreads, 0));
         per_sm = std::max(per_sm, 1);
+        cached_per_sm.store(per_sm);
     }
     const int nb = static_cast<int>(std::min<size_t>((n + kLossThreads - 1) / kLossThreads,
                                                      std::min<size_t>(kMaxBlocks, static_cast<size_t>(di.sm_count) * per_sm)));
