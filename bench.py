@@ -481,6 +481,7 @@ def run_batched_variant(svdlut, torch, dev, stream, args):
     t_s = time_calls(g_s.replay, steps, stream)
     t_e = time_calls(seq, steps, stream)
     return {"images": len(xs), "Mpix": round(mpix, 2), "autotuned_block_px": block_px,
+            "autotuned_schedule": "ranges" if batch.cfg.schedule == 1 else "queue",
             "batched_graph": {"value": round(mpix / (t_b / 1e3), 1), "unit": "Mpix/s", "ms": round(t_b, 4),
                               "GB/s": round(bytes_px / (t_b / 1e3) / 1e9, 1)},
             "plain_x16_graph": {"value": round(mpix / (t_s / 1e3), 1), "unit": "Mpix/s", "ms": round(t_s, 4)},

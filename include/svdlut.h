@@ -135,18 +135,26 @@ typedef struct {
 } svdlut_image;
 
 /* Launch shape of svdlut_apply_batched: target pixels per work block (0 =
- * automatic: about four blocks per SM) and persistent CTAs (0 = one per SM). */
+ * automatic: about four blocks per SM), persistent CTAs (0 = one per SM) and
+ * the block schedule: SVDLUT_SCHED_QUEUE (0) has the CTAs take blocks from an
+ * atomic counter (balances uneven blocks); SVDLUT_SCHED_RANGES (1) gives each
+ * CTA a contiguous range of the image-major block list (fewer image switches,
+ * hence fewer LUT rebuilds per CTA). */
 typedef struct {
     int32_t block_px;
     int32_t ctas;
+    int32_t schedule;
 } svdlut_launch_cfg;
+
+enum { SVDLUT_SCHED_QUEUE = 0, SVDLUT_SCHED_RANGES = 1 };
 
 /*
  * svdlut_apply_cfg -- svdlut_apply with a launch shape: cfg->ctas > 0 plans
  * the work for and launches that many persistent CTAs (at most one per SM),
  * leaving the other SMs to concurrent work on other streams, e.g. the factor
- * generator of the next batch; cfg->block_px is not used (the blocks are
- * planned for the CTA count).  cfg may be NULL (= svdlut_apply).
+ * generator of the next batch; cfg->block_px and cfg->schedule are not used
+ * (the blocks are planned for the CTA count, in contiguous ranges).  cfg may
+ * be NULL (= svdlut_apply).
  * Errors: those of svdlut_apply; INVALID_ARG for a negative CTA count.
  */
 svdlut_status svdlut_apply_cfg(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
@@ -157,8 +165,9 @@ svdlut_status svdlut_apply_cfg(const svdlut_dims *dims, const svdlut_params *par
  * svdlut_apply_batched -- the fused transform of svdlut_apply (Eq. 10) over n
  * images of uneven sizes, each with its own transform, in one persistent
  * launch per 64 images.  imgs is a HOST array of n descriptors (read during the
- * call only).  The images' blocks are taken from a counter in ws, so the call
- * is capturable in a CUDA graph (a 4-byte memset + one kernel per 64 images).
+ * call only).  With the queue schedule the images' blocks are taken from a
+ * counter in ws; either way the call is capturable in a CUDA graph (a 4-byte
+ * memset, for the queue, + one kernel per 64 images).
  * ws: device memory of svdlut_batched_workspace_size(n) bytes, 4-byte aligned;
  * concurrent calls must use different workspaces.  cfg may be NULL.
  * Errors: INVALID_ARG (a bad image, reported with its index), WORKSPACE,
@@ -173,7 +182,8 @@ size_t svdlut_batched_workspace_size(int n);
 
 /*
  * svdlut_autotune_batched -- times svdlut_apply_batched on this batch for a
- * set of block sizes (reps timed launches each, after one warm-up) and
+ * set of block sizes, each with both schedules (reps timed launches each,
+ * after one warm-up) and
  * returns the fastest launch shape in *best (and its time in *best_ms if not
  * NULL).  Synchronises the stream; not capturable.  Writes the images' y.
  */

@@ -92,7 +92,7 @@ def apply(x, params, out=None, stream=None, ctas=None):
                                     ctypes.c_void_p(xb.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                     _stream_ptr(stream)))
     else:
-        cfg = _lib.LaunchCfg(0, int(ctas))
+        cfg = _lib.LaunchCfg(0, int(ctas), 0)
         _lib.check(lib.svdlut_apply_cfg(ctypes.byref(d), ctypes.byref(p), B, H, W, dt,
                                         ctypes.c_void_p(xb.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                         ctypes.byref(cfg), _stream_ptr(stream)))
@@ -442,8 +442,9 @@ class Batch:
         return f"{name}|{'u8' if self.dtype == _lib.U8 else 'f32'}|{shapes}"
 
     def autotune(self, reps=5, stream=None, cache=None):
-        """Time a set of block sizes on this batch (native autotuner) and keep
-        the fastest; returns (block_px, ms).  cache: path of a JSON file of
+        """Time a set of block sizes and both block schedules on this batch
+        (native autotuner) and keep the fastest launch shape (self.cfg);
+        returns (block_px, ms).  cache: path of a JSON file of
         earlier choices keyed by tune_key() (default: $SVDLUT_AUTOTUNE_CACHE,
         none if unset); a hit skips the timing and returns (block_px, None)."""
         import json
@@ -455,7 +456,8 @@ class Batch:
             with open(path) as f:
                 table = json.load(f)
             if key in table:
-                self.cfg = _lib.LaunchCfg(int(table[key]["block_px"]), int(table[key].get("ctas", 0)))
+                self.cfg = _lib.LaunchCfg(int(table[key]["block_px"]), int(table[key].get("ctas", 0)),
+                                          int(table[key].get("schedule", 0)))
                 return self.cfg.block_px, None
         lib = _lib.load()
         best = _lib.LaunchCfg()
@@ -465,7 +467,8 @@ class Batch:
                                                _stream_ptr(stream), reps, ctypes.byref(best), ctypes.byref(ms)))
         self.cfg = best
         if path:
-            table[key] = {"block_px": int(best.block_px), "ctas": int(best.ctas), "ms": float(ms.value)}
+            table[key] = {"block_px": int(best.block_px), "ctas": int(best.ctas), "schedule": int(best.schedule),
+                          "ms": float(ms.value)}
             tmp = path + ".tmp"
             with open(tmp, "w") as f:
                 json.dump(table, f, indent=1, sort_keys=True)

@@ -37,7 +37,10 @@ class Image(ctypes.Structure):
 
 
 class LaunchCfg(ctypes.Structure):
-    _fields_ = [("block_px", ctypes.c_int32), ("ctas", ctypes.c_int32)]
+    _fields_ = [("block_px", ctypes.c_int32), ("ctas", ctypes.c_int32), ("schedule", ctypes.c_int32)]
+
+
+SCHED_QUEUE, SCHED_RANGES = 0, 1
 
 
 class SvdlutError(RuntimeError):

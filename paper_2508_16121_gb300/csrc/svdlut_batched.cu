@@ -2,11 +2,12 @@
 // each with its own transform, and its autotuner.
 //
 // Every image is cut into 128-pixel column strips and row bands (BH rows);
-// the blocks of all images form one image-major list that the CTAs (one per
-// SM) take from an atomic counter, so uneven blocks and uneven content
-// (noise-like images cost more shared-memory gathers than smooth ones) balance
-// out.  A CTA rebuilds its LUT tables only when the next block belongs to
-// another image (image-major order keeps that to a few times per CTA).
+// the blocks of all images form one image-major list.  With the queue
+// schedule the CTAs (one per SM) take blocks from an atomic counter, so uneven
+// blocks and uneven content (noise-like images cost more shared-memory gathers
+// than smooth ones) balance out; with the ranges schedule each CTA takes a
+// contiguous range of the list, so it meets fewer images.  A CTA rebuilds its
+// LUT tables only when the next block belongs to another image.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -94,6 +95,7 @@ static svdlut_status run_batched(const svdlut_image *imgs, int n, svdlut_dtype d
     if ((st = device_info(&di)) != SVDLUT_OK) return st;
     const int block_px = cfg && cfg->block_px > 0 ? cfg->block_px : auto_block_px(imgs, n, di.sm_count);
     const int ctas = cfg && cfg->ctas > 0 ? cfg->ctas : di.sm_count;
+    const bool ranges = cfg && cfg->schedule == SVDLUT_SCHED_RANGES;
     unsigned int *queue = static_cast<unsigned int *>(ws);
     for (int i0 = 0, chunk = 0; i0 < n; i0 += kRaggedMax, ++chunk) {
         LaunchArgs<kRaggedMax> a{};
@@ -102,8 +104,10 @@ static svdlut_status run_batched(const svdlut_image *imgs, int n, svdlut_dtype d
         if ((st = plan_ragged(a, imgs, i0, dtype, block_px, static_cast<size_t>(di.max_smem_optin), &smem)) !=
             SVDLUT_OK)
             return st;
-        a.queue = queue + chunk;
-        SVDLUT_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), s));
+        if (!ranges) {
+            a.queue = queue + chunk;
+            SVDLUT_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), s));
+        }
         if ((st = launch_apply(a, smem, dtype, s, std::min(ctas, a.total_blocks))) != SVDLUT_OK) return st;
     }
     return SVDLUT_OK;
@@ -132,6 +136,8 @@ extern "C" svdlut_status svdlut_apply_batched(const svdlut_image *imgs, int n, s
     for (int i = 0; i < n; ++i)
         if ((st = check_image(imgs[i], dtype, i)) != SVDLUT_OK) return st;
     if (cfg && (cfg->block_px < 0 || cfg->ctas < 0)) return fail(SVDLUT_ERR_INVALID_ARG, "negative launch config");
+    if (cfg && cfg->schedule != SVDLUT_SCHED_QUEUE && cfg->schedule != SVDLUT_SCHED_RANGES)
+        return fail(SVDLUT_ERR_INVALID_ARG, "unknown schedule %d", cfg->schedule);
     if (!ws || ws_bytes < svdlut_batched_workspace_size(n))
         return fail(SVDLUT_ERR_WORKSPACE, "workspace of %zu bytes needed", svdlut_batched_workspace_size(n));
     if (!aligned(ws, 4)) return fail(SVDLUT_ERR_INVALID_ARG, "workspace must be 4-byte aligned");
@@ -153,8 +159,10 @@ extern "C" svdlut_status svdlut_autotune_batched(const svdlut_image *imgs, int n
     if (st != SVDLUT_OK) return st;
     const int base = auto_block_px(imgs, n, di.sm_count);
     std::vector<svdlut_launch_cfg> cands;
-    for (int rows : {16, 32, 64, 128, 256, 512}) cands.push_back({rows * kTileW, 0});
-    cands.push_back({base, 0});
+    for (int sched : {SVDLUT_SCHED_QUEUE, SVDLUT_SCHED_RANGES}) {
+        for (int rows : {16, 32, 64, 128, 256, 512}) cands.push_back({rows * kTileW, 0, sched});
+        cands.push_back({base, 0, sched});
+    }
     cudaEvent_t e0, e1;
     SVDLUT_CUDA_TRY(cudaEventCreate(&e0));
     SVDLUT_CUDA_TRY(cudaEventCreate(&e1));
