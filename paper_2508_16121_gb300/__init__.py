@@ -5,6 +5,14 @@ torch provides device memory and streams.
 
     import paper_2508_16121_gb300 as svdlut
     y = svdlut.apply(x, params)          # x: [B,3,H,W] or [3,H,W], float32 or uint8, CUDA
+    y8 = svdlut.apply_io(x16, params, "u16", "u8")   # 16-bit photo -> 8-bit result
+    g = svdlut.backward(x, params, dy)   # adjoint: dx and every parameter gradient
+    ys = svdlut.Batch(xs, params_list).run()         # ragged batch, one launch
+    p = svdlut.Generator(K, weights).forward(x)      # learned factors for apply
+
+Also: apply_host (host frames), apply_original (the unfused structure),
+lut3d_apply / lut3d_fit2d (the 3D LUT and its 2D fit), mse and cie94 (loss
+terms), and train.Trainer (end-to-end training of the generator).
 """
 from __future__ import annotations
 
