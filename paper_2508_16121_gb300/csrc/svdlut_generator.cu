@@ -150,6 +150,7 @@ inline WsLayout make_ws(int B)
 // Bilinear downsample to 256x256 with half-pixel centres, no antialiasing.
 __global__ void downsample_kernel(const float *__restrict__ x, int B, int H, int W, float *__restrict__ t)
 {
+    pdl_enter();
     const size_t n = static_cast<size_t>(B) * 3 * kThumb * kThumb;
     const float sy_ = static_cast<float>(H) / kThumb, sx_ = static_cast<float>(W) / kThumb;
     for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
@@ -372,6 +373,7 @@ struct ConvFwd {
 
 __global__ void __launch_bounds__(kGT) conv_fwd_kernel(const ConvFwd p)
 {
+    pdl_enter();
     __shared__ __align__(16) __nv_bfloat16 As[64][40];
     __shared__ __align__(16) __nv_bfloat16 Bs[64][40];
     const int m0 = blockIdx.x * 64, z = blockIdx.z;
@@ -623,6 +625,7 @@ __global__ void __launch_bounds__(512) conv_finish_kernel(const float *__restric
                                                           const float *gam, const float *bet, float *mean, float *rstd,
                                                           float *sc, float *sh)
 {
+    pdl_enter();
     __shared__ float red[16];
     const int bn = blockIdx.x, b = bn / N, n = bn - b * N;
     const float *src = part + static_cast<size_t>(n) * M + static_cast<size_t>(b) * P;
@@ -752,6 +755,7 @@ __global__ void __launch_bounds__(256) pool_fc1_kernel(const float *__restrict__
                                                        uint64_t seed, float *__restrict__ rho,
                                                        float *__restrict__ hidden)
 {
+    pdl_enter();
     __shared__ float sr[kRho];
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float v = pool_one(r4, b, tid, training, seed);
@@ -773,6 +777,7 @@ __global__ void __launch_bounds__(256) pool_fc1_kernel(const float *__restrict__
 
 __global__ void fc2_kernel(const float *__restrict__ hidden, HeadW hw, int B, int ntot, ParamOut o)
 {
+    pdl_enter();
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * ntot; e += gridDim.x * blockDim.x) {
         const int b = e / ntot;
         int n = e - b * ntot, h = 0;
@@ -1049,23 +1054,27 @@ extern "C" svdlut_status svdlut_generator_forward(int K, const float *weights, i
     const Layout L = make_layout(K);
     const WsLayout wl = make_ws(B);
     float *w = static_cast<float *>(ws);
-    downsample_kernel<<<static_cast<int>((static_cast<size_t>(B) * 3 * kThumb * kThumb + 255) / 256), 256, 0, s>>>(
-        x, B, H, W, w + wl.thumb);
-    SVDLUT_CUDA_TRY(cudaGetLastError());
+    // a chain of small kernels, each a programmatic dependent launch of the one before
+    if ((st = launch_pdl(downsample_kernel, dim3(static_cast<int>((static_cast<size_t>(B) * 3 * kThumb * kThumb + 255) / 256)),
+                         dim3(256), 0, s, x, B, H, W, w + wl.thumb)) != SVDLUT_OK)
+        return st;
     const float *in = w + wl.thumb, *isc = nullptr, *ish = nullptr;
     for (int i = 0; i < 5; ++i) {
         const int Cin = kCh[i], Cout = kCh[i + 1], S = kSz[i], So = kSz[i + 1];
         const int M = B * So * So, Kd = Cin * 9;
         const int ks = fwd_ksteps(i, fwd_split(B, i)), Z = ((Kd + 31) / 32 + ks - 1) / ks;
         float *r = w + wl.r[i];
-        conv_fwd_kernel<<<dim3((M + 63) / 64, 1, Z), kGT, 0, s>>>(
-            ConvFwd{in, isc, ish, weights + L.conv_w[i], w + wl.part, Cin, S, So, Cout, M, Kd, ks});
+        if ((st = launch_pdl(conv_fwd_kernel, dim3((M + 63) / 64, 1, Z), dim3(kGT), 0, s,
+                             ConvFwd{in, isc, ish, weights + L.conv_w[i], w + wl.part, Cin, S, So, Cout, M, Kd, ks})) !=
+            SVDLUT_OK)
+            return st;
         const bool norm = i < 4;
-        conv_finish_kernel<<<B * Cout, 512, 0, s>>>(
-            w + wl.part, Z, Cout, M, So * So, weights + L.conv_b[i], r, norm ? weights + L.in_g[i] : nullptr,
-            norm ? weights + L.in_b[i] : nullptr, norm ? w + wl.mean[i] : nullptr, norm ? w + wl.rstd[i] : nullptr,
-            norm ? w + wl.sc[i] : nullptr, norm ? w + wl.sh[i] : nullptr);
-        SVDLUT_CUDA_TRY(cudaGetLastError());
+        if ((st = launch_pdl(conv_finish_kernel, dim3(B * Cout), dim3(512), 0, s, static_cast<const float *>(w + wl.part),
+                             Z, Cout, M, So * So, weights + L.conv_b[i], r,
+                             norm ? weights + L.in_g[i] : nullptr, norm ? weights + L.in_b[i] : nullptr,
+                             norm ? w + wl.mean[i] : nullptr, norm ? w + wl.rstd[i] : nullptr,
+                             norm ? w + wl.sc[i] : nullptr, norm ? w + wl.sh[i] : nullptr)) != SVDLUT_OK)
+            return st;
         in = r;
         if (norm) {
             isc = w + wl.sc[i];
@@ -1073,11 +1082,14 @@ extern "C" svdlut_status svdlut_generator_forward(int K, const float *weights, i
         }
     }
     const HeadW hw = head_weights(weights, L, K);
-    pool_fc1_kernel<<<B, 256, 0, s>>>(w + wl.r[4], hw, training, seed, w + wl.rho, w + wl.hidden);
+    if ((st = launch_pdl(pool_fc1_kernel, dim3(B), dim3(256), 0, s, static_cast<const float *>(w + wl.r[4]), hw,
+                         training, seed, w + wl.rho, w + wl.hidden)) != SVDLUT_OK)
+        return st;
     const int ntot = L.head_n[0] + L.head_n[1] + L.head_n[2] + L.head_n[3];
     ParamOut po{out->U, out->S, out->V, out->lut_w, out->g_xy, out->g_xc, out->g_yc, out->grid_w};
-    fc2_kernel<<<blocks_for(static_cast<size_t>(B) * ntot), 256, 0, s>>>(w + wl.hidden, hw, B, ntot, po);
-    SVDLUT_CUDA_TRY(cudaGetLastError());
+    if ((st = launch_pdl(fc2_kernel, dim3(blocks_for(static_cast<size_t>(B) * ntot)), dim3(256), 0, s,
+                         static_cast<const float *>(w + wl.hidden), hw, B, ntot, po)) != SVDLUT_OK)
+        return st;
     return SVDLUT_OK;
 }
 

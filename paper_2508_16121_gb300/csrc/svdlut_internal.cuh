@@ -6,6 +6,7 @@
 
 #include <cstdarg>
 #include <cstdint>
+#include <utility>
 #include <cstdio>
 
 #include "svdlut.h"
@@ -69,5 +70,36 @@ svdlut_status device_info(DeviceInfo *out);
 svdlut_status check_buffer(unsigned int **out);
 
 inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Programmatic dependent launch (chains of small kernels).  The kernel waits
+// for the preceding kernel's results before it reads anything, then lets the
+// next launch in the stream start its launch processing; both are no-ops for
+// a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" :::);
+}
+
+// Launches kernel<<<grid, block, smem, s>>>(args...) as a programmatic
+// dependent launch: its launch overlaps the end of the preceding kernel in
+// the stream (the kernel must call pdl_enter() first).
+template <typename... KArgs, typename... Args>
+svdlut_status launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                         Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SVDLUT_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+    return SVDLUT_OK;
+}
 
 }  // namespace svdlut
