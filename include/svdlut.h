@@ -88,7 +88,10 @@ typedef struct {
  * device, must not overlap.  Pointers must be 4-byte aligned for F32; 16-byte
  * alignment and W % 4 == 0 enable the vectorised path (any other case is
  * handled, more slowly).  Returns INVALID_ARG for null pointers, B, H or W < 1
- * or dims out of range; UNSUPPORTED for dims beyond the limits above.
+ * or dims out of range; UNSUPPORTED for dims beyond the limits above, and when
+ * the grid slices of one 128-pixel-wide block do not fit in shared memory
+ * next to the LUT tables (grids much denser along x than one vertex per 8
+ * pixels combined with a large Dsc and D_t).
  */
 svdlut_status svdlut_apply(const svdlut_dims *dims, const svdlut_params *params, int B, int H,
                            int W, svdlut_dtype dtype, const void *x, void *y,

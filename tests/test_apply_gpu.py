@@ -185,3 +185,32 @@ def test_unaligned_factors_give_identical_output(sv):
     assert shifted["U"].data_ptr() % 16 != 0
     assert torch.equal(got, ref)
     assert np.abs(got.cpu().numpy().astype(np.float64) - oracle.forward(d, p, x)).max() <= TOL
+
+
+def _random_case(rng):
+    """LUT dims over their whole range; grids at most one vertex per 4 pixels
+    (the coarse spatial features of the method; denser slices of a 128-px
+    tile need not fit in shared memory)."""
+    D = int(rng.integers(2, 34))
+    B, H, W = int(rng.integers(1, 4)), int(rng.integers(1, 300)), int(rng.integers(1, 300))
+    d = si.Dims(D, int(rng.integers(1, D + 1)), int(rng.integers(0, 49)),
+                int(rng.integers(2, max(3, min(64, W // 4) + 1))), int(rng.integers(2, max(3, min(64, H // 4) + 1))),
+                int(rng.integers(2, 65)))
+    return d, B, H, W
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_dims_and_sizes(sv, seed):
+    """Seeded random transform dims and image sizes, F32 and u8, against the
+    oracle."""
+    import torch
+    rng = np.random.default_rng(4000 + seed)
+    d, B, H, W = _random_case(rng)
+    x, p = si.make_batch(5000 + seed, B, H, W, d)
+    pd = sv.to_device(p)
+    y = sv.apply(torch.from_numpy(x).cuda(), pd).cpu().numpy().astype(np.float64)
+    assert np.abs(y - oracle.forward(d, p, x)).max() <= TOL, (d, B, H, W)
+    x8 = si.to_u8(x)
+    y8 = sv.apply(torch.from_numpy(x8).cuda(), pd).cpu().numpy().astype(int)
+    ref8 = oracle.quantize_u8(oracle.forward(d, p, oracle.u8_to_unit(x8))).astype(int)
+    assert np.abs(y8 - ref8).max() <= 1, (d, B, H, W)

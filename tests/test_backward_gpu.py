@@ -172,3 +172,19 @@ def test_backward_1080p_batch_of_8(sv):
     for k in g1:
         s = g1[k] + g2[k]
         assert np.abs(g12[k] - s).max() <= 1e-4 * max(np.abs(s).max(), 1.0), k
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_backward_random_dims_and_sizes(sv, seed):
+    """Seeded random transform dims (grids at most one vertex per 8 pixels,
+    as the method's low-resolution features, and at most 33 intensity
+    vertices) and image sizes against the oracle adjoint."""
+    rng = np.random.default_rng(6000 + seed)
+    D = int(rng.integers(2, 34))
+    B, H, W = int(rng.integers(1, 3)), int(rng.integers(1, 160)), int(rng.integers(1, 200))
+    d = si.Dims(D, int(rng.integers(1, D + 1)), int(rng.integers(0, 49)),
+                int(rng.integers(2, max(3, min(64, W // 8) + 1))), int(rng.integers(2, max(3, min(64, H // 8) + 1))),
+                int(rng.integers(2, 34)))
+    x, p = si.make_batch(7000 + seed, B, H, W, d)
+    dy = si.make_upstream(7100 + seed, x.shape)
+    compare(gpu_backward(sv, x, p, dy), oracle.backward(d, p, x, dy), d, x)
