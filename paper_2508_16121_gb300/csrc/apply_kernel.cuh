@@ -1,22 +1,27 @@
 // Fused 2D slicing + 2D LUT transform kernel (Eq. 10, Supp. Eq. 22) for sm_103a.
 //
-// One persistent CTA per SM walks a contiguous range of pixel blocks; a block
-// is a 128-pixel-wide column strip of one image, BH rows tall (BH is planned
-// on the host so that the blocks cover the SMs evenly).  A lane owns 4
-// pixels of a row: columns lane + 32 k of the tile for float images (every
-// warp-wide access covers 32 adjacent pixels, which keeps the table gathers of
-// smooth regions on few cells), or 4 adjacent pixels for 8-bit images (one
-// 32-bit load/store per plane); warp w owns rows w, w + kWarps, ... of the block.
-//  - Prologue, once per image a CTA meets: the nine 2D LUTs are rebuilt from
-//    their SVD factors (Eq. 9) in shared memory, multiplied by their LUT
-//    weights (Eq. 5) and turned into per-cell bilinear coefficients
-//    (phi = a + b da + c db + d da db, Supp. Eq. 15) for the three output
-//    channels: 3 float4 per cell and pair.
+// One persistent CTA per SM walks a contiguous range of pixel blocks (or takes
+// blocks from an atomic queue, for ragged batches); a block is a
+// 128-pixel-wide column strip of one image, BH rows tall (BH is planned on the
+// host so that the blocks cover the SMs evenly).  A lane owns 4 pixels of a
+// row: columns lane + 32 k of the tile for float images (every warp-wide
+// access covers 32 adjacent pixels, which keeps the table gathers of smooth
+// regions on few cells), or 4 adjacent pixels for integer pixel formats (one
+// 32- or 64-bit access per plane or word); warp w owns rows w, w + kWarps, ...
+// of the block.  The pixel formats (planar float, 8- and 16-bit, interleaved)
+// are template parameters (Io<In, Out> below).
+//  - Prologue, once per image a CTA meets: the factor rows arrive by
+//    asynchronous copies, the nine 2D LUTs are rebuilt from their SVD factors
+//    (Eq. 9) in shared memory, multiplied by their LUT weights (Eq. 5) and
+//    turned into per-cell bilinear coefficients (phi = a + b da + c db +
+//    d da db, Supp. Eq. 15) for the three output channels: 3 float4 per cell
+//    and pair.
 //  - Per block: the grid slices of the block's footprint are summed over the
 //    grids that feed each output channel (grid k feeds channel k mod 3, Supp.
-//    Eq. 22) with their weights (Eq. 21); the xc slice is stored per x-cell
-//    and intensity cell in slope form (value, slope along intensity, and
-//    their differences to the next x-cell).
+//    Eq. 22) with their weights (Eq. 21), with the loads of several elements
+//    per thread in flight; the xc slice is stored per x-cell and intensity
+//    cell in slope form (value, slope along intensity, and their differences
+//    to the next x-cell).
 //  - Per row: a warp interpolates the xy and yc slices along y for its row
 //    (yc as value and slope along intensity).
 //  - Per pixel: 9 LDS.128 for the three LUT pairs, 2 LDS.128 (xy), 3 LDS.128
