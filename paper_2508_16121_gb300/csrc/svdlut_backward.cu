@@ -47,8 +47,10 @@ __device__ __forceinline__ int nth_set_bit(unsigned int m, int n)
 // in the group (fixed order); the lowest lane of each group then writes, one
 // corner at a time with a warp barrier between corners, so two groups never
 // update one address in the same step.  key < 0 marks an inactive lane.
-// Every lane of the warp must call this.
-template <int NC>
+// Every lane of the warp must call this.  VEC: every key's NC <= 3 values sit
+// in one 16-byte slot (tab, key, ld and cs multiples of 4 floats), updated
+// with one 16-byte load and store.
+template <int NC, bool VEC = false>
 __device__ __forceinline__ void warp_scatter(float *tab, int key, int ld, int cs, float (&v)[4][NC])
 {
     const unsigned int full = 0xffffffffu;
@@ -87,9 +89,19 @@ __device__ __forceinline__ void warp_scatter(float *tab, int key, int ld, int cs
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         if (leader) {
-            float *t = tab + key + off[q];
+            if constexpr (VEC) {
+                static_assert(NC <= 3, "one 16-byte slot per key");
+                float4 *t = reinterpret_cast<float4 *>(tab + key + off[q]);
+                float4 o = *t;
+                o.x += v[q][0];
+                if constexpr (NC > 1) o.y += v[q][1];
+                if constexpr (NC > 2) o.z += v[q][2];
+                *t = o;
+            } else {
+                float *t = tab + key + off[q];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) t[c] += v[q][c];
+                for (int c = 0; c < NC; ++c) t[c] += v[q][c];
+            }
         }
         __syncwarp();
     }
@@ -132,9 +144,9 @@ __global__ void __launch_bounds__(kLutThreads, 1)
     const int A = pair == 2 ? 1 : 0, Bx = pair == 0 ? 1 : 2;  // axes of the pair
     const int b = blockIdx.y, p = blockIdx.x;
     const int D = a.D, DD = D * D;
-    float *tab = sm + warp * 3 * DD;  // [D][D][3 channels] of this warp's pair
-    float *sums = sm + kLutWarps * 3 * DD;
-    for (int e = threadIdx.x; e < kLutWarps * 3 * DD; e += kLutThreads) sm[e] = 0.f;
+    float *tab = sm + warp * 4 * DD;  // [D][D][3 channels + 1 pad] of this warp's pair
+    float *sums = sm + kLutWarps * 4 * DD;
+    for (int e = threadIdx.x; e < kLutWarps * 4 * DD; e += kLutThreads) sm[e] = 0.f;
     __syncthreads();
 
     const int r0 = static_cast<int>((static_cast<long long>(a.H) * p) / P);
@@ -175,7 +187,7 @@ __global__ void __launch_bounds__(kLutThreads, 1)
             for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) v[q][c] = gy[c] * w[q];
-            warp_scatter<3>(tab, act ? (ia * D + ib) * 3 : -1, D * 3, 3, v);
+            warp_scatter<3, true>(tab, act ? (ia * D + ib) * 4 : -1, D * 4, 4, v);
         }
     }
     // sum of dy_c: the pair-0 warps' totals (every pair warp of a group sees the same pixels)
@@ -192,7 +204,7 @@ __global__ void __launch_bounds__(kLutThreads, 1)
     for (int e = threadIdx.x; e < 9 * DD; e += kLutThreads) {
         const int c = e / (3 * DD), r = e - c * 3 * DD, q = r / DD, cell = r - q * DD;
         float s = 0.f;
-        for (int gq = 0; gq < kLutWarps / 3; ++gq) s += sm[(gq * 3 + q) * 3 * DD + cell * 3 + c];
+        for (int gq = 0; gq < kLutWarps / 3; ++gq) s += sm[(gq * 3 + q) * 4 * DD + cell * 4 + c];
         out[e] = s;
     }
     if (threadIdx.x < 3) {
@@ -682,7 +694,7 @@ static svdlut_status plan_backward(const svdlut_dims *d, int B, int H, int W, in
                                    BwdPlan *pl)
 {
     const int D = d->D_t, Dsc = d->Dsc;
-    pl->lut_smem = sizeof(float) * (static_cast<size_t>(kLutWarps) * 3 * D * D + kLutWarps);
+    pl->lut_smem = sizeof(float) * (static_cast<size_t>(kLutWarps) * 4 * D * D + kLutWarps);
     if (pl->lut_smem > smem_limit) return fail(SVDLUT_ERR_UNSUPPORTED, "D_t=%d too large for the adjoint", D);
     pl->P = std::max(1, std::min(H, (sm_count + B - 1) / B));
     // grid pass: blocks of 128 x BH; bands chosen like the forward plan
