@@ -214,3 +214,20 @@ def test_random_dims_and_sizes(sv, seed):
     y8 = sv.apply(torch.from_numpy(x8).cuda(), pd).cpu().numpy().astype(int)
     ref8 = oracle.quantize_u8(oracle.forward(d, p, oracle.u8_to_unit(x8))).astype(int)
     assert np.abs(y8 - ref8).max() <= 1, (d, B, H, W)
+
+
+def test_8k_frame_u8_and_f32(sv):
+    """A 7680x4320 frame (33 Mpx: beyond the 4K workload, for index widths)
+    in FP32 and u8 against the oracle."""
+    import torch
+    H, W = 4320, 7680
+    d = si.spatial_dims(H, W)
+    x, p = si.make_batch(si.config_seed(11), 1, H, W, d)
+    pd = sv.to_device(p)
+    ref = oracle.forward(d, p, x)
+    y = sv.apply(torch.from_numpy(x).cuda(), pd).cpu().numpy().astype(np.float64)
+    assert np.abs(y - ref).max() <= TOL
+    x8 = si.to_u8(x)
+    y8 = sv.apply(torch.from_numpy(x8).cuda(), pd).cpu().numpy().astype(int)
+    ref8 = oracle.quantize_u8(oracle.forward(d, p, oracle.u8_to_unit(x8))).astype(int)
+    assert np.abs(y8 - ref8).max() <= 1
