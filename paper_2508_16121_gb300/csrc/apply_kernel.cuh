@@ -73,27 +73,71 @@ struct LaunchArgs {
 
 // ---- optional index checks ----
 // Built with -DSVDLUT_CHECK_BOUNDS, every shared-memory gather index of the
-// kernel is tested against its table size; an index out of range is counted
-// in the status words (count, site, index, limit of the first one) and
-// replaced by 0, so the access stays inside the table.  Otherwise the checks
-// compile to nothing.
-enum CheckSite : unsigned int { kChkLut = 1, kChkPxc = 2, kChkRyc = 3, kChkRxy = 4 };
+// kernel is tested against its table size, every lane's run of pixels
+// against its image plane, and every vector access and 16-byte asynchronous
+// copy against its alignment.  A failure is counted in the status words
+// (count, site, index, limit of the first one) and the access is made safe:
+// the index replaced by 0, the pixel run dropped, the vector access done with
+// scalar ones, the copy skipped.  Otherwise the checks compile to nothing.
+enum CheckSite : unsigned int {
+    kChkLut = 1, kChkPxc = 2, kChkRyc = 3, kChkRxy = 4,  // shared-memory gathers
+    kChkPixel = 5,                                       // pixel run outside the plane (index: offset)
+    kChkAlign = 6                                        // misaligned vector access or copy (index: address)
+};
+
+__device__ __forceinline__ void check_record(unsigned int *st, unsigned int site, unsigned int idx, unsigned int limit)
+{
+    if (st && atomicAdd(st, 1u) == 0u) {
+        st[1] = site;
+        st[2] = idx;
+        st[3] = limit;
+    }
+}
 
 __device__ __forceinline__ int checked_index(unsigned int *st, unsigned int site, int idx, int limit)
 {
 #ifdef SVDLUT_CHECK_BOUNDS
     if (idx >= 0 && idx < limit) return idx;
-    if (st && atomicAdd(st, 1u) == 0u) {
-        st[1] = site;
-        st[2] = static_cast<unsigned int>(idx);
-        st[3] = static_cast<unsigned int>(limit);
-    }
+    check_record(st, site, static_cast<unsigned int>(idx), static_cast<unsigned int>(limit));
     return 0;
 #else
     (void)st;
     (void)site;
     (void)limit;
     return idx;
+#endif
+}
+
+// A lane's n pixels from offset off (32 apart when STRIDE, else adjacent)
+// must lie in a plane of `plane` pixels; returns n, or 0 after a failure.
+template <bool STRIDE>
+__device__ __forceinline__ int checked_run(unsigned int *st, size_t off, int n, size_t plane)
+{
+#ifdef SVDLUT_CHECK_BOUNDS
+    if (n <= 0 || off + (STRIDE ? 32 * static_cast<size_t>(n - 1) : static_cast<size_t>(n - 1)) < plane) return n;
+    check_record(st, kChkPixel, static_cast<unsigned int>(off), static_cast<unsigned int>(plane));
+    return 0;
+#else
+    (void)st;
+    (void)off;
+    (void)plane;
+    return n;
+#endif
+}
+
+// vec, unless a vector access at p would be misaligned for `align` bytes
+__device__ __forceinline__ bool checked_vec(unsigned int *st, bool vec, const void *p, size_t align)
+{
+#ifdef SVDLUT_CHECK_BOUNDS
+    if (!vec || (reinterpret_cast<uintptr_t>(p) % align) == 0) return vec;
+    check_record(st, kChkAlign, static_cast<unsigned int>(reinterpret_cast<uintptr_t>(p)),
+                 static_cast<unsigned int>(align));
+    return false;
+#else
+    (void)st;
+    (void)p;
+    (void)align;
+    return vec;
 #endif
 }
 
@@ -412,6 +456,10 @@ struct InU16Hwc {  // interleaved 16-bit [H][W][3], value v / 65535
 // mapping of the input format.
 struct OutF32 {  // planar float
     static constexpr size_t kPixelBytes = 12, kVecAlign = 16;
+    static __device__ __forceinline__ const void *at(const void *base, size_t off)
+    {
+        return static_cast<const float *>(base) + off;
+    }
     template <bool STRIDE>
     static __device__ __forceinline__ void store(void *base, size_t plane, size_t off, const float (&o)[3][4], int n,
                                                  bool vec)
@@ -428,6 +476,10 @@ struct OutF32 {  // planar float
 
 struct OutU8 {  // planar 8-bit, rint(clamp(y, 0, 1) * 255)
     static constexpr size_t kPixelBytes = 3, kVecAlign = 4;
+    static __device__ __forceinline__ const void *at(const void *base, size_t off)
+    {
+        return static_cast<const uint8_t *>(base) + off;
+    }
     template <bool STRIDE>
     static __device__ __forceinline__ void store(void *base, size_t plane, size_t off, const float (&o)[3][4], int n,
                                                  bool vec)
@@ -448,6 +500,10 @@ __device__ __forceinline__ unsigned int pack4(unsigned int a, unsigned int b, un
 
 struct OutU8Hwc {  // interleaved 8-bit, rint(clamp(y, 0, 1) * 255)
     static constexpr size_t kPixelBytes = 3, kVecAlign = 4;
+    static __device__ __forceinline__ const void *at(const void *base, size_t off)
+    {
+        return static_cast<const uint8_t *>(base) + 3 * off;
+    }
     template <bool STRIDE>
     static __device__ __forceinline__ void store(void *base, size_t, size_t off, const float (&o)[3][4], int n,
                                                  bool vec)
@@ -541,8 +597,10 @@ __device__ __forceinline__ void cp_async_wait_all()
 
 __device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-__device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, float *misc, int tmp_floats)
+__device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, float *misc, int tmp_floats,
+                                  unsigned int *check)
 {
+    (void)check;
     const int tid = threadIdx.x;
     const int D = d.D, R = d.R, Rp = padded_rank(R), R4 = (R + 3) / 4, DR = D * R, DRp = D * Rp, Dm1 = D - 1;
     // all nine tables' factors at once when they fit (one global round trip)
@@ -573,8 +631,17 @@ __device__ inline void build_luts(const ImgDesc &d, float4 *lcell, float *tmp, f
                 const int row = e / R4, q = e - row * R4, slot = row / D, i = row - slot * D;
                 const int c = slot / pairs_at_once, pp = pairs_at_once == 3 ? slot - c * 3 : p;
                 const int cp = c * 3 + pp;
-                cp_async16(sU + slot * DRp + i * Rp + 4 * q, d.U + cp * DR + i * R + 4 * q);
-                cp_async16(sV + slot * DRp + i * Rp + 4 * q, d.V + cp * DR + i * R + 4 * q);
+                float *du = sU + slot * DRp + i * Rp + 4 * q, *dv = sV + slot * DRp + i * Rp + 4 * q;
+                const float *su = d.U + cp * DR + i * R + 4 * q, *sv = d.V + cp * DR + i * R + 4 * q;
+#ifdef SVDLUT_CHECK_BOUNDS
+                if (((reinterpret_cast<uintptr_t>(du) | reinterpret_cast<uintptr_t>(dv) |
+                      reinterpret_cast<uintptr_t>(su) | reinterpret_cast<uintptr_t>(sv)) & 15) != 0) {
+                    check_record(check, kChkAlign, static_cast<unsigned int>(reinterpret_cast<uintptr_t>(su)), 16u);
+                    continue;
+                }
+#endif
+                cp_async16(du, su);
+                cp_async16(dv, sv);
             }
             for (int e = tid; e < nf * (R + 1); e += kThreads) {
                 const int slot = e / (R + 1), r = e - slot * (R + 1);
@@ -954,8 +1021,11 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         const int y = d.y_begin + band * d.BH + row;
         const size_t plane = static_cast<size_t>(d.H) * d.W;
         const bool ok = row < d.BH && y < d.y_end && n > 0;
-        if (ok) {
-            In::load(In::at(d.x, static_cast<size_t>(y) * d.W + x), plane, n, d.vec, dst);
+        const size_t off = static_cast<size_t>(y) * d.W + x;
+        const int nc = ok ? checked_run<kStride>(a.check, off, n, plane) : 0;
+        if (nc > 0) {
+            const void *px = In::at(d.x, off);
+            In::load(px, plane, nc, kStride ? d.vec : checked_vec(a.check, d.vec, px, In::kVecAlign), dst);
         } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c) dst[c] = Raw();
@@ -963,7 +1033,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         if constexpr (DX) {
             const float *g = d.dy + static_cast<size_t>(y) * d.W + x;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) dst[3 + c] = ok ? PixIO<float>::load_s(g + c * plane, n) : Raw();
+            for (int c = 0; c < 3; ++c) dst[3 + c] = nc > 0 ? PixIO<float>::load_s(g + c * plane, nc) : Raw();
         }
     };
 
@@ -975,7 +1045,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         const ImgDesc &d = a.img[im];
         if (im != cur_im) {
             __syncthreads();
-            build_luts(d, lcell, scratch, misc, a.scratch_floats);
+            build_luts(d, lcell, scratch, misc, a.scratch_floats, a.check);
             cur_im = im;
         }
         if (first) {  // the first row's pixels, requested after the factor copies
@@ -1021,8 +1091,10 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
             // next row of this warp, possibly in the next block
             if (row + kWarps < g.rows) {
                 const size_t ro = static_cast<size_t>(row + kWarps) * d.W;
-                if (n > 0) {
-                    In::load(In::at(xrow, ro), plane, n, d.vec, nxt);
+                const int nc = checked_run<kStride>(a.check, off0 + ro, n, plane);
+                if (nc > 0) {
+                    const void *px = In::at(xrow, ro);
+                    In::load(px, plane, nc, kStride ? d.vec : checked_vec(a.check, d.vec, px, In::kVecAlign), nxt);
                 } else {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) nxt[c] = Raw();
@@ -1030,7 +1102,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                 if constexpr (DX) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
-                        nxt[3 + c] = n > 0 ? PixIO<float>::load_s(grow + ro + c * plane, n) : Raw();
+                        nxt[3 + c] = nc > 0 ? PixIO<float>::load_s(grow + ro + c * plane, nc) : Raw();
                 }
             } else if (has_next) {
                 load_row(next, warp, nxt);
@@ -1090,7 +1162,15 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                         out[c][k] = fmaf(sl, ec[c], yy[c] + s0);
                     }
                 }
-                Out::template store<kStride>(d.y, plane, static_cast<size_t>(y) * d.W + xbase, out, n, d.vec);
+                {
+                    const size_t off = static_cast<size_t>(y) * d.W + xbase;
+                    const int nc = checked_run<kStride>(a.check, off, n, plane);
+                    const void *py = Out::at(d.y, off);
+                    // (float lanes 32 pixels apart make no vector accesses)
+                    if (nc > 0)
+                        Out::template store<kStride>(d.y, plane, off, out, nc,
+                                                     kStride ? d.vec : checked_vec(a.check, d.vec, py, Out::kVecAlign));
+                }
             }
             if constexpr (DX) {
             if (n > 0) {
@@ -1136,7 +1216,8 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
                     PixIO<float>::store_s(reinterpret_cast<float *>(d.y) + c * plane + static_cast<size_t>(y) * d.W + xbase,
-                                          make_float4(outd[c][0], outd[c][1], outd[c][2], outd[c][3]), n);
+                                          make_float4(outd[c][0], outd[c][1], outd[c][2], outd[c][3]),
+                                          checked_run<true>(a.check, static_cast<size_t>(y) * d.W + xbase, n, plane));
             }
             }
             __syncwarp();  // row tables are rewritten for the next row
