@@ -60,3 +60,23 @@ def test_single_rank_defaults():
     b = _bench()
     assert b.max_over_ranks(1, 3.5) == 3.5
     assert b.job_throughput(1, 8.2944, 1.0) == pytest.approx(8294.4)
+
+
+def test_reference_arm_line_on_cpu():
+    """bench.py --impl reference times the FP64 oracle on the host and prints
+    one JSON line with the headline's metric and unit, its sample and an e2e
+    entry that moves no bytes between host and device."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = [x for x in r.stdout.splitlines() if x.startswith("{")][-1]
+    j = json.loads(line)
+    b = _bench()
+    assert j["impl"] == "reference" and j["metric"] == b.METRIC and j["unit"] == "Mpix/s"
+    assert j["value"] > 0 and j["higher_is_better"] is True and j["steps"] == 2
+    assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["cores"] >= 1
+    assert "rows" in j["cpu_baseline"]["sample"]
+    assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["e2e"]["d2h_bytes_per_step"] == 0
