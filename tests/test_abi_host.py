@@ -103,3 +103,50 @@ def test_check_report_is_unsupported_in_the_normal_build(lib):
     out = (ctypes.c_uint32 * 4)(7, 7, 7, 7)
     assert lib.svdlut_check_report(out) == 2  # SVDLUT_ERR_UNSUPPORTED
     assert list(out) == [0, 0, 0, 0]
+
+
+def _params():
+    return _lib.Params(U=0x2000, S=0x3000, V=0x4000, lut_w=0x5000, g_xy=0x6000, g_xc=0x7000, g_yc=0x8000,
+                       grid_w=0x9000)
+
+
+def test_apply_io_rejects_bad_formats_and_pointers(lib):
+    d, p = _lib.Dims(33, 8, 6, 17, 17, 17), _params()
+    call = lambda fi, fo, x=0x10000, y=0x1000000, H=4, W=4: lib.svdlut_apply_io(  # noqa: E731
+        ctypes.byref(d), ctypes.byref(p), 1, H, W, fi, ctypes.c_void_p(x), fo, ctypes.c_void_p(y), None)
+    assert call(9, 1) == _lib.ERR_INVALID_ARG                     # unknown input format
+    assert call(2, 1, x=0) == _lib.ERR_INVALID_ARG                # null input
+    assert call(2, 1, x=0x10001) == _lib.ERR_INVALID_ARG          # 16-bit input at an odd address
+    assert call(2, 1, x=0x10000, y=0x10004) == _lib.ERR_INVALID_ARG  # overlapping images
+    assert call(1, 0) == _lib.ERR_UNSUPPORTED                     # 8-bit in, float out: not built
+    assert call(0, 2) == _lib.ERR_UNSUPPORTED                     # 16-bit output: not built
+    assert call(2, 1, H=0) == _lib.ERR_INVALID_ARG
+
+
+def test_lut3d_and_loss_entries_reject_bad_arguments(lib):
+    c = ctypes.c_void_p
+    assert lib.svdlut_lut3d_apply(34, c(0x1000), 1, 4, 4, c(0x10000), c(0x20000), c(0x30000), 1 << 20,
+                                  None) == _lib.ERR_INVALID_ARG          # D > 33
+    assert lib.svdlut_lut3d_apply(33, c(0x1000), 1, 4, 4, c(0x10000), c(0x20000), c(0x30000), 16,
+                                  None) == _lib.ERR_WORKSPACE            # workspace too small
+    assert lib.svdlut_lut3d_workspace_size(33, 2) == 2 * 33 ** 3 * 16
+    assert lib.svdlut_lut3d_fit2d(1, c(0x1000), 1, c(0x2000), c(0x3000), None) == _lib.ERR_INVALID_ARG
+    assert lib.svdlut_lut3d_fit2d(33, None, 1, c(0x2000), c(0x3000), None) == _lib.ERR_INVALID_ARG
+    assert lib.svdlut_cie94(c(0x1000), c(0x2000), 1, 4, 4, 1.0, None, 0, c(0x3000), c(0x4000), 16,
+                            None) == _lib.ERR_WORKSPACE
+    assert lib.svdlut_cie94(None, c(0x2000), 1, 4, 4, 1.0, None, 0, c(0x3000), c(0x4000), 4096,
+                            None) == _lib.ERR_INVALID_ARG
+    assert lib.svdlut_cie94(c(0x1002), c(0x2000), 1, 4, 4, 1.0, None, 0, c(0x3000), c(0x4000), 4096,
+                            None) == _lib.ERR_INVALID_ARG                # misaligned float array
+
+
+def test_apply_original_rejects_bad_arguments(lib):
+    d, p = _lib.Dims(33, 8, 6, 17, 17, 17), _params()
+    c = ctypes.c_void_p
+    need = lib.svdlut_apply_original_workspace_size(ctypes.byref(d), 1, 4, 4)
+    assert need > 0
+    args = lambda x, y, ws, nws: (ctypes.byref(d), ctypes.byref(p), c(0x1000), 1, 4, 4, c(x), c(y), c(ws), nws,  # noqa: E731
+                                  None)
+    assert lib.svdlut_apply_original(*args(0x10000, 0x10010, 0x100000, need)) == _lib.ERR_INVALID_ARG  # overlap
+    assert lib.svdlut_apply_original(*args(0x10000, 0x20000, 0x100000, need - 1)) == _lib.ERR_WORKSPACE
+    assert lib.svdlut_apply_original(*args(0x10000, 0x20000, 0x100010, need)) == _lib.ERR_INVALID_ARG  # ws alignment
