@@ -150,3 +150,19 @@ def test_apply_original_rejects_bad_arguments(lib):
     assert lib.svdlut_apply_original(*args(0x10000, 0x10010, 0x100000, need)) == _lib.ERR_INVALID_ARG  # overlap
     assert lib.svdlut_apply_original(*args(0x10000, 0x20000, 0x100000, need - 1)) == _lib.ERR_WORKSPACE
     assert lib.svdlut_apply_original(*args(0x10000, 0x20000, 0x100010, need)) == _lib.ERR_INVALID_ARG  # ws alignment
+
+
+def test_header_is_plain_c():
+    """include/svdlut.h compiles as C99 (no C++ or CUDA types leak into the
+    ABI) and as C++."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    hdr = os.path.join(ROOT, "include", "svdlut.h")
+    r = subprocess.run([cc, "-fsyntax-only", "-x", "c", "-std=c99", "-Wall", "-Wextra", "-Werror", hdr],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([cc, "-fsyntax-only", "-x", "c++", "-Wall", "-Werror", hdr], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
