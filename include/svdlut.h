@@ -318,17 +318,19 @@ svdlut_status svdlut_cie94(const float *y, const float *target, int B, int H, in
  *
  * Some callers may not call cudaMalloc / cudaFree or any allocating routine
  * themselves: a host whose device memory belongs to another runtime's pool,
- * a latency-critical loop where an allocation could stall on a device-wide
- * synchronisation, or code being recorded into a CUDA graph.  This entry takes
+ * or a latency-critical loop where an allocation could stall on a device-wide
+ * synchronisation.  This entry takes
  * the same arguments as svdlut_backward minus the workspace; its scratch space
  * is a fixed 32 MiB array inside the library (present on every GPU that loads
  * it, until the process exits), and it allocates nothing.
  *  - Sizes whose svdlut_backward_workspace_size exceeds 32 MiB are rejected
- *    with SVDLUT_ERR_UNSUPPORTED (e.g. 8 x 1920x1080 or one 3840x2160 image at
- *    D_t=33 and 1/8-resolution grids fit).
+ *    with SVDLUT_ERR_UNSUPPORTED.  The workspace plan depends on the GPU's SM
+ *    count; on a 152-SM GB300, 8 x 1920x1080 and one 3840x2160 image (D_t=33,
+ *    rank 8, K=8 grids at 1/8 resolution) fit.
  *  - The first call on a device looks up the array's device address (one
  *    cudaGetSymbolAddress with that device current); make that first call
- *    before any stream capture.
+ *    before any stream capture.  The lookup is repeated when the current
+ *    context has changed (e.g. after cudaDeviceReset).
  *  - All calls share the one array and leave their data in it.  Calls whose
  *    kernels overlap on the GPU (other streams, other threads) race on it:
  *    serialise them, e.g. on one stream.
@@ -364,7 +366,7 @@ size_t svdlut_apply_original_workspace_size(const svdlut_dims *dims, int B, int 
  * interleaved (HWC) ones [B][H][W][3] with channels (r, g, b) per pixel.
  * Integer inputs map code v to v / 255 (8-bit) or v / 65535 (16-bit);
  * 8-bit outputs are rint(clamp(Y, 0, 1) * 255) as for SVDLUT_U8.  The
- * 16-bit inputs are those of the tone-mapping and PPR10K tasks (Sec. 5.1).
+ * 16-bit inputs are those of the tone-mapping and PPR10K tasks (Sec. 4.1).
  */
 typedef enum {
     SVDLUT_PIX_F32 = 0,     /* planar float                    */

@@ -203,7 +203,7 @@ PIXEL_FORMATS = ("f32", "u8", "u16", "u8_hwc", "u16_hwc")
 
 def decode(v, fmt):
     """Pixels of format fmt -> planar FP64 in [0,1]: 8-bit codes v/255,
-    16-bit codes v/65535 (the 16-bit inputs of Sec. 5.1), float as is."""
+    16-bit codes v/65535 (the 16-bit inputs of Sec. 4.1), float as is."""
     if fmt not in PIXEL_FORMATS:
         raise ValueError(fmt)
     if fmt == "f32":

@@ -21,11 +21,23 @@ layers of a head (a rank-8 factorisation); H_t's output is split as U, then S,
 then V, each in [c][pair] order; H_s's as [K][plane xy, xc, yc][17][17].
 The parameter count at K = 6 is 160,478, Table 6 ("Ours", 160.478K).
 
-Parity status: the paper prints no activations or outputs of the generator,
-so its values are "parity unpinned" beyond: the parameter count (Table 6 and
-its ablation rows), brute-force convolution on tiny inputs, the
-interpolation/normalisation invariants and central differences of this
-module's own forward (tests/test_oracle_generator.py).
+Parity status: the paper prints no activations or outputs of the generator.
+Pinned (tests/test_oracle_generator.py): the parameter count (Table 6 and its
+ablation rows) of param_layout; conv against brute force on tiny inputs;
+downsample, inorm and avgpool4 against their defining invariants;
+splitmix64 against the published SplitMix64 outputs; backward against
+central differences of forward.  "Parity unpinned", function by function,
+because every pin above still passes if the reading is changed:
+  forward          the order conv -> LeakyReLU -> InstanceNorm within a layer
+                   (LeakyReLU and InstanceNorm swapped would pass), the slope
+                   0.2, eps 1e-5, and dropout before the pool;
+  heads_to_params  the split of each head's output (U, S, V order and the
+  params_to_heads  [c][pair] / [K][plane] layouts: a swapped U and V block
+                   would pass);
+  avgpool4         the 4x4 window (8x8 -> 2x2) as the paper's AvgPool;
+  downsample       half-pixel centres without antialiasing;
+  dropout_mask     keeping an element when the top bit of its SplitMix64
+                   output is 0 (the generator itself is pinned).
 """
 from __future__ import annotations
 

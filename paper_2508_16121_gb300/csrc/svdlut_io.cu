@@ -1,5 +1,5 @@
 // svdlut_apply_io: the fused transform between pixel formats.  The 16-bit
-// inputs (the tone-mapping and PPR10K photos, Sec. 5.1) and interleaved
+// inputs (the tone-mapping and PPR10K photos, Sec. 4.1) and interleaved
 // 8-bit frames are decoded, and 8-bit outputs encoded, inside apply_kernel,
 // so a 16-bit photo goes to an 8-bit result in one pass over HBM with no
 // conversion buffers.  Only the pairs listed in svdlut.h are instantiated.

@@ -32,11 +32,26 @@ def _torch():
     return torch
 
 
+def step_decay_lr(base_lr: float, step: int, every: int | None, factor: float = 0.1) -> float:
+    """Learning rate of optimizer step `step` (1-based) under the paper's
+    schedule (Sec. 4.2: Adam at 1e-4, multiplied by 0.1 every 100 epochs):
+    base_lr * factor ** floor((step - 1) / every); constant when every is
+    None or 0."""
+    if not every:
+        return float(base_lr)
+    if step < 1:
+        raise ValueError("steps are counted from 1")
+    return float(base_lr) * float(factor) ** ((step - 1) // int(every))
+
+
 class Trainer:
     def __init__(self, K=8, batch=64, size=256, lr=1e-3, seed=0, teacher_seed=1, teacher_scale=0.1,
-                 data_seed=2, device="cuda", cie94_weight=CIE94_WEIGHT):
+                 data_seed=2, device="cuda", cie94_weight=CIE94_WEIGHT, lr_decay_every=None, lr_decay=0.1):
+        """lr_decay_every: multiply the learning rate by lr_decay every that
+        many steps (the paper's step decay, Sec. 4.2); None keeps it constant."""
         torch = _torch()
         self.K, self.batch, self.size, self.lr = K, batch, size, lr
+        self.lr_decay_every, self.lr_decay = lr_decay_every, float(lr_decay)
         self.cie94_weight = float(cie94_weight)
         self.device = torch.device(device)
         self.data_seed = data_seed
@@ -75,9 +90,13 @@ class Trainer:
             loss = loss + self.cie94_weight * cie94(y, yt, self.cie94_weight, dy=self.dy, accumulate=True)
         g = backward(x, sp, self.dy, want=tuple("d" + n for n in PARAM_NAMES), workspace=self.bwd_ws)
         self.student.backward({n: g["d" + n] for n in PARAM_NAMES}, dweights=self.dw)
-        adam_step(self.student.weights, self.dw, self.m, self.v, self.step, lr=self.lr)
+        adam_step(self.student.weights, self.dw, self.m, self.v, self.step, lr=self.current_lr())
         self.losses.append(loss)
         return loss
+
+    def current_lr(self):
+        """learning rate of the step being taken (self.step, 1-based)"""
+        return step_decay_lr(self.lr, max(self.step, 1), self.lr_decay_every, self.lr_decay)
 
     def run(self, steps):
         for _ in range(steps):
@@ -90,7 +109,8 @@ class Trainer:
     def save(self, path):
         torch = _torch()
         torch.save({"K": self.K, "batch": self.batch, "size": self.size, "lr": self.lr, "step": self.step,
-                    "data_seed": self.data_seed, "cie94_weight": self.cie94_weight, "weights": self.student.weights.cpu(), "m": self.m.cpu(),
+                    "data_seed": self.data_seed, "cie94_weight": self.cie94_weight, "lr_decay_every": self.lr_decay_every,
+                    "lr_decay": self.lr_decay, "weights": self.student.weights.cpu(), "m": self.m.cpu(),
                     "v": self.v.cpu(), "teacher": self.teacher.weights.cpu(), "version": 1}, path)
 
     def load(self, path):
@@ -104,6 +124,8 @@ class Trainer:
         self.v.copy_(ck["v"].to(self.device))
         self.step, self.lr, self.data_seed = ck["step"], ck["lr"], ck["data_seed"]
         self.cie94_weight = ck.get("cie94_weight", self.cie94_weight)
+        self.lr_decay_every = ck.get("lr_decay_every", self.lr_decay_every)
+        self.lr_decay = ck.get("lr_decay", self.lr_decay)
 
 
 def psnr(y, t):
@@ -147,11 +169,15 @@ def main(argv=None):
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--K", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-decay-every", type=int, default=0,
+                    help="multiply the learning rate by --lr-decay every N steps (0: constant)")
+    ap.add_argument("--lr-decay", type=float, default=0.1)
     ap.add_argument("--cie94", type=float, default=CIE94_WEIGHT, help="weight of the CIE94 term (0: MSE only)")
     ap.add_argument("--eval", action="store_true", help="held-out PSNR before and after")
     ap.add_argument("--save", default=None, help="checkpoint path")
     args = ap.parse_args(argv)
-    tr = Trainer(K=args.K, batch=args.batch, size=args.size, lr=args.lr, cie94_weight=args.cie94)
+    tr = Trainer(K=args.K, batch=args.batch, size=args.size, lr=args.lr, cie94_weight=args.cie94,
+                 lr_decay_every=args.lr_decay_every or None, lr_decay=args.lr_decay)
     if args.eval:
         print("before:", evaluate(tr))
     losses = tr.run(args.steps)

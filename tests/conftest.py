@@ -11,9 +11,14 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built CUDA library")
     config.addinivalue_line("markers", "slow: takes more than a few seconds")
+    config.addinivalue_line("markers", "quarantined(reason): GPU test kept out of every run (see its reason)")
 
 
 def pytest_collection_modifyitems(config, items):
+    for it in items:
+        m = it.get_closest_marker("quarantined")
+        if m is not None:
+            it.add_marker(pytest.mark.skip(reason="quarantined: " + (m.args[0] if m.args else "")))
     try:
         import torch
         has_gpu = torch.cuda.is_available()

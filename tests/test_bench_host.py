@@ -80,3 +80,23 @@ def test_reference_arm_line_on_cpu():
     assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["cores"] >= 1
     assert "rows" in j["cpu_baseline"]["sample"]
     assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_spread_and_profiled_traffic(tmp_path, monkeypatch):
+    """Per-step spread (median, p10, p90) and the DRAM counters of the
+    headline kernel, read from the JSON beside its ncu summary only when they
+    were taken on the current kernel sources."""
+    import json
+    b = _bench()
+    s = b.spread([1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0, 8.0, 9.0, 10.0, 11.0])
+    assert s["median"] == 6.0 and s["p10"] == 2.0 and s["p90"] == 10.0 and s["steps"] == 11
+    counters = tmp_path / "c.json"
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    monkeypatch.setattr(b, "PROFILE_COUNTERS", "c.json")
+    monkeypatch.setattr(b, "kernel_hash", lambda read=None: "abc")
+    counters.write_text(json.dumps({"kernel_sources_sha256_16": "abc", "dram_bytes_per_launch": 123}))
+    assert b.profiled_traffic() == 123
+    counters.write_text(json.dumps({"kernel_sources_sha256_16": "old", "dram_bytes_per_launch": 123}))
+    assert b.profiled_traffic() is None
+    counters.write_text("not json")
+    assert b.profiled_traffic() is None

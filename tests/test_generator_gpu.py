@@ -4,20 +4,22 @@ C ABI) against the FP64 generator oracle.
 The convolutions run on BF16 tensor cores (FP32 accumulation), so the bar is
 relative: every predicted parameter array within 2e-2 of the oracle's (norm
 of the difference over the norm of the reference), weight gradients with
-cosine similarity >= 0.999 to the FP64 oracle's.  Per parameter group the
-gradient is compared (relative error <= 5e-2) with the oracle whose
-convolutions multiply BF16-rounded operands: the LeakyReLU sign decisions,
-and through InstanceNorm's cancelling backward the first layers' gradients,
-depend on that rounding (8-19 % between FP64 and BF16 operands in the FP64
-oracle itself), so both sides take those decisions in the kernel's
-precision.  Dropout masks, Adam and MSE are compared exactly / to FP32
-rounding.
+cosine similarity >= 0.999 to the FP64 oracle's, and every parameter group
+of the gradient within its bound of the FP64 oracle (GRAD_GROUP_BOUNDS:
+3 % for the heads, 20 % for the last conv layer and its norm, 50 % for the
+early layers).  Those bounds are about twice what the FP64 oracle itself
+moves when only its convolution operands are rounded to BF16 (LeakyReLU
+decisions near zero, amplified by InstanceNorm's backward); the CPU test
+test_oracle_generator.py pins that margin.  The gradient of the oracle with
+BF16-rounded operands is printed beside it as a diagnostic only.  Dropout
+masks, Adam and MSE are compared exactly / to FP32 rounding.
 """
 import numpy as np
 import pytest
 
 import svdlut_inputs as si
 from oracle import generator as G
+from test_oracle_generator import grad_group_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -103,11 +105,14 @@ def test_backward_matches_oracle(sv, training):
     got = dw.cpu().numpy().astype(np.float64)
     cos = float(got @ ref64) / (np.linalg.norm(got) * np.linalg.norm(ref64))
     assert cos >= 0.999, cos
+    pg, p64 = G.unpack(got, K), G.unpack(ref64, K)
+    errs = {n: rel(pg[n], p64[n]) for n in p64}
+    bad = {n: (e, grad_group_bound(n)) for n, e in errs.items() if e > grad_group_bound(n)}
+    # diagnostic: the same groups against the oracle with BF16-rounded conv operands
     _, cache_b = G.forward(blob, x, K, drop_mask=mask, conv_operands="bf16")
-    ref = G.backward(blob, K, cache_b, d64)
-    pg, pr = G.unpack(got, K), G.unpack(ref, K)
-    errs = {n: rel(pg[n], pr[n]) for n in pr}
-    bad = {n: e for n, e in errs.items() if e > 5e-2}
+    pb = G.unpack(G.backward(blob, K, cache_b, d64), K)
+    print("per-group rel. error vs FP64 oracle / vs BF16-operand oracle:",
+          {n: (round(errs[n], 4), round(rel(pg[n], pb[n]), 4)) for n in p64})
     assert not bad, (bad, errs)
 
 

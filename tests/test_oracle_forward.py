@@ -221,6 +221,8 @@ def test_batched_equals_per_image():
 def test_u8_conversions():
     v = np.arange(256, dtype=np.uint8)
     assert np.array_equal(oracle.u8_to_unit(v), v / 255.0)
-    y = np.array([-0.1, 0.0, 0.5 / 255, 1.5 / 255, 0.2, 1.0, 7.0])
+    # clamp, then round to nearest in FP64; 0.5 * 255 = 127.5 exactly (the
+    # one exact half-integer code in [0, 1]) rounds to the even 128
+    y = np.array([-0.1, 0.0, 0.3 / 255, 0.7 / 255, 0.2, 0.5, 254.4 / 255, 254.6 / 255, 1.0, 7.0])
     q = oracle.quantize_u8(y)
-    assert list(q) == [0, 0, 0, 2, 51, 255, 255]
+    assert list(q) == [0, 0, 0, 1, 51, 128, 254, 255, 255, 255]

@@ -132,3 +132,68 @@ def test_bf16_rounding_definition():
     assert G.bf16_round(-3.0) == -3.0 and G.bf16_round(0.0) == 0.0
     x = np.random.default_rng(5).normal(size=1000)
     assert np.all(np.abs(G.bf16_round(x) - x) <= np.abs(x) * 2.0 ** -8)
+
+
+SPLITMIX_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "splitmix64.txt")
+
+
+def test_splitmix64_known_answers():
+    """The dropout mask's counter-based generator against the published
+    SplitMix64 outputs (tests/golden/splitmix64.txt): output n of the
+    generator seeded with s is the finaliser applied to s + n * golden."""
+    golden_inc = np.uint64(0x9E3779B97F4A7C15)
+    rows = 0
+    for line in open(SPLITMIX_GOLDEN):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        seed, outs = line.split(":")
+        want = [int(v) for v in outs.split()]
+        with np.errstate(over="ignore"):
+            states = np.uint64(int(seed)) + golden_inc * np.arange(len(want), dtype=np.uint64)
+        got = [int(v) for v in G.splitmix64(states)]
+        assert got == want, seed
+        rows += 1
+    assert rows == 2
+
+
+# Per-group bounds of the GPU generator's weight gradient against the FP64
+# oracle (tests/test_generator_gpu.py): relative error ||g - ref|| / ||ref||
+# of each parameter group.  The GPU convolutions multiply BF16-rounded
+# operands; that rounding flips LeakyReLU decisions on near-zero
+# pre-activations, and InstanceNorm's backward (which cancels the mean and
+# the projection on the normalised activation) amplifies the flips in the
+# early layers.  The bounds are set at about twice the change that the FP64
+# oracle itself shows when only its convolution operands are rounded to BF16
+# (test below): the heads see the backbone only through the pooled context
+# and move by < 1 %, the last layers by < 8 %, the first layers by up to 23 %.
+GRAD_GROUP_BOUNDS = (("h", 0.03), ("conv4.", 0.2), ("in3.", 0.2), ("", 0.5))
+
+
+def grad_group_bound(name):
+    for prefix, bound in GRAD_GROUP_BOUNDS:
+        if name.startswith(prefix):
+            return bound
+    raise KeyError(name)
+
+
+def test_bf16_operand_sensitivity_is_within_half_the_gpu_bounds():
+    """The justification of GRAD_GROUP_BOUNDS, on the GPU test's own case: the
+    FP64 oracle's gradient, recomputed with BF16-rounded convolution
+    operands, stays within half of each group's bound."""
+    import svdlut_inputs as si
+    K, B, seed = 6, 3, 777
+    rng = np.random.default_rng(50)
+    blob = G.identity_blob(K, rng, scale=0.05)
+    blob = blob + rng.normal(0, 0.01, size=blob.shape) * (np.abs(blob) > 0)
+    x = np.stack([si.make_image(np.random.default_rng(60 + j), 200, 240) for j in range(B)])
+    for mask in (None, G.dropout_mask(seed, B)):
+        out, cache = G.forward(blob, x, K, drop_mask=mask)
+        r = np.random.default_rng(70)
+        d = {k: r.normal(size=tuple(v.shape)).astype(np.float32).astype(np.float64) for k, v in out.items()}
+        g64 = G.unpack(G.backward(blob, K, cache, d), K)
+        _, cache_b = G.forward(blob, x, K, drop_mask=mask, conv_operands="bf16")
+        gb = G.unpack(G.backward(blob, K, cache_b, d), K)
+        for n in g64:
+            den = max(np.linalg.norm(g64[n]), 1e-30)
+            assert np.linalg.norm(gb[n] - g64[n]) / den <= 0.5 * grad_group_bound(n), n

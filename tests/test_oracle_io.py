@@ -1,5 +1,5 @@
 """Pins of the oracle's pixel-format helpers (the 16-bit and interleaved
-inputs of Sec. 5.1): 16-bit and 8-bit codes agree where they name the same
+inputs of Sec. 4.1): 16-bit and 8-bit codes agree where they name the same
 value (65535 = 255 * 257), hand-written interleaved images decode to the
 expected planes, 8-bit codes survive a decode/encode round trip, and the
 identity transform maps 16-bit codes to round(v / 257) in 8 bits."""

@@ -83,3 +83,19 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                      ctypes.byref(g), None)
     assert st == _lib.ERR_UNSUPPORTED
     assert b"scratch" in lib.svdlut_last_error()
+
+
+def test_noalloc_scratch_holds_the_sizes_the_header_names():
+    """The header says 8 x 1920x1080 and one 3840x2160 image (D_t=33, rank 8,
+    K=8 grids at 1/8 resolution) fit the fixed scratch on a GB300; the
+    workspace plan depends on the SM count, so check it on this GPU."""
+    import torch
+    import paper_2508_16121_gb300 as sv
+    from paper_2508_16121_gb300 import _lib
+    lib = _lib.load(build_if_missing=True)
+    if torch.cuda.get_device_properties(0).multi_processor_count != 152:
+        pytest.skip("the sizes are stated for a 152-SM GB300")
+    for B, H, W in ((8, 1080, 1920), (1, 2160, 3840)):
+        d = sv.dims_of(sv.to_device(si.make_params(np.random.default_rng(403), si.spatial_dims(H, W))))
+        need = lib.svdlut_backward_workspace_size(ctypes.byref(d), B, H, W)
+        assert 0 < need <= 32 << 20, (B, H, W, need)
