@@ -66,10 +66,15 @@ struct LaunchArgs {
     int nvx_max, nvy_max, bh_max;
     int lcell_floats;    // floats reserved for the cell table
     int scratch_floats;  // floats of the block buffers / prologue temporaries
+    int xcol;            // nonzero: per-column xc tables (every image's Dsc <= kXcolMaxDsc)
     unsigned int *queue;  // non-null: blocks are taken from this counter (must be 0 at launch)
     unsigned int *check;  // index-check status (builds with SVDLUT_CHECK_BOUNDS), else null
     ImgDesc img[N];
 };
+
+// Largest intensity-vertex count whose xc slice is tabulated per block column
+// (3 x Dsc x 128 floats: 36 KB at 24); larger Dsc use the per-cell slope form.
+constexpr int kXcolMaxDsc = 24;
 
 // ---- optional index checks ----
 // Built with -DSVDLUT_CHECK_BOUNDS, every shared-memory gather index of the
@@ -108,13 +113,12 @@ __device__ __forceinline__ int checked_index(unsigned int *st, unsigned int site
 #endif
 }
 
-// A lane's n pixels from offset off (32 apart when STRIDE, else adjacent)
-// must lie in a plane of `plane` pixels; returns n, or 0 after a failure.
-template <bool STRIDE>
+// A lane's n adjacent pixels from offset off must lie in a plane of `plane`
+// pixels; returns n, or 0 after a failure.
 __device__ __forceinline__ int checked_run(unsigned int *st, size_t off, int n, size_t plane)
 {
 #ifdef SVDLUT_CHECK_BOUNDS
-    if (n <= 0 || off + (STRIDE ? 32 * static_cast<size_t>(n - 1) : static_cast<size_t>(n - 1)) < plane) return n;
+    if (n <= 0 || off + static_cast<size_t>(n - 1) < plane) return n;
     check_record(st, kChkPixel, static_cast<unsigned int>(off), static_cast<unsigned int>(plane));
     return 0;
 #else
@@ -275,26 +279,26 @@ struct PixIO<uint8_t> {
 };
 
 // ---- pixel formats of the transform's input and output ----
-// A lane handles 4 pixels of a tile row: columns lane + 32 k (k < n) when the
-// input format has kStride (planar float: each warp-wide access covers 32
-// adjacent pixels), else columns lane * 4 + k.  `off` is the offset y * W + x
-// of the lane's first pixel, at(base, off) its address, `plane` = H * W.
-// load(at(..), plane, ..) fills Raw r[3] with the lane's pixels; unpack() turns them into the channel values (r, g, b) of the
-// 4 pixels.  kVecAlign: the alignment that makes the whole-lane vector access
+// A lane handles 4 adjacent pixels of a tile row (columns lane * 4 + k, k <
+// n), so a whole lane is one 128-bit access per float plane (one 32- or
+// 64-bit access per 8- or 16-bit plane or interleaved word).  `off` is the
+// offset y * W + x of the lane's first pixel, at(base, off) its address,
+// `plane` = H * W.  load(at(..), plane, ..) fills Raw r[3] with the lane's
+// pixels; unpack() turns them into the channel values (r, g, b) of the 4
+// pixels.  kVecAlign: the alignment that makes the whole-lane vector access
 // legal (with W % 4 == 0).
 struct InF32 {  // planar float [3][H][W]
     using Raw = float4;  // one per channel
-    static constexpr bool kStride = true;
-    static constexpr size_t kPixelBytes = 12, kVecAlign = 4;
+    static constexpr size_t kPixelBytes = 12, kVecAlign = 16;
     static __device__ __forceinline__ const void *at(const void *base, size_t off)
     {
         return static_cast<const float *>(base) + off;
     }
-    static __device__ __forceinline__ void load(const void *q, size_t plane, int n, bool, Raw *r)
+    static __device__ __forceinline__ void load(const void *q, size_t plane, int n, bool vec, Raw *r)
     {
         const float *p = static_cast<const float *>(q);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) r[c] = PixIO<float>::load_s(p + c * plane, n);
+        for (int c = 0; c < 3; ++c) r[c] = PixIO<float>::load(p + c * plane, n, vec);
     }
     static __device__ __forceinline__ void unpack(const Raw *r, float4 (&v)[3])
     {
@@ -306,7 +310,6 @@ struct InF32 {  // planar float [3][H][W]
 
 struct InU8 {  // planar 8-bit [3][H][W], value v / 255
     using Raw = unsigned int;  // one per channel, byte k = pixel k
-    static constexpr bool kStride = false;
     static constexpr size_t kPixelBytes = 3, kVecAlign = 4;
     static __device__ __forceinline__ const void *at(const void *base, size_t off)
     {
@@ -345,7 +348,6 @@ __device__ __forceinline__ uint2 load_u16x4(const uint16_t *p, int n, bool vec)
 
 struct InU16 {  // planar 16-bit [3][H][W], value v / 65535
     using Raw = uint2;  // one per channel: pixels (0, 1) and (2, 3)
-    static constexpr bool kStride = false;
     static constexpr size_t kPixelBytes = 6, kVecAlign = 8;
     static __device__ __forceinline__ const void *at(const void *base, size_t off)
     {
@@ -376,7 +378,6 @@ __device__ __forceinline__ float byte_value(unsigned int w, int b)
 struct InU8Hwc {  // interleaved 8-bit [H][W][3], value v / 255
     // 12 bytes of 4 pixels: r0 g0 b0 r1 | g1 b1 r2 g2 | b2 r3 g3 b3
     using Raw = unsigned int;
-    static constexpr bool kStride = false;
     static constexpr size_t kPixelBytes = 3, kVecAlign = 4;
     static __device__ __forceinline__ const void *at(const void *base, size_t off)
     {
@@ -415,7 +416,6 @@ struct InU8Hwc {  // interleaved 8-bit [H][W][3], value v / 255
 struct InU16Hwc {  // interleaved 16-bit [H][W][3], value v / 65535
     // 24 bytes of 4 pixels as 6 words: (r0 g0) (b0 r1) | (g1 b1) (r2 g2) | (b2 r3) (g3 b3)
     using Raw = uint2;
-    static constexpr bool kStride = false;
     static constexpr size_t kPixelBytes = 6, kVecAlign = 8;
     static __device__ __forceinline__ const void *at(const void *base, size_t off)
     {
@@ -452,25 +452,20 @@ struct InU16Hwc {  // interleaved 16-bit [H][W][3], value v / 65535
     }
 };
 
-// Outputs: o[c][k] = channel c of the lane's pixel k.  STRIDE: the lane
-// mapping of the input format.
+// Outputs: o[c][k] = channel c of the lane's pixel k.
 struct OutF32 {  // planar float
     static constexpr size_t kPixelBytes = 12, kVecAlign = 16;
     static __device__ __forceinline__ const void *at(const void *base, size_t off)
     {
         return static_cast<const float *>(base) + off;
     }
-    template <bool STRIDE>
     static __device__ __forceinline__ void store(void *base, size_t plane, size_t off, const float (&o)[3][4], int n,
                                                  bool vec)
     {
         float *p = static_cast<float *>(base) + off;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float4 v = make_float4(o[c][0], o[c][1], o[c][2], o[c][3]);
-            if constexpr (STRIDE) PixIO<float>::store_s(p + c * plane, v, n);
-            else PixIO<float>::store(p + c * plane, v, n, vec);
-        }
+        for (int c = 0; c < 3; ++c)
+            PixIO<float>::store(p + c * plane, make_float4(o[c][0], o[c][1], o[c][2], o[c][3]), n, vec);
     }
 };
 
@@ -480,11 +475,9 @@ struct OutU8 {  // planar 8-bit, rint(clamp(y, 0, 1) * 255)
     {
         return static_cast<const uint8_t *>(base) + off;
     }
-    template <bool STRIDE>
     static __device__ __forceinline__ void store(void *base, size_t plane, size_t off, const float (&o)[3][4], int n,
                                                  bool vec)
     {
-        static_assert(!STRIDE, "8-bit output needs adjacent pixels per lane");
         uint8_t *p = static_cast<uint8_t *>(base) + off;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -504,11 +497,9 @@ struct OutU8Hwc {  // interleaved 8-bit, rint(clamp(y, 0, 1) * 255)
     {
         return static_cast<const uint8_t *>(base) + 3 * off;
     }
-    template <bool STRIDE>
     static __device__ __forceinline__ void store(void *base, size_t, size_t off, const float (&o)[3][4], int n,
                                                  bool vec)
     {
-        static_assert(!STRIDE, "8-bit output needs adjacent pixels per lane");
         uint8_t *p = static_cast<uint8_t *>(base) + 3 * off;
         unsigned int q[3][4];
 #pragma unroll
@@ -536,7 +527,6 @@ template <class IN, class OUT>
 struct Io {
     using In = IN;
     using Out = OUT;
-    static_assert(!IN::kStride || std::is_same<OUT, OutF32>::value, "strided lanes need float output");
 };
 
 using IoF32 = Io<InF32, OutF32>;
@@ -759,9 +749,15 @@ __device__ __forceinline__ BlockGeom block_geom(const ImgDesc &d, int lb, int nv
 //   fxy [3][nvy][nvx], fxc [3][nvx][Dsc], fyc [3][nvy][Dsc]   folded grid slices
 //   coli [kTileW] int, cold [kTileW]                           column cells
 //   rowi [bh] int, rowd [bh]                                    row cells
-//   pxc [3][nvx-1][Dsc] float4   xc slope form of x-cell ix, intensity cell j
-//                                (see block_phase_b); row stride Dsc (one
-//                                padding entry) to spread banks
+//   the xc slice, in one of two forms (LaunchArgs::xcol):
+//     xcol [3][Dsc][kTileW]: the folded xc slice interpolated along x at each
+//          column of the block, per intensity vertex; column col is stored
+//          at (col & 3) * 32 + (col >> 2), so that pixel k of every lane of a
+//          warp (column lane * 4 + k) reads consecutive words: no bank
+//          conflicts whatever the intensities;
+//     pxc [3][nvx-1][Dsc] float4: slope form of x-cell ix and intensity cell
+//          j (see block_phase_b), for large Dsc where xcol does not fit; row
+//          stride Dsc (one padding entry) to spread banks
 //   per warp: rxy [nvx] float4 (xy interpolated along y for the warp's row),
 //             ryc [3][Dsc-1] float2 (yc interpolated along y: value at j and
 //             slope to j + 1)
@@ -769,6 +765,7 @@ struct BlockBufs {
     float *fxy, *fxc, *fyc;
     int *coli, *rowi;
     float *cold, *rowd;
+    float *xcol;
     float4 *pxc, *rxy;
     float2 *ryc;
 };
@@ -781,13 +778,18 @@ __host__ __device__ inline int fold_floats(int nvx, int nvy, int Dsc)
     return (3 * nvy * nvx + 3 * nvx * Dsc + 3 * nvy * Dsc + 3) & ~3;
 }
 
-__host__ __device__ inline int block_floats(int nvx, int nvy, int Dsc, int bh)
+__host__ __device__ inline int xc_table_floats(int nvx, int Dsc, bool xcol)
 {
-    return fold_floats(nvx, nvy, Dsc) + 2 * kTileW + ((2 * bh + 3) & ~3) + 3 * (nvx - 1) * Dsc * 4 +
+    return xcol ? 3 * Dsc * kTileW : 3 * (nvx - 1) * Dsc * 4;
+}
+
+__host__ __device__ inline int block_floats(int nvx, int nvy, int Dsc, int bh, bool xcol)
+{
+    return fold_floats(nvx, nvy, Dsc) + 2 * kTileW + ((2 * bh + 3) & ~3) + xc_table_floats(nvx, Dsc, xcol) +
            kWarps * warp_row_floats(nvx, Dsc);
 }
 
-__device__ __forceinline__ BlockBufs block_bufs(float *scratch, int nvx, int nvy, int Dsc, int bh_max)
+__device__ __forceinline__ BlockBufs block_bufs(float *scratch, int nvx, int nvy, int Dsc, int bh_max, bool xcol)
 {
     BlockBufs b;
     const int warp = threadIdx.x >> 5;
@@ -799,8 +801,10 @@ __device__ __forceinline__ BlockBufs block_bufs(float *scratch, int nvx, int nvy
     b.cold = t + kTileW;
     b.rowi = reinterpret_cast<int *>(t + 2 * kTileW);
     b.rowd = t + 2 * kTileW + bh_max;
-    b.pxc = reinterpret_cast<float4 *>(t + 2 * kTileW + ((2 * bh_max + 3) & ~3));
-    float *w = reinterpret_cast<float *>(b.pxc + 3 * (nvx - 1) * Dsc) + warp * warp_row_floats(nvx, Dsc);
+    float *xt = t + 2 * kTileW + ((2 * bh_max + 3) & ~3);
+    b.xcol = xt;
+    b.pxc = reinterpret_cast<float4 *>(xt);
+    float *w = xt + xc_table_floats(nvx, Dsc, xcol) + warp * warp_row_floats(nvx, Dsc);
     b.rxy = reinterpret_cast<float4 *>(w);
     b.ryc = reinterpret_cast<float2 *>(w + nvx * 4);
     return b;
@@ -901,13 +905,29 @@ __device__ inline void block_phase_a(const ImgDesc &d, const BlockGeom &g, const
     }
 }
 
-// Block setup, phase B: the folded xc slice of x-cell ix and intensity cell j
-// in slope form (F, F(j+1) - F(j), F(ix+1) - F(ix), [F(ix+1,j+1) - F(ix+1,j)] -
-// [F(ix,j+1) - F(ix,j)]), so that at (dx, e) it is (x + dx z) + e (y + dx w).
-__device__ inline void block_phase_b(const ImgDesc &d, const BlockGeom &g, const BlockBufs &b)
+// Block setup, phase B: the xc slice table of the block.
+//  xcol: value of the folded xc slice at column col and intensity vertex j,
+//        (1 - dx) F(ix, j) + dx F(ix + 1, j) (Supp. Eq. 20 along x), at the
+//        permuted position of the column (see BlockBufs).
+//  pxc:  the slice of x-cell ix and intensity cell j in slope form (F,
+//        F(j+1) - F(j), F(ix+1) - F(ix), [F(ix+1,j+1) - F(ix+1,j)] -
+//        [F(ix,j+1) - F(ix,j)]), so that at (dx, e) it is (x + dx z) +
+//        e (y + dx w).
+__device__ inline void block_phase_b(const ImgDesc &d, const BlockGeom &g, const BlockBufs &b, bool xcol)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nvx = g.nvx, Dsc = d.Dsc, Dc1 = Dsc - 1;
+    if (xcol) {
+        for (int e = threadIdx.x; e < 3 * Dsc * kTileW; e += kThreads) {
+            const int col = e & (kTileW - 1), r = e >> 7;  // r = c * Dsc + j
+            const int c = r >= Dsc ? (r >= 2 * Dsc ? 2 : 1) : 0, j = r - c * Dsc;
+            const int ix = b.coli[col];
+            const float *f0 = b.fxc + (c * nvx + ix) * Dsc + j;
+            const float v0 = f0[0], v1 = f0[Dsc];
+            b.xcol[r * kTileW + (col & 3) * 32 + (col >> 2)] = fmaf(v1 - v0, b.cold[col], v0);
+        }
+        return;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int r = warp; r < 3 * (nvx - 1); r += kWarps) {
         const int c = r / (nvx - 1), ixl = r - c * (nvx - 1);
         const float *f0 = b.fxc + (c * nvx + ixl) * Dsc;
@@ -946,25 +966,40 @@ __device__ __forceinline__ void warp_row_tables(const BlockGeom &g, const BlockB
 }
 
 // One LUT pair: add the folded, weighted bilinear value of the three output
-// channels (coefficient form of Supp. Eq. 15).  q points at the cell's 3 float4.
-__device__ __forceinline__ void lut_pair(const float4 *__restrict__ q, float da, float db, float &y0, float &y1,
-                                         float &y2)
+// channels (coefficient form of Supp. Eq. 15) from the cell's 3 float4.
+__device__ __forceinline__ void lut_pair(const float4 &q0, const float4 &q1, const float4 &q2, float da, float db,
+                                         float &y0, float &y1, float &y2)
 {
-    const float4 q0 = q[0];
-    const float4 q1 = q[1];
-    const float4 q2 = q[2];
     y0 += fmaf(fmaf(q2.y, da, q1.z), db, fmaf(q0.w, da, q0.x));
     y1 += fmaf(fmaf(q2.z, da, q1.w), db, fmaf(q1.x, da, q0.y));
     y2 += fmaf(fmaf(q2.w, da, q2.x), db, fmaf(q1.y, da, q0.z));
 }
 
+// One LUT pair's part of the adjoint: with upstream gradients g of the three
+// output channels, d/dp_alpha and d/dp_beta of sum_c g_c phi_c (weights
+// already folded in): (D-1) (b + d db) and (D-1) (c + d da) per channel.
+__device__ __forceinline__ void lut_pair_dx(const float4 &q0, const float4 &q1, const float4 &q2, float da, float db,
+                                            const float (&g)[3], float fD1, float &ga, float &gb)
+{
+    // b = (q0.w, q1.x, q1.y), c = (q1.z, q1.w, q2.x), d = (q2.y, q2.z, q2.w)
+    const float sa = g[0] * fmaf(q2.y, db, q0.w) + g[1] * fmaf(q2.z, db, q1.x) + g[2] * fmaf(q2.w, db, q1.y);
+    const float sb = g[0] * fmaf(q2.y, da, q1.z) + g[1] * fmaf(q2.z, da, q1.w) + g[2] * fmaf(q2.w, da, q2.x);
+    ga = fmaf(fD1, sa, ga);
+    gb = fmaf(fD1, sb, gb);
+}
+
+static_assert(kTileW == 128, "the xcol table and the lane mapping assume 128-pixel tiles");
+
 // DX = false: the forward transform, y = f(x).
-// DX = true (T = float): the pixel part of the adjoint, dx = (df/dx)^T dy,
-// from the slopes of the same cell coefficients: for a pair (alpha, beta),
-// d phi / d p_alpha = (D-1) (b + d delta_beta), d phi / d p_beta = (D-1) (c +
-// d delta_alpha) per output channel (weights already folded in); the xc / yc
+// DX = true (float images): the pixel part of the adjoint, dx = (df/dx)^T dy,
+// from the slopes of the same cell coefficients (lut_pair_dx); the xc / yc
 // terms add (Dsc-1) (s1 - s0) for their channel; zero where the input was
 // clamped (outside [0,1]).
+//
+// A lane takes 4 adjacent pixels of a row (one 128-bit access per float
+// plane).  Every pixel gathers its own cells: reusing a lane's previous cell
+// when unchanged saved shared-memory wavefronts in smooth regions but cost
+// more in compares than it saved.
 template <class IO, int N, bool DX>
 __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constant__ LaunchArgs<N> a)
 {
@@ -974,6 +1009,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
     float *scratch = misc + kMiscFloats;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool xcol = a.xcol != 0;
     // Block schedule: a contiguous range per CTA, or (queue) blocks taken in
     // order from a global counter so that uneven blocks balance out.
     int *slot = reinterpret_cast<int *>(misc + kMaxK * 4 + 3);
@@ -994,14 +1030,9 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
     using Out = typename IO::Out;
     using Raw = typename In::Raw;
     static_assert(!DX || std::is_same<IO, IoF32>::value, "the adjoint takes float images");
-    // Pixel k of a lane in a 128-pixel tile row: column lane + 32 k for float
-    // images (each warp-wide access covers 32 adjacent pixels, so lanes of a
-    // coherent region gather the same table cells), lane * 4 + k for integer
-    // images (one 32- or 64-bit access per lane and plane or word).
-    constexpr bool kStride = In::kStride;
+    // the lane's pixels of a tile row: columns x0 + lane * 4 + k, k < n
     auto lane_px = [&](int W, int x0, int &x) {
-        x = x0 + (kStride ? lane : lane * 4);
-        if (kStride) return x < W ? min(4, (W - x + 31) >> 5) : 0;
+        x = x0 + lane * 4;
         return min(4, W - x);
     };
 
@@ -1010,8 +1041,25 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         while (im + 1 < a.n && a.img[im + 1].block_begin <= blk) ++im;
         return im;
     };
-    constexpr int NP = DX ? 6 : 3;  // planes loaded per row: x (and dy)
-    // loads this lane's 4 pixels of row `row` (block-relative) of block blk
+    constexpr int NP = DX ? 6 : 3;  // Raw words loaded per row: x (and dy)
+    // this lane's pixels at image offset off (n of them, 0 for none)
+    auto load_px = [&](const ImgDesc &d, size_t off, int n, size_t plane, Raw (&dst)[NP]) {
+        const int nc = n > 0 ? checked_run(a.check, off, n, plane) : 0;
+        if (nc > 0) {
+            const void *px = In::at(d.x, off);
+            In::load(px, plane, nc, checked_vec(a.check, d.vec, px, In::kVecAlign), dst);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dst[c] = Raw();
+        }
+        if constexpr (DX) {
+            const float *g = d.dy + off;
+            const bool v = checked_vec(a.check, d.vec, g, 16);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dst[3 + c] = nc > 0 ? PixIO<float>::load(g + c * plane, nc, v) : Raw();
+        }
+    };
+    // loads this lane's pixels of row `row` (block-relative) of block blk
     auto load_row = [&](int blk, int row, Raw (&dst)[NP]) {
         const ImgDesc &d = a.img[find_image(blk)];
         const int lb = blk - d.block_begin;
@@ -1019,22 +1067,8 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         int x;
         const int n = lane_px(d.W, strip * kTileW, x);
         const int y = d.y_begin + band * d.BH + row;
-        const size_t plane = static_cast<size_t>(d.H) * d.W;
-        const bool ok = row < d.BH && y < d.y_end && n > 0;
-        const size_t off = static_cast<size_t>(y) * d.W + x;
-        const int nc = ok ? checked_run<kStride>(a.check, off, n, plane) : 0;
-        if (nc > 0) {
-            const void *px = In::at(d.x, off);
-            In::load(px, plane, nc, kStride ? d.vec : checked_vec(a.check, d.vec, px, In::kVecAlign), dst);
-        } else {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) dst[c] = Raw();
-        }
-        if constexpr (DX) {
-            const float *g = d.dy + static_cast<size_t>(y) * d.W + x;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) dst[3 + c] = nc > 0 ? PixIO<float>::load_s(g + c * plane, nc) : Raw();
-        }
+        const bool ok = row < d.BH && y < d.y_end;
+        load_px(d, static_cast<size_t>(y) * d.W + x, ok ? n : 0, static_cast<size_t>(d.H) * d.W, dst);
     };
 
     Raw cur[NP], nxt[NP];
@@ -1043,30 +1077,36 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
     for (;;) {
         const int im = find_image(blk);
         const ImgDesc &d = a.img[im];
-        if (im != cur_im) {
-            __syncthreads();
-            build_luts(d, lcell, scratch, misc, a.scratch_floats, a.check);
-            cur_im = im;
-        }
-        if (first) {  // the first row's pixels, requested after the factor copies
-            load_row(blk, warp, cur);
-            first = false;
-        }
         const BlockGeom g = block_geom(d, blk - d.block_begin, a.nvx_max, a.nvy_max);
-        const BlockBufs b = block_bufs(scratch, g.nvx, g.nvy, d.Dsc, a.bh_max);
-        __syncthreads();  // previous block's rows done with the buffers
+        const BlockBufs b = block_bufs(scratch, g.nvx, g.nvy, d.Dsc, a.bh_max, xcol);
+        // the first row's pixels are requested after the factor copies, so
+        // that those do not queue behind them
+        auto first_row = [&]() {
+            if (first) {
+                load_row(blk, warp, cur);
+                first = false;
+            }
+        };
+        __syncthreads();  // previous block's rows done with the buffers and the cell table
+        if (im != cur_im) {
+            build_luts(d, lcell, scratch, misc, a.scratch_floats, a.check);
+            __syncthreads();
+        }
+        cur_im = im;
+        first_row();
         if (a.queue && threadIdx.x == 0) *slot = static_cast<int>(atomicAdd(a.queue, 1u));
         block_phase_a(d, g, b, misc);
         __syncthreads();
         const int next = a.queue ? *slot : blk + 1;
         const bool has_next = next < b_end;
-        block_phase_b(d, g, b);
+        block_phase_b(d, g, b, xcol);
         __syncthreads();
 
         // ---- rows of this warp ----
         const int D = d.D, Dsc = d.Dsc, Dc1 = Dsc - 1;
         const int nc3 = (D - 1) * D * 3;  // float4 per pair table
         const int D3 = D * 3;             // float4 per cell row
+        const int lut_lim = 3 * nc3 - 2;  // each cell reads 3 float4
         const float fD1 = static_cast<float>(D - 1), fD2 = static_cast<float>(D - 2);
         const float fS1 = static_cast<float>(Dc1), fS2 = static_cast<float>(Dsc - 2);
         const float bias0 = misc[kMaxK * 4 + 0], bias1 = misc[kMaxK * 4 + 1], bias2 = misc[kMaxK * 4 + 2];
@@ -1076,44 +1116,40 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
         float dxk[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int col = kStride ? lane + 32 * k : lane * 4 + k;
-            ixl[k] = b.coli[col];
-            dxk[k] = b.cold[col];
+            ixl[k] = b.coli[lane * 4 + k];
+            dxk[k] = b.cold[lane * 4 + k];
         }
+        // 4 adjacent pixels usually span at most two x-cells: 3 xy vertices
+        const bool xy_fast = ixl[3] - ixl[0] <= 1;
         const int xcs = (g.nvx - 1) * Dsc;  // float4 per channel of pxc
+        const float *xcl = b.xcol + lane;   // + (c * Dsc + j) * kTileW + k * 32
         const size_t plane = static_cast<size_t>(d.H) * d.W;
-        // offset of this lane's pixels in row 0 of the block (input, and dy for the adjoint)
+        // offset of this lane's pixels in row 0 of the block
         const size_t off0 = static_cast<size_t>(g.y0) * d.W + xbase;
-        const void *xrow = In::at(d.x, off0);
-        const float *grow = DX ? d.dy + off0 : nullptr;
+        // xc slice of channel c at intensity cell j for pixel k: value at j
+        // and slope to j + 1
+        auto xc_slice = [&](int c, int j, int k, float &v, float &sl) {
+            if (xcol) {
+                const float *f = xcl + checked_index(a.check, kChkPxc, (c * Dsc + j) * kTileW + k * 32,
+                                                     3 * Dsc * kTileW - kTileW - 31);
+                v = f[0];
+                sl = f[kTileW] - v;
+            } else {
+                const float4 q = b.pxc[checked_index(a.check, kChkPxc, c * xcs + ixl[k] * Dsc + j, 3 * xcs)];
+                v = fmaf(q.z, dxk[k], q.x);
+                sl = fmaf(q.w, dxk[k], q.y);
+            }
+        };
 #pragma unroll 1
         for (int row = warp; row < g.rows; row += kWarps) {
             // next row of this warp, possibly in the next block
-            if (row + kWarps < g.rows) {
-                const size_t ro = static_cast<size_t>(row + kWarps) * d.W;
-                const int nc = checked_run<kStride>(a.check, off0 + ro, n, plane);
-                if (nc > 0) {
-                    const void *px = In::at(xrow, ro);
-                    In::load(px, plane, nc, kStride ? d.vec : checked_vec(a.check, d.vec, px, In::kVecAlign), nxt);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) nxt[c] = Raw();
-                }
-                if constexpr (DX) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        nxt[3 + c] = nc > 0 ? PixIO<float>::load_s(grow + ro + c * plane, nc) : Raw();
-                }
-            } else if (has_next) {
-                load_row(next, warp, nxt);
-            }
+            if (row + kWarps < g.rows) load_px(d, off0 + static_cast<size_t>(row + kWarps) * d.W, n, plane, nxt);
+            else if (has_next) load_row(next, warp, nxt);
             const int y = g.y0 + row;
             warp_row_tables(g, b, Dsc, row);
             __syncwarp();
-            if (!DX && n > 0) {
-                // adjacent pixels (8-bit images) usually span at most two x-cells: 3 vertices
-                const bool xy_fast = !kStride && ixl[3] - ixl[0] <= 1;
-                float4 xa, xb, xc;
+            if (n > 0) {
+                float4 xa, xb, xc;  // xy vertices ixl[0] .. ixl[0] + 2 (fast path)
                 if (xy_fast) {
                     xa = b.rxy[ixl[0]];
                     xb = b.rxy[ixl[0] + 1];
@@ -1121,104 +1157,85 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                 }
                 float4 pv[3];
                 In::unpack(cur, pv);
-                const float4 pr = pv[0], pg = pv[1], pb = pv[2];
                 float out[3][4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    float p[3] = {get(pr, k), get(pg, k), get(pb, k)};
+                    float4 q[3][3];  // cell coefficients of the three pairs
+                    float2 ry[3];    // yc entries of the three channels
+                    float p[3] = {get(pv[0], k), get(pv[1], k), get(pv[2], k)};
                     int ic[3], jc[3];
                     float dc[3], ec[3];
+                    bool inside[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
+                        inside[c] = p[c] >= 0.f && p[c] <= 1.f;
                         p[c] = __saturatef(p[c]);
                         ic[c] = cell_of(p[c], fD1, fD2, dc[c]);
                         jc[c] = cell_of(p[c], fS1, fS2, ec[c]);
                     }
-                    float y0 = bias0, y1 = bias1, y2 = bias2;
-                    const int lut_lim = 3 * nc3 - 2;  // each cell reads 3 float4
-                    lut_pair(lcell + checked_index(a.check, kChkLut, ic[0] * D3 + ic[1] * 3, lut_lim), dc[0],
-                             dc[1], y0, y1, y2);
-                    lut_pair(lcell + checked_index(a.check, kChkLut, nc3 + ic[0] * D3 + ic[2] * 3, lut_lim), dc[0],
-                             dc[2], y0, y1, y2);
-                    lut_pair(lcell + checked_index(a.check, kChkLut, 2 * nc3 + ic[1] * D3 + ic[2] * 3, lut_lim),
-                             dc[1], dc[2], y0, y1, y2);
-                    // xy slicing: row-interpolated vertices, lerp along x
-                    const float4 r0 =
-                        xy_fast ? (ixl[k] == ixl[0] ? xa : xb) : b.rxy[checked_index(a.check, kChkRxy, ixl[k], g.nvx)];
-                    const float4 r1 = xy_fast ? (ixl[k] == ixl[0] ? xb : xc)
-                                              : b.rxy[checked_index(a.check, kChkRxy, ixl[k] + 1, g.nvx)];
-                    const float dx = dxk[k];
-                    y0 += fmaf(r1.x - r0.x, dx, r0.x);
-                    y1 += fmaf(r1.y - r0.y, dx, r0.y);
-                    y2 += fmaf(r1.z - r0.z, dx, r0.z);
-                    float yy[3] = {y0, y1, y2};
-                    // xc + yc slicing share the intensity cell of channel c
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float4 q = b.pxc[checked_index(a.check, kChkPxc, c * xcs + ixl[k] * Dsc + jc[c], 3 * xcs)];
-                        const float2 qy = b.ryc[checked_index(a.check, kChkRyc, c * Dc1 + jc[c], 3 * Dc1)];
-                        const float s0 = fmaf(q.z, dx, q.x) + qy.x;  // value at j
-                        const float sl = fmaf(q.w, dx, q.y) + qy.y;  // slope to j + 1
-                        out[c][k] = fmaf(sl, ec[c], yy[c] + s0);
-                    }
-                }
-                {
-                    const size_t off = static_cast<size_t>(y) * d.W + xbase;
-                    const int nc = checked_run<kStride>(a.check, off, n, plane);
-                    const void *py = Out::at(d.y, off);
-                    // (float lanes 32 pixels apart make no vector accesses)
-                    if (nc > 0)
-                        Out::template store<kStride>(d.y, plane, off, out, nc,
-                                                     kStride ? d.vec : checked_vec(a.check, d.vec, py, Out::kVecAlign));
-                }
-            }
-            if constexpr (DX) {
-            if (n > 0) {
-                float outd[3][4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    float xv[3] = {get(cur[0], k), get(cur[1], k), get(cur[2], k)};
-                    const float gy[3] = {get(cur[3], k), get(cur[4], k), get(cur[5], k)};
-                    float p[3], dc[3], ec[3], gp[3] = {0.f, 0.f, 0.f};
-                    int ic[3], jc[3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        p[c] = fminf(fmaxf(xv[c], 0.f), 1.f);
-                        ic[c] = cell_of(p[c], fD1, fD2, dc[c]);
-                        jc[c] = cell_of(p[c], fS1, fS2, ec[c]);
-                    }
-                    // LUT pairs (rg, rb, gb): slopes along both axes
+                    // LUT pairs (rg, rb, gb): axes (A, B)
+                    const int cid[3] = {ic[0] * D3 + ic[1] * 3, nc3 + ic[0] * D3 + ic[2] * 3,
+                                        2 * nc3 + ic[1] * D3 + ic[2] * 3};
 #pragma unroll
                     for (int pr = 0; pr < 3; ++pr) {
-                        const int A = pr == 2 ? 1 : 0, Bx = pr == 0 ? 1 : 2;
-                        const float4 *q =
-                            lcell + checked_index(a.check, kChkLut, pr * nc3 + ic[A] * D3 + ic[Bx] * 3, 3 * nc3 - 2);
-                        const float4 q0 = q[0], q1 = q[1], q2 = q[2];
-                        // b = (q0.w, q1.x, q1.y), c = (q1.z, q1.w, q2.x), d = (q2.y, q2.z, q2.w)
-                        const float da = dc[A], db = dc[Bx];
-                        const float sa = gy[0] * fmaf(q2.y, db, q0.w) + gy[1] * fmaf(q2.z, db, q1.x) +
-                                         gy[2] * fmaf(q2.w, db, q1.y);
-                        const float sb = gy[0] * fmaf(q2.y, da, q1.z) + gy[1] * fmaf(q2.z, da, q1.w) +
-                                         gy[2] * fmaf(q2.w, da, q2.x);
-                        gp[A] = fmaf(fD1, sa, gp[A]);
-                        gp[Bx] = fmaf(fD1, sb, gp[Bx]);
+                        const float4 *c4 = lcell + checked_index(a.check, kChkLut, cid[pr], lut_lim);
+                        q[pr][0] = c4[0];
+                        q[pr][1] = c4[1];
+                        q[pr][2] = c4[2];
                     }
-                    const float dx = dxk[k];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float4 q = b.pxc[checked_index(a.check, kChkPxc, c * xcs + ixl[k] * Dsc + jc[c], 3 * xcs)];
-                        const float2 qy = b.ryc[checked_index(a.check, kChkRyc, c * Dc1 + jc[c], 3 * Dc1)];
-                        const float sl = fmaf(q.w, dx, q.y) + qy.y;  // slope to j + 1
-                        gp[c] = fmaf(gy[c] * fS1, sl, gp[c]);
-                        outd[c][k] = (xv[c] >= 0.f && xv[c] <= 1.f) ? gp[c] : 0.f;
+                    for (int c = 0; c < 3; ++c) ry[c] = b.ryc[checked_index(a.check, kChkRyc, c * Dc1 + jc[c], 3 * Dc1)];
+                    if constexpr (!DX) {
+                        float y0 = bias0, y1 = bias1, y2 = bias2;
+                        lut_pair(q[0][0], q[0][1], q[0][2], dc[0], dc[1], y0, y1, y2);
+                        lut_pair(q[1][0], q[1][1], q[1][2], dc[0], dc[2], y0, y1, y2);
+                        lut_pair(q[2][0], q[2][1], q[2][2], dc[1], dc[2], y0, y1, y2);
+                        // xy slicing: row-interpolated vertices, lerp along x
+                        const float4 r0 = xy_fast ? (ixl[k] == ixl[0] ? xa : xb)
+                                                  : b.rxy[checked_index(a.check, kChkRxy, ixl[k], g.nvx)];
+                        const float4 r1 = xy_fast ? (ixl[k] == ixl[0] ? xb : xc)
+                                                  : b.rxy[checked_index(a.check, kChkRxy, ixl[k] + 1, g.nvx)];
+                        const float dx = dxk[k];
+                        const float yy[3] = {y0 + fmaf(r1.x - r0.x, dx, r0.x), y1 + fmaf(r1.y - r0.y, dx, r0.y),
+                                             y2 + fmaf(r1.z - r0.z, dx, r0.z)};
+                        // xc + yc slicing share the intensity cell of channel c
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            float v, sl;
+                            xc_slice(c, jc[c], k, v, sl);
+                            out[c][k] = fmaf(sl + ry[c].y, ec[c], yy[c] + (v + ry[c].x));
+                        }
+                        (void)inside;
+                    } else {
+                        const float gy[3] = {get(cur[3], k), get(cur[4], k), get(cur[5], k)};
+                        float gp[3] = {0.f, 0.f, 0.f};
+                        lut_pair_dx(q[0][0], q[0][1], q[0][2], dc[0], dc[1], gy, fD1, gp[0], gp[1]);
+                        lut_pair_dx(q[1][0], q[1][1], q[1][2], dc[0], dc[2], gy, fD1, gp[0], gp[2]);
+                        lut_pair_dx(q[2][0], q[2][1], q[2][2], dc[1], dc[2], gy, fD1, gp[1], gp[2]);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            float v, sl;
+                            xc_slice(c, jc[c], k, v, sl);
+                            gp[c] = fmaf(gy[c] * fS1, sl + ry[c].y, gp[c]);
+                            out[c][k] = inside[c] ? gp[c] : 0.f;
+                        }
                     }
                 }
+                const size_t off = static_cast<size_t>(y) * d.W + xbase;
+                const int nc = checked_run(a.check, off, n, plane);
+                if (nc > 0) {
+                    if constexpr (!DX) {
+                        const void *py = Out::at(d.y, off);
+                        Out::store(d.y, plane, off, out, nc, checked_vec(a.check, d.vec, py, Out::kVecAlign));
+                    } else {
+                        float *py = static_cast<float *>(d.y) + off;
+                        const bool v = checked_vec(a.check, d.vec, py, 16);
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    PixIO<float>::store_s(reinterpret_cast<float *>(d.y) + c * plane + static_cast<size_t>(y) * d.W + xbase,
-                                          make_float4(outd[c][0], outd[c][1], outd[c][2], outd[c][3]),
-                                          checked_run<true>(a.check, static_cast<size_t>(y) * d.W + xbase, n, plane));
-            }
+                        for (int c = 0; c < 3; ++c)
+                            PixIO<float>::store(py + c * plane, make_float4(out[c][0], out[c][1], out[c][2], out[c][3]),
+                                                nc, v);
+                    }
+                }
             }
             __syncwarp();  // row tables are rewritten for the next row
 #pragma unroll

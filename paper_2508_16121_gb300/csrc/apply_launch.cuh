@@ -24,6 +24,8 @@ ImgDesc make_desc_io(const svdlut_dims *d, const svdlut_params *p, int b, int H,
 
 // Shared-memory bytes of args a for block heights up to bh_max; the
 // all-nine-tables prologue is enabled when it fits.  Sets lcell/scratch sizes.
+// Shared-memory bytes of args a for block heights up to bh_max; the
+// all-nine-tables prologue is enabled when it fits.  Sets lcell/scratch sizes.
 template <int N>
 size_t apply_smem_bytes(LaunchArgs<N> &a, size_t limit)
 {
@@ -33,7 +35,7 @@ size_t apply_smem_bytes(LaunchArgs<N> &a, size_t limit)
         Dmax = std::max(Dmax, e.D);
         pro1 = std::max(pro1, prologue_floats_n(e.D, e.R, 1));
         pro3 = std::max(pro3, prologue_floats_n(e.D, e.R, 3));
-        blk = std::max(blk, block_floats(a.nvx_max, a.nvy_max, e.Dsc, a.bh_max));
+        blk = std::max(blk, block_floats(a.nvx_max, a.nvy_max, e.Dsc, a.bh_max, a.xcol != 0));
     }
     a.lcell_floats = lcell_floats(Dmax);
     auto bytes = [&](int scratch) {
@@ -60,11 +62,12 @@ svdlut_status plan_uniform(LaunchArgs<N> &a, int sm_count, size_t smem_limit, si
     int best = -1;
     double best_score = -1e30;
     const int nvx = span_bound(kTileW, W, e0.Dsx);
+    a.xcol = e0.Dsc <= kXcolMaxDsc;
     const int fixed = lcell_floats(e0.D) + kMiscFloats;
     const int pro = prologue_floats_n(e0.D, e0.R, 1);  // required; all-pairs-at-once is optional
     for (int bands = 1; bands <= max_bands; ++bands) {
         const int BH = (rows + bands - 1) / bands;
-        const int need = fixed + std::max(pro, block_floats(nvx, span_bound(BH, H, e0.Dsy), e0.Dsc, BH));
+        const int need = fixed + std::max(pro, block_floats(nvx, span_bound(BH, H, e0.Dsy), e0.Dsc, BH, a.xcol != 0));
         if (sizeof(float) * static_cast<size_t>(need) > smem_limit) continue;
         const long long T = static_cast<long long>(a.n) * strips * bands;
         const double waves = std::ceil(static_cast<double>(T) / sm_count - 1e-9);

@@ -45,6 +45,9 @@ static svdlut_status plan_ragged(LaunchArgs<kRaggedMax> &a, const svdlut_image *
     a.nvx_max = 2;
     a.nvy_max = 2;
     a.bh_max = 1;
+    a.xcol = 1;
+    for (int i = 0; i < a.n; ++i)
+        if (imgs[i0 + i].dims.Dsc > kXcolMaxDsc) a.xcol = 0;
     for (int i = 0; i < a.n; ++i) {
         const svdlut_image &im = imgs[i0 + i];
         ImgDesc e = make_desc(&im.dims, &im.params, 0, im.H, im.W, dt, im.x, im.y);
@@ -57,7 +60,7 @@ static svdlut_status plan_ragged(LaunchArgs<kRaggedMax> &a, const svdlut_image *
             const size_t need =
                 sizeof(float) * (static_cast<size_t>(lcell_floats(im.dims.D_t)) + kMiscFloats +
                                  std::max(prologue_floats_n(im.dims.D_t, im.dims.rank, 1),
-                                          block_floats(nvx, nvy, im.dims.Dsc, BH)));
+                                          block_floats(nvx, nvy, im.dims.Dsc, BH, a.xcol != 0)));
             if (need <= smem_limit) break;
             if (BH <= 1)
                 return fail(SVDLUT_ERR_UNSUPPORTED, "image %d: grid slices do not fit in shared memory", i0 + i);

@@ -231,3 +231,29 @@ def test_8k_frame_u8_and_f32(sv):
     y8 = sv.apply(torch.from_numpy(x8).cuda(), pd).cpu().numpy().astype(int)
     ref8 = oracle.quantize_u8(oracle.forward(d, p, oracle.u8_to_unit(x8))).astype(int)
     assert np.abs(y8 - ref8).max() <= 1
+
+
+@pytest.mark.parametrize("dims", ["paper", "spatial"])
+def test_on_vertex_and_upper_edge_inputs(sv, dims):
+    """Inputs exactly on LUT and slicing vertices (p = i/32, which includes
+    every i/16 of the 17-vertex intensity axis), at 0 and at the upper edge
+    p = 1 (where the cell below is taken with frac = 1, reading R5), on an
+    image whose pixel positions also fall on spatial vertices: 257 x 257, so
+    (W-1) and (H-1) are multiples of (Ds-1) for Ds = 17 and for the
+    1/8-resolution Ds = 33.  FP32 within 2e-5 of the oracle; the 8-bit codes
+    0 and 255 (p = 0 and 1) within 1 LSB."""
+    import torch
+    H = W = 257
+    d = si.paper_dims() if dims == "paper" else si.spatial_dims(H, W)
+    assert (W - 1) % (d.Dsx - 1) == 0 and (H - 1) % (d.Dsy - 1) == 0
+    rng = np.random.default_rng(31)
+    _, p = si.make_batch(32, 2, H, W, d)
+    x = (rng.integers(0, 33, size=(2, 3, H, W)) / 32.0).astype(np.float32)
+    x[0, :, :64] = 1.0          # upper edge on every axis
+    x[1, :, :64] = 0.0
+    x[1, 0, 64:128] = 1.0       # mixed: one channel at the edge
+    check_f32(sv, d, x, p)
+    x8 = np.where(rng.uniform(size=x.shape) < 0.5, 0, 255).astype(np.uint8)
+    y8 = sv.apply(torch.from_numpy(x8).cuda(), sv.to_device(p)).cpu().numpy().astype(int)
+    ref = oracle.quantize_u8(oracle.forward(d, p, oracle.u8_to_unit(x8))).astype(int)
+    assert np.abs(y8 - ref).max() <= 1
