@@ -551,6 +551,18 @@ __device__ __forceinline__ int cell_of(float p, float fDm1, float fDm2, float &f
     return __float_as_int(m) - 0x4B400000;
 }
 
+// The same cell as cell_of, returned as the bit pattern of 1.5 * 2^23 + i
+// (i = bits - kCellBias): callers fold the bias into their address
+// arithmetic (unsigned, modulo 2^32).
+constexpr unsigned int kCellBias = 0x4B400000u;
+__device__ __forceinline__ unsigned int cell_bits(float p, float fDm1, float fDm2, float &frac)
+{
+    const float t = fminf(fmaf(p, fDm1, -0.5f), fDm2);
+    const float m = t + 12582912.0f;
+    frac = fmaf(p, fDm1, -(m - 12582912.0f));
+    return static_cast<unsigned int>(__float_as_int(m));
+}
+
 // ---- LUT prologue: Eq. 9 reconstruction, Eq. 5 weight fold, cell coefficients ----
 // Factor rows are padded with zeros to Rp floats, a multiple of 4 with Rp / 4
 // odd: rows are read as float4, and the lanes of a quarter warp reading
@@ -990,6 +1002,18 @@ __device__ __forceinline__ void lut_pair_dx(const float4 &q0, const float4 &q1, 
 
 static_assert(kTileW == 128, "the xcol table and the lane mapping assume 128-pixel tiles");
 
+// Cell at byte offset off of the cell table (3 float4 per cell).
+__device__ __forceinline__ const float4 *lut_at(const float4 *lcell, unsigned int off, unsigned int *check, int lim)
+{
+#ifdef SVDLUT_CHECK_BOUNDS
+    return lcell + checked_index(check, kChkLut, static_cast<int>(off >> 4), lim);
+#else
+    (void)check;
+    (void)lim;
+    return reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(lcell) + off);
+#endif
+}
+
 // DX = false: the forward transform, y = f(x).
 // DX = true (float images): the pixel part of the adjoint, dx = (df/dx)^T dy,
 // from the slopes of the same cell coefficients (lut_pair_dx); the xc / yc
@@ -1140,84 +1164,171 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                 sl = fmaf(q.w, dxk[k], q.y);
             }
         };
-#pragma unroll 1
-        for (int row = warp; row < g.rows; row += kWarps) {
-            // next row of this warp, possibly in the next block
-            if (row + kWarps < g.rows) load_px(d, off0 + static_cast<size_t>(row + kWarps) * d.W, n, plane, nxt);
-            else if (has_next) load_row(next, warp, nxt);
-            const int y = g.y0 + row;
-            warp_row_tables(g, b, Dsc, row);
-            __syncwarp();
-            if (n > 0) {
-                float4 xa, xb, xc;  // xy vertices ixl[0] .. ixl[0] + 2 (fast path)
-                if (xy_fast) {
-                    xa = b.rxy[ixl[0]];
-                    xb = b.rxy[ixl[0] + 1];
-                    xc = b.rxy[min(ixl[0] + 2, g.nvx - 1)];
-                }
-                float4 pv[3];
-                In::unpack(cur, pv);
-                float out[3][4];
+        // Fast rows (the common case, uniform over the block): per-column xc
+        // tables, D - 1 = 2 (Dsc - 1) (the slice cell is the LUT cell halved:
+        // the 17 intensity vertices are every other LUT vertex), and x-cells
+        // at least 3 pixels wide (a lane's 4 pixels touch at most 2 of them).
+        const bool fast = xcol && D - 1 == 2 * Dc1 && d.W - 1 >= 3 * (d.Dsx - 1);
+        auto rows = [&](auto fast_tag) {
+            constexpr bool FAST = decltype(fast_tag)::value;
+            // fast rows: xy of pixel k = xa + w0[k] (xb - xa) + w1[k] (xc - xb)
+            float w0[4], w1[4];
+            if constexpr (FAST) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    float4 q[3][3];  // cell coefficients of the three pairs
-                    float2 ry[3];    // yc entries of the three channels
-                    float p[3] = {get(pv[0], k), get(pv[1], k), get(pv[2], k)};
-                    int ic[3], jc[3];
-                    float dc[3], ec[3];
-                    bool inside[3];
+                    const bool c0 = ixl[k] == ixl[0];
+                    w0[k] = c0 ? dxk[k] : 1.f;
+                    w1[k] = c0 ? 0.f : dxk[k];
+                }
+            }
+            const unsigned int rowB = static_cast<unsigned int>(D3) * 16u, pairB = static_cast<unsigned int>(nc3) * 16u;
+            const unsigned int kRow = 0u - kCellBias * rowB, kCol = 0u - kCellBias * 48u;
+#pragma unroll 1
+            for (int row = warp; row < g.rows; row += kWarps) {
+                // next row of this warp, possibly in the next block
+                if (row + kWarps < g.rows) load_px(d, off0 + static_cast<size_t>(row + kWarps) * d.W, n, plane, nxt);
+                else if (has_next) load_row(next, warp, nxt);
+                const int y = g.y0 + row;
+                warp_row_tables(g, b, Dsc, row);
+                __syncwarp();
+                float out[3][4];
+                if constexpr (FAST) {
+                    const float4 xa = b.rxy[ixl[0]], xb = b.rxy[ixl[0] + 1], xc = b.rxy[min(ixl[0] + 2, g.nvx - 1)];
+                    const float base[3] = {bias0 + xa.x, bias1 + xa.y, bias2 + xa.z};
+                    const float ab[3] = {xb.x - xa.x, xb.y - xa.y, xb.z - xa.z};
+                    const float bc[3] = {xc.x - xb.x, xc.y - xb.y, xc.z - xb.z};
+                    float4 pv[3];
+                    In::unpack(cur, pv);
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        inside[c] = p[c] >= 0.f && p[c] <= 1.f;
-                        p[c] = __saturatef(p[c]);
-                        ic[c] = cell_of(p[c], fD1, fD2, dc[c]);
-                        jc[c] = cell_of(p[c], fS1, fS2, ec[c]);
-                    }
-                    // LUT pairs (rg, rb, gb): axes (A, B)
-                    const int cid[3] = {ic[0] * D3 + ic[1] * 3, nc3 + ic[0] * D3 + ic[2] * 3,
-                                        2 * nc3 + ic[1] * D3 + ic[2] * 3};
-#pragma unroll
-                    for (int pr = 0; pr < 3; ++pr) {
-                        const float4 *c4 = lcell + checked_index(a.check, kChkLut, cid[pr], lut_lim);
-                        q[pr][0] = c4[0];
-                        q[pr][1] = c4[1];
-                        q[pr][2] = c4[2];
-                    }
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) ry[c] = b.ryc[checked_index(a.check, kChkRyc, c * Dc1 + jc[c], 3 * Dc1)];
-                    if constexpr (!DX) {
-                        float y0 = bias0, y1 = bias1, y2 = bias2;
-                        lut_pair(q[0][0], q[0][1], q[0][2], dc[0], dc[1], y0, y1, y2);
-                        lut_pair(q[1][0], q[1][1], q[1][2], dc[0], dc[2], y0, y1, y2);
-                        lut_pair(q[2][0], q[2][1], q[2][2], dc[1], dc[2], y0, y1, y2);
-                        // xy slicing: row-interpolated vertices, lerp along x
-                        const float4 r0 = xy_fast ? (ixl[k] == ixl[0] ? xa : xb)
-                                                  : b.rxy[checked_index(a.check, kChkRxy, ixl[k], g.nvx)];
-                        const float4 r1 = xy_fast ? (ixl[k] == ixl[0] ? xb : xc)
-                                                  : b.rxy[checked_index(a.check, kChkRxy, ixl[k] + 1, g.nvx)];
-                        const float dx = dxk[k];
-                        const float yy[3] = {y0 + fmaf(r1.x - r0.x, dx, r0.x), y1 + fmaf(r1.y - r0.y, dx, r0.y),
-                                             y2 + fmaf(r1.z - r0.z, dx, r0.z)};
-                        // xc + yc slicing share the intensity cell of channel c
+                    for (int k = 0; k < 4; ++k) {
+                        float p[3] = {get(pv[0], k), get(pv[1], k), get(pv[2], k)};
+                        unsigned int cb[3];
+                        float dc[3];
+                        bool inside[3];
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            float v, sl;
-                            xc_slice(c, jc[c], k, v, sl);
-                            out[c][k] = fmaf(sl + ry[c].y, ec[c], yy[c] + (v + ry[c].x));
+                            inside[c] = p[c] >= 0.f && p[c] <= 1.f;
+                            cb[c] = cell_bits(__saturatef(p[c]), fD1, fD2, dc[c]);
                         }
-                        (void)inside;
-                    } else {
-                        const float gy[3] = {get(cur[3], k), get(cur[4], k), get(cur[5], k)};
-                        float gp[3] = {0.f, 0.f, 0.f};
-                        lut_pair_dx(q[0][0], q[0][1], q[0][2], dc[0], dc[1], gy, fD1, gp[0], gp[1]);
-                        lut_pair_dx(q[1][0], q[1][1], q[1][2], dc[0], dc[2], gy, fD1, gp[0], gp[2]);
-                        lut_pair_dx(q[2][0], q[2][1], q[2][2], dc[1], dc[2], gy, fD1, gp[1], gp[2]);
+                        // LUT cells of the pairs rg, rb, gb: row offset of the first
+                        // channel of the pair plus column offset of the second
+                        const unsigned int Rr = cb[0] * rowB + kRow, Rg = cb[1] * rowB + kRow;
+                        const unsigned int Cg = cb[1] * 48u + kCol, Cb = cb[2] * 48u + kCol;
+                        const float4 *q0 = lut_at(lcell, Rr + Cg, a.check, lut_lim);
+                        const float4 *q1 = lut_at(lcell, pairB + Rr + Cb, a.check, lut_lim);
+                        const float4 *q2 = lut_at(lcell, 2u * pairB + Rg + Cb, a.check, lut_lim);
+                        float yy[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) yy[c] = fmaf(w0[k], ab[c], fmaf(w1[k], bc[c], base[c]));
+                        // slice cell: the LUT cell halved, e = (i mod 2 + frac) / 2
+                        int jc[3];
+                        float ec[3];
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            float v, sl;
-                            xc_slice(c, jc[c], k, v, sl);
-                            gp[c] = fmaf(gy[c] * fS1, sl + ry[c].y, gp[c]);
-                            out[c][k] = inside[c] ? gp[c] : 0.f;
+                            jc[c] = static_cast<int>((cb[c] - kCellBias) >> 1);
+                            ec[c] = fmaf(dc[c], 0.5f, (cb[c] & 1u) ? 0.5f : 0.f);
+                        }
+                        if constexpr (!DX) {
+                            lut_pair(q0[0], q0[1], q0[2], dc[0], dc[1], yy[0], yy[1], yy[2]);
+                            lut_pair(q1[0], q1[1], q1[2], dc[0], dc[2], yy[0], yy[1], yy[2]);
+                            lut_pair(q2[0], q2[1], q2[2], dc[1], dc[2], yy[0], yy[1], yy[2]);
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                const float *f = xcl + checked_index(a.check, kChkPxc, (c * Dsc + jc[c]) * kTileW + k * 32,
+                                                                     3 * Dsc * kTileW - kTileW - 31);
+                                const float2 r = b.ryc[checked_index(a.check, kChkRyc, c * Dc1 + jc[c], 3 * Dc1)];
+                                const float v = f[0];
+                                out[c][k] = fmaf((f[kTileW] - v) + r.y, ec[c], yy[c] + (v + r.x));
+                            }
+                            (void)inside;
+                        } else {
+                            const float gy[3] = {get(cur[3], k), get(cur[4], k), get(cur[5], k)};
+                            float gp[3] = {0.f, 0.f, 0.f};
+                            lut_pair_dx(q0[0], q0[1], q0[2], dc[0], dc[1], gy, fD1, gp[0], gp[1]);
+                            lut_pair_dx(q1[0], q1[1], q1[2], dc[0], dc[2], gy, fD1, gp[0], gp[2]);
+                            lut_pair_dx(q2[0], q2[1], q2[2], dc[1], dc[2], gy, fD1, gp[1], gp[2]);
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                const float *f = xcl + checked_index(a.check, kChkPxc, (c * Dsc + jc[c]) * kTileW + k * 32,
+                                                                     3 * Dsc * kTileW - kTileW - 31);
+                                const float2 r = b.ryc[checked_index(a.check, kChkRyc, c * Dc1 + jc[c], 3 * Dc1)];
+                                gp[c] = fmaf(gy[c] * fS1, (f[kTileW] - f[0]) + r.y, gp[c]);
+                                out[c][k] = inside[c] ? gp[c] : 0.f;
+                            }
+                            (void)yy;
+                            (void)ec;
+                        }
+                    }
+                } else {
+                    float4 xa, xb, xc;  // xy vertices ixl[0] .. ixl[0] + 2 (fast path)
+                    if (xy_fast) {
+                        xa = b.rxy[ixl[0]];
+                        xb = b.rxy[ixl[0] + 1];
+                        xc = b.rxy[min(ixl[0] + 2, g.nvx - 1)];
+                    }
+                    float4 pv[3];
+                    In::unpack(cur, pv);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float4 q[3][3];  // cell coefficients of the three pairs
+                        float2 ry[3];    // yc entries of the three channels
+                        float p[3] = {get(pv[0], k), get(pv[1], k), get(pv[2], k)};
+                        int ic[3], jc[3];
+                        float dc[3], ec[3];
+                        bool inside[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            inside[c] = p[c] >= 0.f && p[c] <= 1.f;
+                            p[c] = __saturatef(p[c]);
+                            ic[c] = cell_of(p[c], fD1, fD2, dc[c]);
+                            jc[c] = cell_of(p[c], fS1, fS2, ec[c]);
+                        }
+                        // LUT pairs (rg, rb, gb): axes (A, B)
+                        const int cid[3] = {ic[0] * D3 + ic[1] * 3, nc3 + ic[0] * D3 + ic[2] * 3,
+                                            2 * nc3 + ic[1] * D3 + ic[2] * 3};
+#pragma unroll
+                        for (int pr = 0; pr < 3; ++pr) {
+                            const float4 *c4 = lcell + checked_index(a.check, kChkLut, cid[pr], lut_lim);
+                            q[pr][0] = c4[0];
+                            q[pr][1] = c4[1];
+                            q[pr][2] = c4[2];
+                        }
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) ry[c] = b.ryc[checked_index(a.check, kChkRyc, c * Dc1 + jc[c], 3 * Dc1)];
+                        if constexpr (!DX) {
+                            float y0 = bias0, y1 = bias1, y2 = bias2;
+                            lut_pair(q[0][0], q[0][1], q[0][2], dc[0], dc[1], y0, y1, y2);
+                            lut_pair(q[1][0], q[1][1], q[1][2], dc[0], dc[2], y0, y1, y2);
+                            lut_pair(q[2][0], q[2][1], q[2][2], dc[1], dc[2], y0, y1, y2);
+                            // xy slicing: row-interpolated vertices, lerp along x
+                            const float4 r0 = xy_fast ? (ixl[k] == ixl[0] ? xa : xb)
+                                                      : b.rxy[checked_index(a.check, kChkRxy, ixl[k], g.nvx)];
+                            const float4 r1 = xy_fast ? (ixl[k] == ixl[0] ? xb : xc)
+                                                      : b.rxy[checked_index(a.check, kChkRxy, ixl[k] + 1, g.nvx)];
+                            const float dx = dxk[k];
+                            const float yy[3] = {y0 + fmaf(r1.x - r0.x, dx, r0.x), y1 + fmaf(r1.y - r0.y, dx, r0.y),
+                                                 y2 + fmaf(r1.z - r0.z, dx, r0.z)};
+                            // xc + yc slicing share the intensity cell of channel c
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                float v, sl;
+                                xc_slice(c, jc[c], k, v, sl);
+                                out[c][k] = fmaf(sl + ry[c].y, ec[c], yy[c] + (v + ry[c].x));
+                            }
+                            (void)inside;
+                        } else {
+                            const float gy[3] = {get(cur[3], k), get(cur[4], k), get(cur[5], k)};
+                            float gp[3] = {0.f, 0.f, 0.f};
+                            lut_pair_dx(q[0][0], q[0][1], q[0][2], dc[0], dc[1], gy, fD1, gp[0], gp[1]);
+                            lut_pair_dx(q[1][0], q[1][1], q[1][2], dc[0], dc[2], gy, fD1, gp[0], gp[2]);
+                            lut_pair_dx(q[2][0], q[2][1], q[2][2], dc[1], dc[2], gy, fD1, gp[1], gp[2]);
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                float v, sl;
+                                xc_slice(c, jc[c], k, v, sl);
+                                gp[c] = fmaf(gy[c] * fS1, sl + ry[c].y, gp[c]);
+                                out[c][k] = inside[c] ? gp[c] : 0.f;
+                            }
                         }
                     }
                 }
@@ -1236,11 +1347,13 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
                                                 nc, v);
                     }
                 }
-            }
-            __syncwarp();  // row tables are rewritten for the next row
+                __syncwarp();  // row tables are rewritten for the next row
 #pragma unroll
-            for (int c = 0; c < NP; ++c) cur[c] = nxt[c];
-        }
+                for (int c = 0; c < NP; ++c) cur[c] = nxt[c];
+            }
+        };
+        if (fast) rows(std::true_type{});
+        else rows(std::false_type{});
         if (warp >= g.rows && has_next) load_row(next, warp, cur);  // no row here
         if (!has_next) break;
         blk = next;
