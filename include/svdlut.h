@@ -165,6 +165,33 @@ svdlut_status svdlut_apply_cfg(const svdlut_dims *dims, const svdlut_params *par
                                svdlut_stream_t stream);
 
 /*
+ * svdlut_apply_ws -- svdlut_apply (with cfg as in svdlut_apply_cfg) whose
+ * per-image tables are computed once per call into a caller workspace instead
+ * of by every CTA: one small kernel rebuilds each image's nine 2D LUTs from
+ * their factors (Eq. 9) times the pair weights (Eq. 5) in the per-cell
+ * coefficient form of the bilinear interpolation (Supp. Eq. 15), folds the
+ * grid slices per output channel (Supp. Eqs. 21-22) and sums the biases; the
+ * transform kernel, launched as its programmatic dependent, copies its part
+ * of those tables into shared memory.  The result is bit-identical to
+ * svdlut_apply.
+ * ws: device memory of at least svdlut_apply_workspace_size(dims, B) bytes,
+ * 256-byte aligned, not overlapping x or y; its contents on entry do not
+ * matter and are overwritten; concurrent calls must use different workspaces.
+ * cfg may be NULL.
+ * Errors: those of svdlut_apply_cfg; WORKSPACE (NULL or too small);
+ * INVALID_ARG (misaligned or overlapping workspace).
+ */
+svdlut_status svdlut_apply_ws(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
+                              svdlut_dtype dtype, const void *x, void *y, const svdlut_launch_cfg *cfg, void *ws,
+                              size_t ws_bytes, svdlut_stream_t stream);
+
+/* Workspace bytes of svdlut_apply_ws for B images of these dims (0 if the
+ * dims are invalid or B < 1): per image 4 * 3 * (D_t-1) * D_t * 12 bytes of
+ * cell table plus 4 * (3 * (Dsy*Dsx + Dsx*Dsc + Dsy*Dsc) + 3) bytes of folded
+ * grids and biases, each rounded up to 256 bytes. */
+size_t svdlut_apply_workspace_size(const svdlut_dims *dims, int B);
+
+/*
  * svdlut_apply_batched -- the fused transform of svdlut_apply (Eq. 10) over n
  * images of uneven sizes, each with its own transform, in one persistent
  * launch per 64 images.  imgs is a HOST array of n descriptors (read during the

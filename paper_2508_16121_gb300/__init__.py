@@ -69,12 +69,16 @@ def _stream_ptr(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def apply(x, params, out=None, stream=None, ctas=None):
+def apply(x, params, out=None, stream=None, ctas=None, workspace=True):
     """Fused SVDLUT apply (Eq. 10).  x: CUDA tensor [B,3,H,W] or [3,H,W],
     float32 or uint8, contiguous.  params: dict of float32 CUDA tensors with
     an optional leading batch axis (see include/svdlut.h).  Returns y with
-    x's shape and dtype.  ctas: persistent CTAs to use (svdlut_apply_cfg;
-    default one per SM)."""
+    x's shape and dtype.  ctas: persistent CTAs to use (default one per SM).
+    workspace: True (default) runs svdlut_apply_ws, whose per-image tables
+    are precomputed once into a workspace taken from PyTorch's allocator on
+    the call's stream; a uint8 CUDA tensor of svdlut_apply_workspace_size
+    bytes is used as given; False runs svdlut_apply / svdlut_apply_cfg
+    (every CTA rebuilds the tables itself)."""
     torch = _torch()
     squeeze = x.dim() == 3
     xb = x.unsqueeze(0) if squeeze else x
@@ -95,7 +99,20 @@ def apply(x, params, out=None, stream=None, ctas=None):
     if y.shape != xb.shape or y.dtype != xb.dtype or not y.is_contiguous():
         raise ValueError("out must match x in shape and dtype")
     lib = _lib.load()
-    if ctas is None:
+    if workspace is not False:
+        need = lib.svdlut_apply_workspace_size(ctypes.byref(d), B)
+        if workspace is True:
+            ws = _stream_workspace(torch, need, xb.device, stream)
+        else:
+            ws = workspace
+            if not ws.is_cuda or ws.dtype != torch.uint8 or ws.numel() < need:
+                raise ValueError(f"workspace must be a uint8 CUDA tensor of at least {need} bytes")
+        cfg = _lib.LaunchCfg(0, int(ctas or 0), 0)
+        _lib.check(lib.svdlut_apply_ws(ctypes.byref(d), ctypes.byref(p), B, H, W, dt,
+                                       ctypes.c_void_p(xb.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                       ctypes.byref(cfg), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                       _stream_ptr(stream)))
+    elif ctas is None:
         _lib.check(lib.svdlut_apply(ctypes.byref(d), ctypes.byref(p), B, H, W, dt,
                                     ctypes.c_void_p(xb.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                     _stream_ptr(stream)))
@@ -105,6 +122,15 @@ def apply(x, params, out=None, stream=None, ctas=None):
                                         ctypes.c_void_p(xb.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                         ctypes.byref(cfg), _stream_ptr(stream)))
     return y[0] if squeeze else y
+
+
+def _stream_workspace(torch, nbytes, device, stream):
+    """Device scratch of nbytes from PyTorch's caching allocator, owned by the
+    stream the call runs on (so concurrent streams never share it)."""
+    if stream is None:
+        return torch.empty(nbytes, dtype=torch.uint8, device=device)
+    with torch.cuda.stream(stream):
+        return torch.empty(nbytes, dtype=torch.uint8, device=device)
 
 
 # pixel formats of apply_io (svdlut_pixfmt): code, element dtypes, interleaved?

@@ -57,6 +57,10 @@ struct ImgDesc {
     int block_begin;  // first global block index of this image
     float rW1, rH1;   // 1/(W-1), 1/(H-1); 0 when W or H is 1
     int vec;         // whole-lane vector loads and stores allowed (W % 4 == 0, aligned images)
+    // precomputed per image by prep_kernel (workspace path), else null:
+    float *pcell;  // the cell table, laid out as in shared memory (lcell_floats(D) floats)
+    float *pfold;  // grid slices folded per output channel: xy [3][Dsy][Dsx], xc [3][Dsx][Dsc],
+                   // yc [3][Dsy][Dsc], then the three summed biases
 };
 
 template <int N>
@@ -67,6 +71,7 @@ struct LaunchArgs {
     int lcell_floats;    // floats reserved for the cell table
     int scratch_floats;  // floats of the block buffers / prologue temporaries
     int xcol;            // nonzero: per-column xc tables (every image's Dsc <= kXcolMaxDsc)
+    int pre;             // nonzero: cell tables and folded grids precomputed (ImgDesc::pcell, pfold)
     unsigned int *queue;  // non-null: blocks are taken from this counter (must be 0 at launch)
     unsigned int *check;  // index-check status (builds with SVDLUT_CHECK_BOUNDS), else null
     ImgDesc img[N];
@@ -825,7 +830,8 @@ __device__ __forceinline__ BlockBufs block_bufs(float *scratch, int nvx, int nvy
 // Block setup, phase A: grid slices of the block footprint folded per output
 // channel (sum over grids k = c mod 3 of w_k times grid k: Supp. Eqs. 21-22);
 // column and row cell tables.
-__device__ inline void block_phase_a(const ImgDesc &d, const BlockGeom &g, const BlockBufs &b, const float *misc)
+__device__ inline void block_phase_a(const ImgDesc &d, const BlockGeom &g, const BlockBufs &b, const float *misc,
+                                     bool fold = true)
 {
     const int tid = threadIdx.x;
     const int nvx = g.nvx, nvy = g.nvy, Dsc = d.Dsc, K = d.K;
@@ -836,7 +842,9 @@ __device__ inline void block_phase_a(const ImgDesc &d, const BlockGeom &g, const
     // thread takes kFoldBatch elements at a time and issues all their loads
     // before the first FMA, so the slices cost a few memory round trips.
     const int nxy = 3 * nvy * nvx, nxc = 3 * nvx * Dsc, nyc = 3 * nvy * Dsc, ntot = nxy + nxc + nyc;
-    if (K > 0) {
+    if (!fold) {
+        // the folded slices were copied from the precomputed ones (setup_pre)
+    } else if (K > 0) {
         // element e -> its first grid value's address and its channel c (by
         // comparison: one division per element)
         auto locate = [&](int e, int &c, size_t &kst) -> const float * {
@@ -914,6 +922,231 @@ __device__ inline void block_phase_a(const ImgDesc &d, const BlockGeom &g, const
         spatial_cell(g.y0 + row, d.H, d.Dsy, d.rH1, iy, dy);
         b.rowi[row] = max(0, min(iy - g.iylo, nvy - 2));
         b.rowd[row] = dy;
+    }
+}
+
+// ---- precomputed per-image tables (workspace path) ----
+// Floats of the folded grid slices of one image, and the offset of its three
+// summed biases after them.
+__host__ __device__ inline size_t pfold_floats(int Dsx, int Dsy, int Dsc)
+{
+    return 3 * (static_cast<size_t>(Dsy) * Dsx + static_cast<size_t>(Dsx) * Dsc + static_cast<size_t>(Dsy) * Dsc);
+}
+
+// q = floor(n / m) for 0 <= n < 2^20, m >= 1, with rm = 1.0f / m: n + 0.5 is
+// at least 0.5 away from a multiple of m, far more than the float error.
+__device__ __forceinline__ int quot(int n, float rm) { return static_cast<int>((static_cast<float>(n) + 0.5f) * rm); }
+
+// Block setup from the precomputed tables: on an image switch the cell table
+// (16-byte asynchronous copies) and the summed biases; for every block the
+// folded slices of its footprint (4-byte asynchronous copies).  The caller
+// waits for the copies.
+__device__ inline void setup_pre(const ImgDesc &d, const BlockGeom &g, const BlockBufs &b, float4 *lcell,
+                                 float *misc, bool rebuild)
+{
+    const int tid = threadIdx.x;
+    const int nvx = g.nvx, nvy = g.nvy, Dsc = d.Dsc, Dsx = d.Dsx, Dsy = d.Dsy;
+    const float *pxy = d.pfold, *pxc = pxy + 3 * static_cast<size_t>(Dsy) * Dsx,
+                *pyc = pxc + 3 * static_cast<size_t>(Dsx) * Dsc;
+    if (rebuild) {
+        const float4 *src = reinterpret_cast<const float4 *>(d.pcell);
+        const int n4 = lcell_floats(d.D) / 4;
+        for (int e = tid; e < n4; e += kThreads) cp_async16(lcell + e, src + e);
+        if (tid < 3) misc[kMaxK * 4 + tid] = __ldg(d.pfold + pfold_floats(Dsx, Dsy, Dsc) + tid);
+    }
+    const int nxy = nvy * nvx, nxc = nvx * Dsc, nyc = nvy * Dsc, oxy = 3 * nxy, oxc = 3 * nxc;
+    const int ntot = oxy + oxc + 3 * nyc;
+    const float rnvx = 1.0f / static_cast<float>(nvx);
+    for (int o = tid; o < ntot; o += kThreads) {
+        const float *src;
+        if (o < oxy) {
+            const int c = o >= nxy ? (o >= 2 * nxy ? 2 : 1) : 0, f = o - c * nxy, r = quot(f, rnvx);
+            src = pxy + (static_cast<size_t>(c) * Dsy + g.iylo + r) * Dsx + g.ixlo + (f - r * nvx);
+        } else if (o < oxy + oxc) {
+            const int f0 = o - oxy, c = f0 >= nxc ? (f0 >= 2 * nxc ? 2 : 1) : 0;
+            src = pxc + (static_cast<size_t>(c) * Dsx + g.ixlo) * Dsc + (f0 - c * nxc);
+        } else {
+            const int f0 = o - oxy - oxc, c = f0 >= nyc ? (f0 >= 2 * nyc ? 2 : 1) : 0;
+            src = pyc + (static_cast<size_t>(c) * Dsy + g.iylo) * Dsc + (f0 - c * nyc);
+        }
+        cp_async4(b.fxy + o, src);  // fxy, fxc, fyc are consecutive
+    }
+}
+
+// Per-image precomputation for the workspace path, one launch per chunk of
+// images: the first CTAs build the cell table of each (image, pair) -- T = (U S) w
+// V^T of the pair's three channel tables (Eq. 9, Eq. 5 weight) and the
+// coefficient form of Supp. Eq. 15, in the same arithmetic order as
+// build_luts, so both paths give identical tables; the other CTAs fold the
+// grid slices per output channel (Supp. Eqs. 21-22; same order as
+// block_phase_a) and sum the biases.  Lets the dependent apply kernel launch
+// as soon as it starts.
+constexpr int kPrepThreads = 512;
+template <int N>
+struct PrepArgs {
+    int n;
+    ImgDesc img[N];
+};
+
+__host__ __device__ inline int prep_smem_floats(int D, int R) { return 2 * 3 * D * padded_rank(R) + 3 * D * D; }
+
+
+// CTAs [0, kLutCtas * n) build the cell rows [i0, i1) of (image, pair,
+// part): T rows i0 .. i1 of the pair's three channel tables, then the cells.
+constexpr int kLutParts = 4, kLutCtas = 3 * kLutParts;
+
+template <int N>
+__global__ void __launch_bounds__(kPrepThreads) prep_kernel(const __grid_constant__ PrepArgs<N> a)
+{
+    // launched as a programmatic dependent of the preceding kernel: wait for
+    // its results (e.g. generator outputs) before reading anything
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" :::);
+    extern __shared__ __align__(16) float ps[];
+    const int tid = threadIdx.x;
+    if (static_cast<int>(blockIdx.x) < kLutCtas * a.n) {
+        const ImgDesc &d = a.img[blockIdx.x / kLutCtas];
+        const int rem = blockIdx.x % kLutCtas, p = rem / kLutParts, part = rem - p * kLutParts;
+        const int D = d.D, R = d.R, Rp = padded_rank(R), R4 = (R + 3) / 4, DR = D * R, DRp = D * Rp, Dm1 = D - 1;
+        const int i0 = (Dm1 * part) / kLutParts, i1 = (Dm1 * (part + 1)) / kLutParts;  // cell rows
+        const int nrow = i1 - i0 + 1;                                                    // T rows i0 .. i1
+        if (i1 <= i0) return;
+        float *sU = ps, *sV = ps + 3 * DRp, *sT = ps + 6 * DRp;  // [3 c][D][Rp] x 2, [3 c][nrow][D]
+        // factor rows (U scaled by S and the pair weight, as build_luts): U
+        // rows i0 .. i1 and all V rows; the loads of kBatch elements are
+        // issued before any of their stores
+        constexpr int kBatch = 4;
+        const int nu = 3 * nrow * Rp, nv = 3 * DRp;
+        for (int e0 = tid; e0 < nu + nv; e0 += kBatch * kPrepThreads) {
+            float val[kBatch];
+            int dst[kBatch];
+#pragma unroll
+            for (int q = 0; q < kBatch; ++q) {
+                const int e = e0 + q * kPrepThreads;
+                dst[q] = -1;
+                val[q] = 0.f;
+                if (e < nu) {
+                    const int row = e / Rp, r = e - row * Rp, c = row / nrow, i = i0 + row - c * nrow, cp = c * 3 + p;
+                    dst[q] = c * DRp + i * Rp + r;
+                    if (r < R)
+                        val[q] = __ldg(d.U + cp * DR + i * R + r) * __ldg(d.S + cp * R + r) * __ldg(d.lw + c * 4 + p);
+                } else if (e < nu + nv) {
+                    const int f = e - nu, row = f / Rp, r = f - row * Rp, c = row / D, i = row - c * D;
+                    dst[q] = 3 * DRp + f;
+                    if (r < R) val[q] = __ldg(d.V + (c * 3 + p) * DR + i * R + r);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kBatch; ++q)
+                if (dst[q] >= 0) ps[dst[q]] = val[q];
+        }
+        __syncthreads();
+        for (int e = tid; e < 3 * nrow * D; e += kPrepThreads) {
+            const int row = e / D, j = e - row * D, c = row / nrow, i = i0 + row - c * nrow;
+            const float4 *u = reinterpret_cast<const float4 *>(sU + c * DRp + i * Rp);
+            const float4 *v = reinterpret_cast<const float4 *>(sV + c * DRp + j * Rp);
+            float acc = 0.f;
+            for (int q = 0; q < R4; ++q) {
+                const float4 x = u[q], y = v[q];
+                acc = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, acc))));
+            }
+            sT[e] = acc;
+        }
+        __syncthreads();
+        float4 *out = reinterpret_cast<float4 *>(d.pcell) + static_cast<size_t>(p) * Dm1 * D * 3;
+        for (int e = tid; e < (i1 - i0) * Dm1; e += kPrepThreads) {
+            const int ii = e / Dm1, j = e - ii * Dm1, i = i0 + ii;
+            float v00[3], bb[3], cc[3], dd[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float *t = sT + (c * nrow + ii) * D + j;
+                const float t00 = t[0], t01 = t[1], t10 = t[D], t11 = t[D + 1];
+                v00[c] = t00;
+                bb[c] = t10 - t00;
+                cc[c] = t01 - t00;
+                dd[c] = t11 - t10 - t01 + t00;
+            }
+            float4 *q = out + (i * D + j) * 3;
+            q[0] = make_float4(v00[0], v00[1], v00[2], bb[0]);
+            q[1] = make_float4(bb[1], bb[2], cc[0], cc[1]);
+            q[2] = make_float4(cc[2], dd[0], dd[1], dd[2]);
+        }
+        return;
+    }
+    // folded grid slices and summed biases of all images (grid-stride; the
+    // loads of kBatch outputs are issued before their sums)
+    const ImgDesc &d0 = a.img[0];  // same dims for every image of the chunk
+    const int K = d0.K, Dsx = d0.Dsx, Dsy = d0.Dsy, Dsc = d0.Dsc;
+    const int nxy = Dsy * Dsx, nxc = Dsx * Dsc, nyc = Dsy * Dsc;
+    const int per = 3 * (nxy + nxc + nyc) + 3, total = per * a.n;
+    const int stride = (static_cast<int>(gridDim.x) - kLutCtas * a.n) * kPrepThreads;
+    constexpr int kBatch = 4, kTerms = 3;
+    for (int t0 = (static_cast<int>(blockIdx.x) - kLutCtas * a.n) * kPrepThreads + tid; t0 < total;
+         t0 += kBatch * stride) {
+        float g[kBatch][kTerms], w[kBatch][kTerms];
+        int which[kBatch], ch[kBatch], im[kBatch], o[kBatch], e[kBatch];
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) {
+            const int t = t0 + q * stride;
+            im[q] = t < total ? t / per : 0;
+            o[q] = t - im[q] * per;
+            const ImgDesc &d = a.img[im[q]];
+            const float *gsrc = nullptr;
+            int kst = 0;
+            if (t >= total || o[q] >= per - 3) {
+                which[q] = 3;  // bias (or nothing)
+                ch[q] = t < total ? o[q] - (per - 3) : 0;
+                e[q] = 0;
+            } else if (o[q] < 3 * nxy) {
+                which[q] = 0;
+                ch[q] = o[q] >= nxy ? (o[q] >= 2 * nxy ? 2 : 1) : 0;
+                e[q] = o[q] - ch[q] * nxy;
+                gsrc = d.gxy;
+                kst = nxy;
+            } else if (o[q] < 3 * (nxy + nxc)) {
+                which[q] = 1;
+                const int f = o[q] - 3 * nxy;
+                ch[q] = f >= nxc ? (f >= 2 * nxc ? 2 : 1) : 0;
+                e[q] = f - ch[q] * nxc;
+                gsrc = d.gxc;
+                kst = nxc;
+            } else {
+                which[q] = 2;
+                const int f = o[q] - 3 * (nxy + nxc);
+                ch[q] = f >= nyc ? (f >= 2 * nyc ? 2 : 1) : 0;
+                e[q] = f - ch[q] * nyc;
+                gsrc = d.gyc;
+                kst = nyc;
+            }
+#pragma unroll
+            for (int m = 0; m < kTerms; ++m) {
+                const int k = ch[q] + 3 * m;
+                const bool ok = which[q] < 3 && k < K;
+                g[q][m] = ok ? __ldg(gsrc + static_cast<size_t>(k) * kst + e[q]) : 0.f;
+                w[q][m] = ok ? __ldg(d.gw + k * 4 + which[q]) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) {
+            const int t = t0 + q * stride;
+            if (t >= total) continue;
+            const ImgDesc &d = a.img[im[q]];
+            float acc;
+            if (which[q] == 3) {  // summed bias of channel c: b^c + the grid biases feeding c
+                acc = __ldg(d.lw + ch[q] * 4 + 3);
+                for (int k = ch[q]; k < K; k += 3) acc += __ldg(d.gw + k * 4 + 3);
+            } else {
+                acc = 0.f;
+#pragma unroll
+                for (int m = 0; m < kTerms; ++m)
+                    if (ch[q] + 3 * m < K) acc = fmaf(w[q][m], g[q][m], acc);
+                const float *gsrc = which[q] == 0 ? d.gxy : (which[q] == 1 ? d.gxc : d.gyc);
+                const int kst = which[q] == 0 ? nxy : (which[q] == 1 ? nxc : nyc);
+                for (int k = ch[q] + 3 * kTerms; k < K; k += 3)
+                    acc = fmaf(__ldg(d.gw + k * 4 + which[q]), __ldg(gsrc + static_cast<size_t>(k) * kst + e[q]), acc);
+            }
+            d.pfold[o[q]] = acc;
+        }
     }
 }
 
@@ -1032,6 +1265,9 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
     float *misc = smem + a.lcell_floats;
     float *scratch = misc + kMiscFloats;
 
+    // the next kernel of the stream (e.g. the next call's prep_kernel, which
+    // waits for this one before reading anything) may begin launching
+    asm volatile("griddepcontrol.launch_dependents;\n" :::);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool xcol = a.xcol != 0;
     // Block schedule: a contiguous range per CTA, or (queue) blocks taken in
@@ -1097,7 +1333,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
 
     Raw cur[NP], nxt[NP];
     int cur_im = -1;
-    bool first = true;
+    bool first = true, pre_wait = a.pre != 0;
     for (;;) {
         const int im = find_image(blk);
         const ImgDesc &d = a.img[im];
@@ -1112,14 +1348,26 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(const __grid_constan
             }
         };
         __syncthreads();  // previous block's rows done with the buffers and the cell table
-        if (im != cur_im) {
+        if (a.pre) {
+            // The pixels are inputs of the call, complete before the launch:
+            // the first row is requested while the precomputation may still
+            // run (programmatic dependent launch); the tables after it ends.
+            first_row();
+            if (pre_wait) {
+                asm volatile("griddepcontrol.wait;\n" ::: "memory");
+                pre_wait = false;
+            }
+            setup_pre(d, g, b, lcell, misc, im != cur_im);
+            cp_async_wait_all();
+            __syncthreads();
+        } else if (im != cur_im) {
             build_luts(d, lcell, scratch, misc, a.scratch_floats, a.check);
             __syncthreads();
         }
         cur_im = im;
         first_row();
         if (a.queue && threadIdx.x == 0) *slot = static_cast<int>(atomicAdd(a.queue, 1u));
-        block_phase_a(d, g, b, misc);
+        block_phase_a(d, g, b, misc, !a.pre);
         __syncthreads();
         const int next = a.queue ? *slot : blk + 1;
         const bool has_next = next < b_end;

@@ -122,9 +122,38 @@ svdlut_status launch_apply_t(LaunchArgs<N> &a, size_t smem, int sm_count, int ma
     if ((st = check_buffer(&a.check)) != SVDLUT_OK) return st;
     if (grid <= 0) grid = std::min(a.total_blocks, sm_count);
     grid = std::max(1, std::min(grid, a.total_blocks));
+    if (a.pre) {
+        // dependent of the preceding prep_kernel: it may start while that
+        // kernel runs and waits for it before reading the tables
+        return launch_pdl(apply_kernel<IO, N, DX>, dim3(grid), dim3(kThreads), smem, s, a);
+    }
     apply_kernel<IO, N, DX><<<grid, kThreads, smem, s>>>(a);
     SVDLUT_CUDA_TRY(cudaGetLastError());
     return SVDLUT_OK;
+}
+
+// Workspace bytes of the precomputed tables of one image, and the launch of
+// prep_kernel over a chunk of planned images (pcell / pfold set).
+inline size_t prep_image_bytes(const svdlut_dims *d)
+{
+    auto a256 = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
+    return a256(sizeof(float) * static_cast<size_t>(lcell_floats(d->D_t))) +
+           a256(sizeof(float) * (pfold_floats(d->Dsx, d->Dsy, d->Dsc) + 3));
+}
+
+template <int N>
+svdlut_status launch_prep(const LaunchArgs<N> &a, int sm_count, cudaStream_t s)
+{
+    const ImgDesc &e0 = a.img[0];
+    if (static_cast<double>(pfold_floats(e0.Dsx, e0.Dsy, e0.Dsc) + 3) * a.n >= 2147483647.0)
+        return fail(SVDLUT_ERR_UNSUPPORTED, "grids of %d images too large for the workspace path", a.n);
+    PrepArgs<N> pa{};
+    pa.n = a.n;
+    for (int i = 0; i < a.n; ++i) pa.img[i] = a.img[i];
+    const int fold_ctas = std::max(sm_count, 2 * sm_count - kLutCtas * a.n);
+    const size_t smem = sizeof(float) * static_cast<size_t>(prep_smem_floats(a.img[0].D, a.img[0].R));
+    // programmatic dependent of the preceding kernel (it waits for it first)
+    return launch_pdl(prep_kernel<N>, dim3(kLutCtas * a.n + fold_ctas), dim3(kPrepThreads), smem, s, pa);
 }
 
 // Launches apply_kernel for args whose blocks are already planned.  dx_mode

@@ -78,14 +78,15 @@ ImgDesc make_desc(const svdlut_dims *d, const svdlut_params *p, int b, int H, in
 using namespace svdlut;
 
 static svdlut_status apply_impl(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
-                                svdlut_dtype dtype, const void *x, void *y, int ctas, svdlut_stream_t stream);
+                                svdlut_dtype dtype, const void *x, void *y, int ctas, void *ws, size_t ws_bytes,
+                                svdlut_stream_t stream);
 
 extern "C" svdlut_status svdlut_apply(const svdlut_dims *dims, const svdlut_params *params, int B, int H,
                                       int W, svdlut_dtype dtype, const void *x, void *y,
                                       svdlut_stream_t stream)
 {
     SVDLUT_TRACE("svdlut_apply");
-    return apply_impl(dims, params, B, H, W, dtype, x, y, 0, stream);
+    return apply_impl(dims, params, B, H, W, dtype, x, y, 0, nullptr, 0, stream);
 }
 
 extern "C" svdlut_status svdlut_apply_cfg(const svdlut_dims *dims, const svdlut_params *params, int B, int H,
@@ -95,11 +96,29 @@ extern "C" svdlut_status svdlut_apply_cfg(const svdlut_dims *dims, const svdlut_
     SVDLUT_TRACE("svdlut_apply_cfg");
     clear_error();
     if (cfg && cfg->ctas < 0) return fail(SVDLUT_ERR_INVALID_ARG, "negative CTA count");
-    return apply_impl(dims, params, B, H, W, dtype, x, y, cfg ? cfg->ctas : 0, stream);
+    return apply_impl(dims, params, B, H, W, dtype, x, y, cfg ? cfg->ctas : 0, nullptr, 0, stream);
+}
+
+extern "C" size_t svdlut_apply_workspace_size(const svdlut_dims *dims, int B)
+{
+    if (B < 1 || check_dims(dims) != SVDLUT_OK) return 0;
+    return static_cast<size_t>(B) * prep_image_bytes(dims);
+}
+
+extern "C" svdlut_status svdlut_apply_ws(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
+                                         svdlut_dtype dtype, const void *x, void *y, const svdlut_launch_cfg *cfg,
+                                         void *ws, size_t ws_bytes, svdlut_stream_t stream)
+{
+    SVDLUT_TRACE("svdlut_apply_ws");
+    clear_error();
+    if (cfg && cfg->ctas < 0) return fail(SVDLUT_ERR_INVALID_ARG, "negative CTA count");
+    if (!ws) return fail(SVDLUT_ERR_WORKSPACE, "workspace is NULL");
+    return apply_impl(dims, params, B, H, W, dtype, x, y, cfg ? cfg->ctas : 0, ws, ws_bytes, stream);
 }
 
 static svdlut_status apply_impl(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
-                                svdlut_dtype dtype, const void *x, void *y, int ctas, svdlut_stream_t stream)
+                                svdlut_dtype dtype, const void *x, void *y, int ctas, void *ws, size_t ws_bytes,
+                                svdlut_stream_t stream)
 {
     clear_error();
     svdlut_status st = check_dims(dims);
@@ -115,18 +134,41 @@ static svdlut_status apply_impl(const svdlut_dims *dims, const svdlut_params *pa
     const char *xs = static_cast<const char *>(x), *ys = static_cast<const char *>(y);
     if (xs < ys + bytes && ys < xs + bytes) return fail(SVDLUT_ERR_INVALID_ARG, "x and y overlap");
 
+    const size_t per_img = prep_image_bytes(dims);
+    if (ws) {
+        if (ws_bytes < static_cast<size_t>(B) * per_img)
+            return fail(SVDLUT_ERR_WORKSPACE, "workspace of %zu bytes needed (got %zu)",
+                        static_cast<size_t>(B) * per_img, ws_bytes);
+        if (!aligned(ws, 256)) return fail(SVDLUT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+        char *ws_c = static_cast<char *>(ws);
+        if ((ws_c < ys + bytes && ys < ws_c + B * per_img) || (ws_c < xs + bytes && xs < ws_c + B * per_img))
+            return fail(SVDLUT_ERR_INVALID_ARG, "workspace overlaps x or y");
+    }
+
     DeviceInfo di;
     if ((st = device_info(&di)) != SVDLUT_OK) return st;
     const int n_cta = ctas > 0 ? std::min(ctas, di.sm_count) : di.sm_count;  // persistent CTAs to plan for
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     for (int b0 = 0; b0 < B; b0 += kPlainChunk) {
         LaunchArgs<kPlainChunk> a{};
         a.n = std::min(kPlainChunk, B - b0);
-        for (int i = 0; i < a.n; ++i) a.img[i] = make_desc(dims, params, b0 + i, H, W, dtype, x, y);
+        for (int i = 0; i < a.n; ++i) {
+            a.img[i] = make_desc(dims, params, b0 + i, H, W, dtype, x, y);
+            if (ws) {
+                char *w = static_cast<char *>(ws) + static_cast<size_t>(b0 + i) * per_img;
+                a.img[i].pcell = reinterpret_cast<float *>(w);
+                a.img[i].pfold = reinterpret_cast<float *>(
+                    w + ((sizeof(float) * static_cast<size_t>(lcell_floats(dims->D_t)) + 255) & ~static_cast<size_t>(255)));
+            }
+        }
         size_t smem = 0;
         if ((st = plan_uniform(a, n_cta, static_cast<size_t>(di.max_smem_optin), &smem)) != SVDLUT_OK)
             return st;
-        if ((st = launch_apply(a, smem, dtype, reinterpret_cast<cudaStream_t>(stream), n_cta)) != SVDLUT_OK)
-            return st;
+        if (ws) {
+            if ((st = launch_prep(a, di.sm_count, s)) != SVDLUT_OK) return st;
+            a.pre = 1;
+        }
+        if ((st = launch_apply(a, smem, dtype, s, n_cta)) != SVDLUT_OK) return st;
     }
     return SVDLUT_OK;
 }

@@ -257,3 +257,56 @@ def test_on_vertex_and_upper_edge_inputs(sv, dims):
     y8 = sv.apply(torch.from_numpy(x8).cuda(), sv.to_device(p)).cpu().numpy().astype(int)
     ref = oracle.quantize_u8(oracle.forward(d, p, oracle.u8_to_unit(x8))).astype(int)
     assert np.abs(y8 - ref).max() <= 1
+
+
+@pytest.mark.parametrize("d,B,H,W", [(si.spatial_dims(130, 515), 2, 130, 515), (si.paper_dims(), 3, 67, 257),
+                                     (si.Dims(33, 33, 48, 9, 7, 64), 1, 70, 260), (si.Dims(2, 1, 0, 2, 2, 2), 2, 5, 9),
+                                     (si.Dims(17, 8, 8, 9, 5, 33), 1, 300, 515)])
+def test_workspace_path_equals_plain_path(sv, d, B, H, W):
+    """svdlut_apply_ws (tables precomputed once per image into a workspace)
+    against svdlut_apply (tables rebuilt in every CTA): identical bits, in
+    FP32 and u8, and within 2e-5 of the oracle."""
+    import torch
+    x, p = si.make_batch(600 + H, B, H, W, d)
+    xt, pd = torch.from_numpy(x).cuda(), sv.to_device(p)
+    y_ws = sv.apply(xt, pd, workspace=True)
+    y_plain = sv.apply(xt, pd, workspace=False)
+    torch.cuda.synchronize()
+    assert torch.equal(y_ws, y_plain)
+    assert np.abs(y_ws.cpu().numpy().astype(np.float64) - oracle.forward(d, p, x)).max() <= TOL
+    x8 = torch.from_numpy(si.to_u8(x)).cuda()
+    assert torch.equal(sv.apply(x8, pd, workspace=True), sv.apply(x8, pd, workspace=False))
+    # an explicit workspace (stale contents do not matter) and the CTA cap
+    from paper_2508_16121_gb300 import _lib
+    need = _lib.load().svdlut_apply_workspace_size(ctypes_dims(sv, pd), B)
+    ws = torch.full((need,), 0xAB, dtype=torch.uint8, device="cuda")
+    assert torch.equal(sv.apply(xt, pd, workspace=ws, ctas=37), y_plain)
+
+
+def ctypes_dims(sv, pd):
+    import ctypes
+    return ctypes.byref(sv.dims_of(pd))
+
+
+def test_workspace_errors(sv):
+    import ctypes
+    import torch
+    from paper_2508_16121_gb300 import _lib
+    lib = _lib.load()
+    d = si.spatial_dims(64, 128)
+    x, p = si.make_batch(7, 1, 64, 128, d)
+    xt, pd = torch.from_numpy(x).cuda(), sv.to_device(p)
+    dims = sv.dims_of(pd)
+    need = lib.svdlut_apply_workspace_size(ctypes.byref(dims), 1)
+    assert need > 0 and lib.svdlut_apply_workspace_size(ctypes.byref(dims), 0) == 0
+    with pytest.raises(ValueError):
+        sv.apply(xt, pd, workspace=torch.empty(need - 1, dtype=torch.uint8, device="cuda"))
+    ps = sv._param_struct(pd, 1, dims)
+    y = torch.empty_like(xt)
+    buf = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    args = (ctypes.byref(dims), ctypes.byref(ps), 1, 64, 128, _lib.F32, ctypes.c_void_p(xt.data_ptr()),
+            ctypes.c_void_p(y.data_ptr()), None)
+    assert lib.svdlut_apply_ws(*args, None, need, None) == _lib.ERR_WORKSPACE
+    assert lib.svdlut_apply_ws(*args, ctypes.c_void_p(buf.data_ptr()), need - 1, None) == _lib.ERR_WORKSPACE
+    assert lib.svdlut_apply_ws(*args, ctypes.c_void_p(buf.data_ptr() + 4), need, None) == _lib.ERR_INVALID_ARG
+    torch.cuda.synchronize()
