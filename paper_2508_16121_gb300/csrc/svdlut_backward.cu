@@ -130,19 +130,25 @@ struct BwdArgs {
 // ---------------------------------------------------------------------------
 // LUT gradients: G^c_p[i][j] = sum_px dy_c * bilinear weight of vertex (i, j)
 // at (x_alpha, x_beta) for pair p = (alpha, beta).
-// grid (P, B); CTA p owns rows [p H / P, (p+1) H / P) of image blockIdx.y.
-// Warp (group g, pair q) scatters the pixels of group g into its table
-// [D][D][3 channels] for pair q.
+// grid (P, B); CTA (p, b) owns the rows [p H / P, (p+1) H / P) of image b.
+// Warp (group g, pair q) takes the 128-column strips g, g + 4, ... and walks
+// down the CTA's rows of each; lane l takes columns l + 32 k (k = 0..3:
+// coalesced loads) and keeps, per column, the four corner contributions
+// (three channels each) of its current cell in registers: while the cell
+// does not change (smooth regions, where consecutive rows fall in the same
+// cell) it only accumulates; when it changes, the warp scatters the finished
+// sums into its private table [D][D][3 channels + 1 pad] (deterministic
+// warp_scatter).  Rows are loaded two ahead.
 // Output: lut_part[b][p][c][pair][D*D], sums_part[b][p][c] (sum of dy_c).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kLutThreads, 1)
-    lut_grad_kernel(BwdArgs a, int P, float *__restrict__ lut_part, float *__restrict__ sums_part)
+    lut_grad_kernel(BwdArgs a, float *__restrict__ lut_part, float *__restrict__ sums_part)
 {
     extern __shared__ __align__(16) float sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = warp / 3, pair = warp - grp * 3;
     const int A = pair == 2 ? 1 : 0, Bx = pair == 0 ? 1 : 2;  // axes of the pair
-    const int b = blockIdx.y, p = blockIdx.x;
+    const int P = gridDim.x, p = blockIdx.x, b = blockIdx.y;
     const int D = a.D, DD = D * D;
     float *tab = sm + warp * 4 * DD;  // [D][D][3 channels + 1 pad] of this warp's pair
     float *sums = sm + kLutWarps * 4 * DD;
@@ -151,43 +157,78 @@ __global__ void __launch_bounds__(kLutThreads, 1)
 
     const int r0 = static_cast<int>((static_cast<long long>(a.H) * p) / P);
     const int r1 = static_cast<int>((static_cast<long long>(a.H) * (p + 1)) / P);
+    constexpr int kGroups = kLutWarps / 3;
     const size_t plane = static_cast<size_t>(a.H) * a.W;
     const float *xb = a.x + static_cast<size_t>(b) * 3 * plane;
     const float *gb = a.dy + static_cast<size_t>(b) * 3 * plane;
     const float fD1 = static_cast<float>(D - 1), fD2 = static_cast<float>(D - 2);
-    const int units = (r1 - r0) * a.strips;
     float dysum[3] = {0.f, 0.f, 0.f};
-    for (int u = grp; u < units; u += kLutWarps / 3) {
-        const int row = r0 + u / a.strips, strip = u - (u / a.strips) * a.strips;
-        // pixel k of the lane: column x + 32 k (a warp-wide access covers 32
-        // adjacent pixels, whose cells often coincide: fewer scatter groups)
+    float acc[4][4][3];  // [column k][corner][channel]
+    int acc_key[4] = {-1, -1, -1, -1};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[k][q][c] = 0.f;
+    for (int strip = grp; strip < a.strips; strip += kGroups) {
         const int x = strip * kTileW + lane;
-        const int n = x < a.W ? min(4, (a.W - x + 31) >> 5) : 0;
-        const size_t o = static_cast<size_t>(row) * a.W + x;
-        float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa, g0 = pa, g1 = pa, g2 = pa;
-        if (n > 0) {
-            pa = PixIO<float>::load_s(xb + A * plane + o, n);
-            pb = PixIO<float>::load_s(xb + Bx * plane + o, n);
-            g0 = PixIO<float>::load_s(gb + o, n);
-            g1 = PixIO<float>::load_s(gb + plane + o, n);
-            g2 = PixIO<float>::load_s(gb + 2 * plane + o, n);
+        const int n = x < a.W ? min(4, (a.W - x + 31) >> 5) : 0;  // this lane's columns x + 32 k, k < n
+        struct Row {
+            float4 pa, pb, g0, g1, g2;
+        };
+        auto load = [&](int r, Row &o) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            o.pa = o.pb = o.g0 = o.g1 = o.g2 = z;
+            if (r < r1 && n > 0) {
+                const size_t off = static_cast<size_t>(r) * a.W + x;
+                o.pa = PixIO<float>::load_s(xb + A * plane + off, n);
+                o.pb = PixIO<float>::load_s(xb + Bx * plane + off, n);
+                o.g0 = PixIO<float>::load_s(gb + off, n);
+                o.g1 = PixIO<float>::load_s(gb + plane + off, n);
+                o.g2 = PixIO<float>::load_s(gb + 2 * plane + off, n);
+            }
+        };
+        Row cur, nx1, nx2;
+        load(r0, cur);
+        load(r0 + 1, nx1);
+        for (int r = r0; r < r1; ++r) {
+            load(r + 2, nx2);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const bool act = k < n;
+                const float gy[3] = {get(cur.g0, k), get(cur.g1, k), get(cur.g2, k)};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) dysum[c] += gy[c];
+                float da, db;
+                const int ia = cell_of(fminf(fmaxf(get(cur.pa, k), 0.f), 1.f), fD1, fD2, da);
+                const int ib = cell_of(fminf(fmaxf(get(cur.pb, k), 0.f), 1.f), fD1, fD2, db);
+                const float w[4] = {(1.f - da) * (1.f - db), da * (1.f - db), (1.f - da) * db, da * db};
+                const int key = act ? (ia * D + ib) * 4 : -1;
+                const bool change = key != acc_key[k];
+                if (__any_sync(0xffffffffu, change))
+                    warp_scatter<3, true>(tab, change ? acc_key[k] : -1, D * 4, 4, acc[k]);
+                if (change) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) acc[k][q][c] = gy[c] * w[q];
+                    acc_key[k] = key;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) acc[k][q][c] = fmaf(gy[c], w[q], acc[k][q][c]);
+                }
+            }
+            cur = nx1;
+            nx1 = nx2;
         }
+        // the strip's runs end here
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const bool act = k < n;
-            const float gy[3] = {act ? get(g0, k) : 0.f, act ? get(g1, k) : 0.f, act ? get(g2, k) : 0.f};
-#pragma unroll
-            for (int c = 0; c < 3; ++c) dysum[c] += gy[c];
-            float da, db;
-            const int ia = cell_of(fminf(fmaxf(get(pa, k), 0.f), 1.f), fD1, fD2, da);
-            const int ib = cell_of(fminf(fmaxf(get(pb, k), 0.f), 1.f), fD1, fD2, db);
-            const float w[4] = {(1.f - da) * (1.f - db), da * (1.f - db), (1.f - da) * db, da * db};
-            float v[4][3];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) v[q][c] = gy[c] * w[q];
-            warp_scatter<3, true>(tab, act ? (ia * D + ib) * 4 : -1, D * 4, 4, v);
+            warp_scatter<3, true>(tab, acc_key[k], D * 4, 4, acc[k]);
+            acc_key[k] = -1;
         }
     }
     // sum of dy_c: the pair-0 warps' totals (every pair warp of a group sees the same pixels)
@@ -199,17 +240,17 @@ __global__ void __launch_bounds__(kLutThreads, 1)
         sums[grp * 3 + 2] = dysum[2];
     }
     __syncthreads();
-    // CTA partial [c][pair][cell]: sum the 4 groups in order
+    // CTA partial [c][pair][cell]: sum the groups in order
     float *out = lut_part + (static_cast<size_t>(b) * P + p) * 9 * DD;
     for (int e = threadIdx.x; e < 9 * DD; e += kLutThreads) {
         const int c = e / (3 * DD), r = e - c * 3 * DD, q = r / DD, cell = r - q * DD;
         float s = 0.f;
-        for (int gq = 0; gq < kLutWarps / 3; ++gq) s += sm[(gq * 3 + q) * 4 * DD + cell * 4 + c];
+        for (int gq = 0; gq < kGroups; ++gq) s += sm[(gq * 3 + q) * 4 * DD + cell * 4 + c];
         out[e] = s;
     }
     if (threadIdx.x < 3) {
         float s = 0.f;
-        for (int gq = 0; gq < kLutWarps / 3; ++gq) s += sums[gq * 3 + threadIdx.x];
+        for (int gq = 0; gq < kGroups; ++gq) s += sums[gq * 3 + threadIdx.x];
         sums_part[(static_cast<size_t>(b) * P + p) * 3 + threadIdx.x] = s;
     }
 }
@@ -666,7 +707,9 @@ struct BwdPlan {
     size_t lut_smem;   // bytes
     GridPlan gp;
     size_t grid_smem;  // bytes
-    size_t off_lut, off_sums, off_grid, off_dF, total;  // workspace layout (bytes)
+    // workspace layout (bytes); the last part holds the per-image tables of
+    // the dx pass (prep_kernel)
+    size_t off_lut, off_sums, off_grid, off_dF, off_prep, prep_img, total;
 };
 
 static size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
@@ -741,6 +784,9 @@ static svdlut_status plan_backward(const svdlut_dims *d, int B, int H, int W, in
     pl->off_dF = off;
     off = align256(off + sizeof(float) * static_cast<size_t>(B) *
                              (3 * d->Dsy * d->Dsx + 3 * d->Dsx * Dsc + 3 * d->Dsy * Dsc));
+    pl->off_prep = off;
+    pl->prep_img = prep_image_bytes(d);
+    off += static_cast<size_t>(B) * pl->prep_img;
     pl->total = off;
     return SVDLUT_OK;
 }
@@ -795,7 +841,20 @@ extern "C" svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_p
     if ((st = device_info(&di)) != SVDLUT_OK) return st;
     const size_t smem_limit = static_cast<size_t>(di.max_smem_optin);
 
-    // 1. dx through the forward kernel's adjoint mode
+    const svdlut_grads g0{};
+    const svdlut_grads &g = grads ? *grads : g0;
+    const bool want_lut = g.dU || g.dS || g.dV || g.dlut_w;
+    const bool want_grid = dims->K > 0 && (g.dg_xy || g.dg_xc || g.dg_yc || g.dgrid_w);
+    BwdPlan pl;
+    if ((st = plan_backward(dims, B, H, W, di.sm_count, smem_limit, &pl)) != SVDLUT_OK) return st;
+    const bool have_ws = ws && ws_bytes >= pl.total;
+    if ((want_lut || want_grid) && !have_ws)
+        return fail(SVDLUT_ERR_WORKSPACE, "workspace of %zu bytes needed (got %zu)", pl.total, ws ? ws_bytes : 0);
+    if (have_ws && !aligned(ws, 256)) return fail(SVDLUT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+
+    // 1. dx through the forward kernel's adjoint mode; with a workspace, the
+    // per-image tables are precomputed once (prep_kernel) instead of in
+    // every CTA
     if (dx) {
         for (int b0 = 0; b0 < B; b0 += kPlainChunk) {
             LaunchArgs<kPlainChunk> a{};
@@ -804,23 +863,24 @@ extern "C" svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_p
                 a.img[i] = make_desc(dims, params, b0 + i, H, W, SVDLUT_F32, x, dx);
                 a.img[i].dy = dy + static_cast<size_t>(b0 + i) * 3 * H * W;
                 a.img[i].vec = a.img[i].vec && aligned(a.img[i].dy, 16);
+                if (have_ws) {
+                    char *wp = static_cast<char *>(ws) + pl.off_prep + static_cast<size_t>(b0 + i) * pl.prep_img;
+                    a.img[i].pcell = reinterpret_cast<float *>(wp);
+                    a.img[i].pfold = reinterpret_cast<float *>(
+                        wp + ((sizeof(float) * static_cast<size_t>(lcell_floats(dims->D_t)) + 255) &
+                              ~static_cast<size_t>(255)));
+                }
             }
             size_t smem = 0;
             if ((st = plan_uniform(a, di.sm_count, smem_limit, &smem)) != SVDLUT_OK) return st;
+            if (have_ws) {
+                if ((st = launch_prep(a, di.sm_count, s)) != SVDLUT_OK) return st;
+                a.pre = 1;
+            }
             if ((st = launch_apply(a, smem, SVDLUT_F32, s, 0, true)) != SVDLUT_OK) return st;
         }
     }
-    const svdlut_grads g0{};
-    const svdlut_grads &g = grads ? *grads : g0;
-    const bool want_lut = g.dU || g.dS || g.dV || g.dlut_w;
-    const bool want_grid = dims->K > 0 && (g.dg_xy || g.dg_xc || g.dg_yc || g.dgrid_w);
     if (!want_lut && !want_grid) return SVDLUT_OK;
-
-    BwdPlan pl;
-    if ((st = plan_backward(dims, B, H, W, di.sm_count, smem_limit, &pl)) != SVDLUT_OK) return st;
-    if (!ws || ws_bytes < pl.total)
-        return fail(SVDLUT_ERR_WORKSPACE, "workspace of %zu bytes needed (got %zu)", pl.total, ws ? ws_bytes : 0);
-    if (!aligned(ws, 256)) return fail(SVDLUT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     char *w = static_cast<char *>(ws);
     float *lut_part = reinterpret_cast<float *>(w + pl.off_lut);
     float *sums_part = reinterpret_cast<float *>(w + pl.off_sums);
@@ -855,7 +915,7 @@ extern "C" svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_p
     if (pl.grid_smem + 256 > static_cast<size_t>(di.max_smem_optin) || pl.lut_smem > static_cast<size_t>(di.max_smem_optin))
         return fail(SVDLUT_ERR_UNSUPPORTED, "adjoint tables do not fit in shared memory");
     // 2. LUT pass (also produces the dy channel sums used by every bias)
-    lut_grad_kernel<<<dim3(pl.P, B), kLutThreads, pl.lut_smem, s>>>(a, pl.P, lut_part, sums_part);
+    lut_grad_kernel<<<dim3(pl.P, B), kLutThreads, pl.lut_smem, s>>>(a, lut_part, sums_part);
     SVDLUT_CUDA_TRY(cudaGetLastError());
     if (want_lut) {
         FinArgs f{params->U, params->S, params->V, params->lut_w, g.dU, g.dS, g.dV, g.dlut_w,
