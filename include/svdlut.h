@@ -207,8 +207,17 @@ svdlut_status svdlut_apply_batched(const svdlut_image *imgs, int n, svdlut_dtype
                                    const svdlut_launch_cfg *cfg, void *ws, size_t ws_bytes,
                                    svdlut_stream_t stream);
 
-/* Workspace bytes for a batch of n images (0 if n < 1). */
+/* Workspace bytes for a batch of n images (0 if n < 1): the block-queue
+ * counters.  With this minimum every CTA rebuilds the tables of each image it
+ * meets. */
 size_t svdlut_batched_workspace_size(int n);
+
+/* Workspace bytes for these n images with their per-image tables (the LUT
+ * cell tables and folded grids of svdlut_apply_ws, computed once per call by
+ * one small kernel and copied into each CTA); 0 on bad arguments.  A
+ * workspace of at least this size, 256-byte aligned, makes
+ * svdlut_apply_batched use them (same results, bit for bit). */
+size_t svdlut_batched_tables_workspace_size(const svdlut_image *imgs, int n);
 
 /*
  * svdlut_autotune_batched -- times svdlut_apply_batched on this batch for a

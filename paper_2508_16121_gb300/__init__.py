@@ -433,7 +433,9 @@ class Batch:
     host descriptor array and the device workspace so that repeated calls
     (and CUDA-graph capture of a call) marshal nothing new."""
 
-    def __init__(self, xs, params_list, outs=None):
+    def __init__(self, xs, params_list, outs=None, tables=True):
+        """tables: give svdlut_apply_batched the workspace for the per-image
+        tables (computed once per call instead of in every CTA)."""
         torch = _torch()
         if len(xs) != len(params_list) or not xs:
             raise ValueError("need one parameter dict per image")
@@ -452,8 +454,9 @@ class Batch:
             self.imgs[i] = _lib.Image(x.shape[1], x.shape[2], d, _param_struct(p, 1, d),
                                       ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()))
         lib = _lib.load()
-        self.ws = torch.zeros(max(int(lib.svdlut_batched_workspace_size(n)), 4), dtype=torch.uint8,
-                              device=xs[0].device)
+        need = lib.svdlut_batched_tables_workspace_size(self.imgs, n) if tables else \
+            lib.svdlut_batched_workspace_size(n)
+        self.ws = torch.zeros(max(int(need), 4), dtype=torch.uint8, device=xs[0].device)
         self.cfg = None
 
     def run(self, stream=None):

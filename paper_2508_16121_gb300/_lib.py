@@ -88,6 +88,8 @@ def _declare(lib):
     lib.svdlut_apply_batched.restype = c_int
     lib.svdlut_batched_workspace_size.argtypes = [c_int]
     lib.svdlut_batched_workspace_size.restype = c_size_t
+    lib.svdlut_batched_tables_workspace_size.argtypes = [P(Image), c_int]
+    lib.svdlut_batched_tables_workspace_size.restype = c_size_t
     lib.svdlut_autotune_batched.argtypes = [P(Image), c_int, c_int, c_void_p, c_size_t, c_void_p, c_int,
                                             P(LaunchCfg), ctypes.POINTER(ctypes.c_float)]
     lib.svdlut_autotune_batched.restype = c_int

@@ -985,6 +985,7 @@ constexpr int kPrepThreads = 512;
 template <int N>
 struct PrepArgs {
     int n;
+    int start[N + 1];  // first fold output of each image in the flat index (host prefix sums)
     ImgDesc img[N];
 };
 
@@ -1074,11 +1075,9 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const __grid_constan
         return;
     }
     // folded grid slices and summed biases of all images (grid-stride; the
-    // loads of kBatch outputs are issued before their sums)
-    const ImgDesc &d0 = a.img[0];  // same dims for every image of the chunk
-    const int K = d0.K, Dsx = d0.Dsx, Dsy = d0.Dsy, Dsc = d0.Dsc;
-    const int nxy = Dsy * Dsx, nxc = Dsx * Dsc, nyc = Dsy * Dsc;
-    const int per = 3 * (nxy + nxc + nyc) + 3, total = per * a.n;
+    // loads of kBatch outputs are issued before their sums); image i owns the
+    // flat outputs [start[i], start[i + 1])
+    const int total = a.start[a.n];
     const int stride = (static_cast<int>(gridDim.x) - kLutCtas * a.n) * kPrepThreads;
     constexpr int kBatch = 4, kTerms = 3;
     for (int t0 = (static_cast<int>(blockIdx.x) - kLutCtas * a.n) * kPrepThreads + tid; t0 < total;
@@ -1088,9 +1087,14 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const __grid_constan
 #pragma unroll
         for (int q = 0; q < kBatch; ++q) {
             const int t = t0 + q * stride;
-            im[q] = t < total ? t / per : 0;
-            o[q] = t - im[q] * per;
-            const ImgDesc &d = a.img[im[q]];
+            int i = 0;
+            if (t < total)
+                while (t >= a.start[i + 1]) ++i;
+            im[q] = i;
+            o[q] = t - a.start[i];
+            const ImgDesc &d = a.img[i];
+            const int nxy = d.Dsy * d.Dsx, nxc = d.Dsx * d.Dsc, nyc = d.Dsy * d.Dsc;
+            const int per = 3 * (nxy + nxc + nyc) + 3;
             const float *gsrc = nullptr;
             int kst = 0;
             if (t >= total || o[q] >= per - 3) {
@@ -1121,7 +1125,7 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const __grid_constan
 #pragma unroll
             for (int m = 0; m < kTerms; ++m) {
                 const int k = ch[q] + 3 * m;
-                const bool ok = which[q] < 3 && k < K;
+                const bool ok = which[q] < 3 && k < d.K;
                 g[q][m] = ok ? __ldg(gsrc + static_cast<size_t>(k) * kst + e[q]) : 0.f;
                 w[q][m] = ok ? __ldg(d.gw + k * 4 + which[q]) : 0.f;
             }
@@ -1131,6 +1135,7 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const __grid_constan
             const int t = t0 + q * stride;
             if (t >= total) continue;
             const ImgDesc &d = a.img[im[q]];
+            const int K = d.K;
             float acc;
             if (which[q] == 3) {  // summed bias of channel c: b^c + the grid biases feeding c
                 acc = __ldg(d.lw + ch[q] * 4 + 3);
@@ -1140,6 +1145,7 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const __grid_constan
 #pragma unroll
                 for (int m = 0; m < kTerms; ++m)
                     if (ch[q] + 3 * m < K) acc = fmaf(w[q][m], g[q][m], acc);
+                const int nxy = d.Dsy * d.Dsx, nxc = d.Dsx * d.Dsc, nyc = d.Dsy * d.Dsc;
                 const float *gsrc = which[q] == 0 ? d.gxy : (which[q] == 1 ? d.gxc : d.gyc);
                 const int kst = which[q] == 0 ? nxy : (which[q] == 1 ? nxc : nyc);
                 for (int k = ch[q] + 3 * kTerms; k < K; k += 3)

@@ -141,17 +141,33 @@ inline size_t prep_image_bytes(const svdlut_dims *d)
            a256(sizeof(float) * (pfold_floats(d->Dsx, d->Dsy, d->Dsc) + 3));
 }
 
+// Points the descriptor's precomputed tables at w (prep_image_bytes(d) bytes).
+inline void set_prep_tables(ImgDesc &e, const svdlut_dims *d, char *w)
+{
+    e.pcell = reinterpret_cast<float *>(w);
+    e.pfold = reinterpret_cast<float *>(
+        w + ((sizeof(float) * static_cast<size_t>(lcell_floats(d->D_t)) + 255) & ~static_cast<size_t>(255)));
+}
+
 template <int N>
 svdlut_status launch_prep(const LaunchArgs<N> &a, int sm_count, cudaStream_t s)
 {
-    const ImgDesc &e0 = a.img[0];
-    if (static_cast<double>(pfold_floats(e0.Dsx, e0.Dsy, e0.Dsc) + 3) * a.n >= 2147483647.0)
-        return fail(SVDLUT_ERR_UNSUPPORTED, "grids of %d images too large for the workspace path", a.n);
     PrepArgs<N> pa{};
     pa.n = a.n;
-    for (int i = 0; i < a.n; ++i) pa.img[i] = a.img[i];
+    double total = 0;
+    int smem_fl = 0;
+    for (int i = 0; i < a.n; ++i) {
+        const ImgDesc &e = a.img[i];
+        pa.img[i] = e;
+        pa.start[i] = static_cast<int>(total);
+        total += static_cast<double>(pfold_floats(e.Dsx, e.Dsy, e.Dsc) + 3);
+        if (total >= 2147483647.0)
+            return fail(SVDLUT_ERR_UNSUPPORTED, "grids of %d images too large for the workspace path", a.n);
+        smem_fl = std::max(smem_fl, prep_smem_floats(e.D, e.R));
+    }
+    pa.start[a.n] = static_cast<int>(total);
     const int fold_ctas = std::max(sm_count, 2 * sm_count - kLutCtas * a.n);
-    const size_t smem = sizeof(float) * static_cast<size_t>(prep_smem_floats(a.img[0].D, a.img[0].R));
+    const size_t smem = sizeof(float) * static_cast<size_t>(smem_fl);
     // programmatic dependent of the preceding kernel (it waits for it first)
     return launch_pdl(prep_kernel<N>, dim3(kLutCtas * a.n + fold_ctas), dim3(kPrepThreads), smem, s, pa);
 }

@@ -154,12 +154,7 @@ static svdlut_status apply_impl(const svdlut_dims *dims, const svdlut_params *pa
         a.n = std::min(kPlainChunk, B - b0);
         for (int i = 0; i < a.n; ++i) {
             a.img[i] = make_desc(dims, params, b0 + i, H, W, dtype, x, y);
-            if (ws) {
-                char *w = static_cast<char *>(ws) + static_cast<size_t>(b0 + i) * per_img;
-                a.img[i].pcell = reinterpret_cast<float *>(w);
-                a.img[i].pfold = reinterpret_cast<float *>(
-                    w + ((sizeof(float) * static_cast<size_t>(lcell_floats(dims->D_t)) + 255) & ~static_cast<size_t>(255)));
-            }
+            if (ws) set_prep_tables(a.img[i], dims, static_cast<char *>(ws) + static_cast<size_t>(b0 + i) * per_img);
         }
         size_t smem = 0;
         if ((st = plan_uniform(a, n_cta, static_cast<size_t>(di.max_smem_optin), &smem)) != SVDLUT_OK)

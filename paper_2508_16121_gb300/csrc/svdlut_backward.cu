@@ -863,13 +863,9 @@ extern "C" svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_p
                 a.img[i] = make_desc(dims, params, b0 + i, H, W, SVDLUT_F32, x, dx);
                 a.img[i].dy = dy + static_cast<size_t>(b0 + i) * 3 * H * W;
                 a.img[i].vec = a.img[i].vec && aligned(a.img[i].dy, 16);
-                if (have_ws) {
-                    char *wp = static_cast<char *>(ws) + pl.off_prep + static_cast<size_t>(b0 + i) * pl.prep_img;
-                    a.img[i].pcell = reinterpret_cast<float *>(wp);
-                    a.img[i].pfold = reinterpret_cast<float *>(
-                        wp + ((sizeof(float) * static_cast<size_t>(lcell_floats(dims->D_t)) + 255) &
-                              ~static_cast<size_t>(255)));
-                }
+                if (have_ws)
+                    set_prep_tables(a.img[i], dims,
+                                    static_cast<char *>(ws) + pl.off_prep + static_cast<size_t>(b0 + i) * pl.prep_img);
             }
             size_t smem = 0;
             if ((st = plan_uniform(a, di.sm_count, smem_limit, &smem)) != SVDLUT_OK) return st;

@@ -90,6 +90,20 @@ static int auto_block_px(const svdlut_image *imgs, int n, int sm_count)
     return static_cast<int>(std::min(1024.0 * kTileW, std::max(16.0 * kTileW, t)));
 }
 
+// Workspace of the queue counters alone, and with the precomputed per-image
+// tables after them (256-byte aligned).
+static size_t queue_bytes(int n)
+{
+    const size_t chunks = (static_cast<size_t>(n) + kRaggedMax - 1) / kRaggedMax;
+    return (chunks * sizeof(unsigned int) + 255) & ~static_cast<size_t>(255);
+}
+static size_t tables_bytes(const svdlut_image *imgs, int n)
+{
+    size_t t = 0;
+    for (int i = 0; i < n; ++i) t += prep_image_bytes(&imgs[i].dims);
+    return t;
+}
+
 static svdlut_status run_batched(const svdlut_image *imgs, int n, svdlut_dtype dtype, const svdlut_launch_cfg *cfg,
                                  void *ws, size_t ws_bytes, cudaStream_t s)
 {
@@ -100,6 +114,9 @@ static svdlut_status run_batched(const svdlut_image *imgs, int n, svdlut_dtype d
     const int ctas = cfg && cfg->ctas > 0 ? cfg->ctas : di.sm_count;
     const bool ranges = cfg && cfg->schedule == SVDLUT_SCHED_RANGES;
     unsigned int *queue = static_cast<unsigned int *>(ws);
+    // per-image tables precomputed once (prep_kernel) when the workspace holds them
+    const bool pre = ws_bytes >= queue_bytes(n) + tables_bytes(imgs, n) && aligned(ws, 256);
+    char *tab = static_cast<char *>(ws) + queue_bytes(n);
     for (int i0 = 0, chunk = 0; i0 < n; i0 += kRaggedMax, ++chunk) {
         LaunchArgs<kRaggedMax> a{};
         a.n = std::min(kRaggedMax, n - i0);
@@ -110,6 +127,14 @@ static svdlut_status run_batched(const svdlut_image *imgs, int n, svdlut_dtype d
         if (!ranges) {
             a.queue = queue + chunk;
             SVDLUT_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), s));
+        }
+        if (pre) {
+            for (int i = 0; i < a.n; ++i) {
+                set_prep_tables(a.img[i], &imgs[i0 + i].dims, tab);
+                tab += prep_image_bytes(&imgs[i0 + i].dims);
+            }
+            if ((st = launch_prep(a, di.sm_count, s)) != SVDLUT_OK) return st;
+            a.pre = 1;
         }
         if ((st = launch_apply(a, smem, dtype, s, std::min(ctas, a.total_blocks))) != SVDLUT_OK) return st;
     }
@@ -123,8 +148,15 @@ using namespace svdlut;
 extern "C" size_t svdlut_batched_workspace_size(int n)
 {
     if (n < 1) return 0;
-    const size_t chunks = (static_cast<size_t>(n) + kRaggedMax - 1) / kRaggedMax;
-    return (chunks * sizeof(unsigned int) + 255) & ~static_cast<size_t>(255);
+    return queue_bytes(n);
+}
+
+extern "C" size_t svdlut_batched_tables_workspace_size(const svdlut_image *imgs, int n)
+{
+    if (!imgs || n < 1) return 0;
+    for (int i = 0; i < n; ++i)
+        if (check_dims(&imgs[i].dims) != SVDLUT_OK) return 0;
+    return queue_bytes(n) + tables_bytes(imgs, n);
 }
 
 extern "C" svdlut_status svdlut_apply_batched(const svdlut_image *imgs, int n, svdlut_dtype dtype,

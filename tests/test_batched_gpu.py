@@ -190,3 +190,19 @@ def test_both_schedules_give_identical_output(sv, block_rows):
     for (x, d, p), y in zip(items, outs[1]):
         ref = sv.apply(torch.from_numpy(x).cuda(), sv.to_device(p))
         assert (y - ref).abs().max().item() <= 1e-6
+
+
+def test_tables_workspace_gives_identical_output(sv):
+    """Per-image tables precomputed into the workspace (prep_kernel) against
+    every CTA rebuilding them: identical bits, mixed dims and sizes, F32 and
+    u8, more than one launch chunk."""
+    import torch
+    items = si.make_ragged(seed=23, sizes=[(130, 37), (257, 67), (64, 64), (1, 1), (515, 300)] * 14)
+    for u8 in (False, True):
+        xs = [torch.from_numpy(si.to_u8(x) if u8 else x).cuda() for x, _, _ in items]
+        ps = [sv.to_device(p) for _, _, p in items]
+        a = [y.clone() for y in sv.Batch(xs, ps, tables=True).run()]
+        b = sv.Batch(xs, ps, tables=False).run()
+        torch.cuda.synchronize()
+        for ya, yb in zip(a, b):
+            assert torch.equal(ya, yb)
