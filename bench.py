@@ -657,6 +657,58 @@ def cpu_baseline(x, p, d, reps=2):
                       f"({dt:.1f} s wall)"}
 
 
+def oracle_table(reps_fast=5, reps_slow=3):
+    """Timings of the FP64 CPU oracle on the host for the five workloads of
+    the benchmark table (Mpix/s, median of repeated runs, one thread and all
+    host cores): 256x256 apply, 3840x2160 apply, the 16-image ragged batch
+    (sum over its images), the adjoint of 8 x 1920x1080 (the oracle's adjoint
+    is single-threaded) and the generator forward per 3840x2160 image."""
+    import oracle
+    from oracle import generator as G
+    oracle.build()
+    cores = os.cpu_count() or 1
+
+    def med(fn, reps):
+        ts = []
+        for _ in range(reps):
+            t = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t)
+        return statistics.median(ts)
+
+    out = {"cores": cores, "unit": "Mpix/s (median of repeated runs)"}
+    for name, H, W in (("config0_256x256", 256, 256), ("config1_3840x2160", H4K, W4K)):
+        d = si.spatial_dims(H, W)
+        x, p = si.make_batch(si.config_seed(0 if H == 256 else 1), 1, H, W, d)
+        oracle.forward(d, p, x[..., :8, :], nthreads=cores)  # warm
+        t1 = med(lambda: oracle.forward(d, p, x, nthreads=1), reps_slow if H > 256 else reps_fast)
+        tn = med(lambda: oracle.forward(d, p, x, nthreads=cores), reps_fast)
+        out[name] = {"1_core": round(H * W / t1 / 1e6, 3), f"{cores}_cores": round(H * W / tn / 1e6, 3)}
+    items = si.make_ragged()
+    px = sum(x.shape[1] * x.shape[2] for x, _, _ in items)
+
+    def ragged(n):
+        for x, d, p in items:
+            oracle.forward(d, p, x, nthreads=n)
+    t1, tn = med(lambda: ragged(1), reps_slow), med(lambda: ragged(cores), reps_fast)
+    out["config2_16_ragged"] = {"1_core": round(px / t1 / 1e6, 3), f"{cores}_cores": round(px / tn / 1e6, 3),
+                                "Mpix": round(px / 1e6, 2)}
+    Hb, Wb, B = 1080, 1920, 8
+    db = si.spatial_dims(Hb, Wb)
+    xb, pb = si.make_batch(si.config_seed(3), B, Hb, Wb, db)
+    gb = si.make_upstream(si.config_seed(3) + 1, xb.shape)
+    t1 = med(lambda: oracle.backward(db, pb, xb, gb), reps_slow)
+    out["config3_backward_8x1080p"] = {"1_core": round(B * Hb * Wb / t1 / 1e6, 3), "s_per_call": round(t1, 2),
+                                       "note": "the oracle's adjoint runs on one core"}
+    K = 8
+    blob = G.identity_blob(K, np.random.default_rng(si.config_seed(4)), scale=0.05)
+    x4, _ = si.make_batch(si.config_seed(4), 1, H4K, W4K, si.Dims(33, 8, K, 17, 17, 17))
+    tg = med(lambda: G.forward(blob, x4, K), reps_fast)
+    out["config4_generator_forward"] = {"ms_per_image": round(tg * 1e3, 2),
+                                        "note": "numpy FP64 with its default BLAS threads; input 3840x2160"}
+    return out
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return None
@@ -703,7 +755,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="time the FP64 CPU oracle on the five benchmark workloads and print one JSON line")
     args = ap.parse_args()
+    if args.oracle_table:
+        print(json.dumps(oracle_table()), flush=True)
+        return
     args.warmup = max(3, args.warmup)
     world, rank, local = (1, 0, 0)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1:
