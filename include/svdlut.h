@@ -375,6 +375,15 @@ svdlut_status svdlut_backward_noalloc(const svdlut_dims *dims, const svdlut_para
                                       int W, const float *x, const float *dy, float *dx,
                                       const svdlut_grads *grads, svdlut_stream_t stream);
 
+/*
+ * svdlut_tensor_core_timeouts -- number of tensor-core tiles (the tcgen05
+ * weight-gradient GEMM of svdlut_generator_backward) whose bounded wait for
+ * their matrix multiplies expired since the last call, on the current device;
+ * the counter is then reset.  Such a tile writes NaN instead of its result.
+ * Synchronises the device.  Not a computation of the paper.
+ */
+svdlut_status svdlut_tensor_core_timeouts(uint32_t *count);
+
 /* Message of the last error raised on this thread ("" if none). */
 const char *svdlut_last_error(void);
 

@@ -124,6 +124,8 @@ def _declare(lib):
     lib.svdlut_apply_ws.argtypes = [P(Dims), P(Params), c_int, c_int, c_int, c_int, c_void_p, c_void_p,
                                     P(LaunchCfg), c_void_p, c_size_t, c_void_p]
     lib.svdlut_apply_ws.restype = c_int
+    lib.svdlut_tensor_core_timeouts.argtypes = [c_void_p]
+    lib.svdlut_tensor_core_timeouts.restype = c_int
     lib.svdlut_apply_workspace_size.argtypes = [P(Dims), c_int]
     lib.svdlut_apply_workspace_size.restype = c_size_t
     lib.svdlut_apply_host.argtypes = [P(Dims), P(Params), c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,

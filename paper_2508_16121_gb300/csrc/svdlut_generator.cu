@@ -8,6 +8,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "svdlut_internal.cuh"
@@ -77,17 +78,21 @@ struct WsLayout {
 
 inline size_t act_size(int B, int i) { return static_cast<size_t>(B) * kCh[i + 1] * kSz[i + 1] * kSz[i + 1]; }
 
-// Weight gradient of conv i: the sum over the batch's output pixels is cut
-// into chunks of wgrad_chunk_px pixels (one GEMM slice each, a multiple of the
-// 32-wide K step) so that output tiles x chunks give about four resident
-// CTAs per SM.
+// Weight gradient of conv i (wgrad_kernel): tiles of 126 im2col columns
+// (with the bias column) and N = output channels padded to 16, 32 or 64; the
+// batch's output pixels are cut into chunks of wgrad_chunk_px pixels (a
+// multiple of the 64-pixel stage) so that tiles x chunks fill the resident
+// CTAs of one wave on 152 SMs (a fixed split: the summation order, hence the
+// result, does not depend on the device).
+inline int wgrad_np(int Cout) { return Cout <= 16 ? 16 : Cout <= 32 ? 32 : 64; }
+inline int wgrad_tiles(int i) { return (kCh[i] * 9 + 1 + 125) / 126; }
 inline int wgrad_chunk_px(int B, int i)
 {
-    const int pix = B * kSz[i + 1] * kSz[i + 1];
-    const int tiles = ((kCh[i + 1] + 63) / 64) * ((kCh[i] * 9 + 1 + 63) / 64);
-    const int want = std::max(1, (4 * 152 + tiles - 1) / tiles);
+    const int pix = B * kSz[i + 1] * kSz[i + 1], np = wgrad_np(kCh[i + 1]);
+    const int ctas = (np <= 16 ? 3 : 2) * 152;  // wgrad_ctas_per_sm(np) x SMs
+    const int want = std::max(1, (ctas + wgrad_tiles(i) - 1) / wgrad_tiles(i));
     const int px = (pix + want - 1) / want;
-    return std::max(32, (px + 31) / 32 * 32);
+    return std::max(64, (px + 63) / 64 * 64);
 }
 inline int wgrad_chunks(int B, int i)
 {
@@ -169,12 +174,8 @@ __global__ void downsample_kernel(const float *__restrict__ x, int B, int H, int
     }
 }
 
-// ---- BF16 tensor-core GEMM:  C[m][n] = sum_k A(m, k) B(k, n) ----
-// 64 x 64 tile per CTA, 4 warps of 32 x 32, K staged 32 at a time in shared
-// memory as BF16 (rows padded to 40 elements: conflict-free fragment loads),
-// mma.sync m16n8k16 with FP32 accumulators.  A and B are gather functors
-// (im2col and friends); the epilogue functor stores C.  blockIdx.z selects a
-// reduction chunk (the functors map (k, z) to their global index).
+// ---- BF16 mma.sync fragments of the forward and input-gradient convolutions ----
+// (64 x 64 output tile per CTA, 4 warps of 32 x 32, m16n8k16, FP32 accumulators)
 constexpr int kGT = 128;
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
@@ -186,175 +187,266 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// SPLIT = false: operands rounded to BF16 (forward).  SPLIT = true: each FP32
-// operand is carried as hi + lo BF16 parts and the product is accumulated as
-// hi*hi + hi*lo + lo*hi (three MMAs, ~16 mantissa bits): the backward passes
-// sum long chains of cancelling terms, where plain BF16 loses too much.
-// ROWS = true: a loading thread keeps one tile row (m or n) and 16 consecutive
-// k, for functors whose row index is costly to decode (im2col over input
-// pixels); ROWS = false: it keeps one k and strides over rows, for functors
-// whose k index is costly (pixels of a weight-gradient chunk).
-template <bool SPLIT, bool ROWS, class AL, class BL, class EP>
-__global__ void __launch_bounds__(kGT) mma_gemm_kernel(int M, int N, int Kd, AL al, BL bl, EP ep)
+// ---- weight gradients of the stride-2 pad-1 3x3 convolutions on tcgen05 ----
+// dW[o][j] = sum over the batch's output pixels p of dz[o][p] im2col[p][j],
+// j = (c, ky, kx) < Kd = 9 Cin, and the bias gradient as column j = Kd (an
+// all-ones im2col column).  A CTA takes one tile of kWRows = 126 columns j
+// (blockIdx.x: 42 whole (c, ky) groups, so the three kx of a group never
+// straddle two tiles) and one chunk of pixels (blockIdx.y), and writes that
+// chunk's partial [Cout][Kd + 1] slice; wgrad_reduce_kernel sums the chunks
+// in a fixed order.  The columns j are the MMA's M = 128 rows (TMEM lanes),
+// the output channels its N = NP >= Cout columns, the pixels its K: per
+// stage of kWK = 64 pixels both operands are staged K-major in shared memory
+// (two stages in flight) as BF16 hi and lo parts, and one thread issues
+// lo*hi + hi*lo + hi*hi (three kind::f16 MMAs per 16-wide K step, about 16
+// mantissa bits: the gradient sums are long chains of cancelling terms) into
+// FP32 accumulators in TMEM.  Shared-memory layout: no swizzle, core
+// matrices of 8 rows x 16 bytes; element (r, k) of an R-row operand sits at
+// byte (k / 8) * 16 R + 16 r + 2 (k % 8), so the 8 pixels of one octet of
+// one row are a single 16-byte store, and a warp's stores of consecutive
+// rows are free of bank conflicts.  Staging tasks: an A task is one (c, ky)
+// group x one pixel octet, the 16 input values of one input row under it
+// (four float4 loads; 2 ox0 is a multiple of 16) and its left neighbour,
+// mapped through the InstanceNorm affine, giving the three kx rows; a B task
+// is one dz row x one octet (two float4 loads).  Rows that never change (the
+// bias row, the padding rows of the tile and of N) are written once.  Every
+// wait is bounded: on expiry the outputs are NaN and g_umma_timeouts counts
+// the warp.
+constexpr int kWT = 256;     // threads: warp w reads TMEM lanes 32 (w % 4) .. + 31
+constexpr int kWK = 64;      // pixels per stage (four K steps of 16)
+constexpr int kWRows = 126;  // columns j per tile
+__device__ unsigned int g_umma_timeouts;
+
+static_assert(kSz[0] % 16 == 0 && kSz[1] % 16 == 0 && kSz[2] % 16 == 0 && kSz[3] % 16 == 0 && kSz[4] % 16 == 0,
+              "input rows of the weight gradient are loaded as float4 from 16-float boundaries");
+static_assert(kSz[5] % 8 == 0, "an output row holds whole pixel octets, an image whole stages");
+static_assert(kCh[1] <= 64 && kCh[2] <= 64 && kCh[3] <= 64 && kCh[4] <= 64 && kCh[5] <= 64,
+              "output channels of a weight gradient: at most the MMA's N = 64");
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// shared-memory matrix descriptor, no swizzle: start, leading (K) and stride
+// (M/N) byte offsets between core matrices, descriptor version 1
+__device__ __forceinline__ uint64_t umma_sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
-    constexpr int NP = SPLIT ? 2 : 1;
-    __shared__ __align__(16) __nv_bfloat16 As[NP][64][40];
-    __shared__ __align__(16) __nv_bfloat16 Bs[NP][64][40];
-    const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64, z = blockIdx.z;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int g = lane >> 2, t = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    for (int k0 = 0; k0 < Kd; k0 += 32) {
-        // all 2 x 16 gathers of this thread are issued before any is used
-        constexpr int kPer = 64 * 32 / kGT;
-        float va[kPer], vb[kPer];
-        if (ROWS) {
-            const int r = tid >> 1, c0 = (tid & 1) * kPer, m = m0 + r, n = n0 + r;
-#pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                const int k = k0 + c0 + q;
-                va[q] = (m < M && k < Kd) ? al(m, k, z) : 0.f;
-                vb[q] = (n < N && k < Kd) ? bl(k, n, z) : 0.f;
-            }
-        } else {
-            const int c = tid & 31, k = k0 + c;
-#pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                const int r = (tid >> 5) + 4 * q, m = m0 + r, n = n0 + r;
-                va[q] = (m < M && k < Kd) ? al(m, k, z) : 0.f;
-                vb[q] = (n < N && k < Kd) ? bl(k, n, z) : 0.f;
-            }
-        }
-        const int r = ROWS ? tid >> 1 : 0, c0 = ROWS ? (tid & 1) * kPer : 0;
-        if (!ROWS) {
-            const int c = tid & 31;
-#pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                const int rr = (tid >> 5) + 4 * q;
-                const __nv_bfloat16 ha = __float2bfloat16_rn(va[q]), hb = __float2bfloat16_rn(vb[q]);
-                As[0][rr][c] = ha;
-                Bs[0][rr][c] = hb;
-                if (SPLIT) {
-                    As[NP - 1][rr][c] = __float2bfloat16_rn(va[q] - __bfloat162float(ha));
-                    Bs[NP - 1][rr][c] = __float2bfloat16_rn(vb[q] - __bfloat162float(hb));
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < (ROWS ? kPer : 0); q += 2) {
-            const __nv_bfloat162 ha = __floats2bfloat162_rn(va[q], va[q + 1]);
-            const __nv_bfloat162 hb = __floats2bfloat162_rn(vb[q], vb[q + 1]);
-            *reinterpret_cast<__nv_bfloat162 *>(&As[0][r][c0 + q]) = ha;
-            *reinterpret_cast<__nv_bfloat162 *>(&Bs[0][r][c0 + q]) = hb;
-            if (SPLIT) {
-                *reinterpret_cast<__nv_bfloat162 *>(&As[NP - 1][r][c0 + q]) = __floats2bfloat162_rn(
-                    va[q] - __low2float(ha), va[q + 1] - __high2float(ha));
-                *reinterpret_cast<__nv_bfloat162 *>(&Bs[NP - 1][r][c0 + q]) = __floats2bfloat162_rn(
-                    vb[q] - __low2float(hb), vb[q + 1] - __high2float(hb));
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 32; kk += 16) {
-            uint32_t a[NP][2][4], b[NP][4][2];
-#pragma unroll
-            for (int pp = 0; pp < NP; ++pp) {
-#pragma unroll
-                for (int mi = 0; mi < 2; ++mi) {
-                    const int r = wm + mi * 16 + g;
-                    a[pp][mi][0] = *reinterpret_cast<const uint32_t *>(&As[pp][r][kk + 2 * t]);
-                    a[pp][mi][1] = *reinterpret_cast<const uint32_t *>(&As[pp][r + 8][kk + 2 * t]);
-                    a[pp][mi][2] = *reinterpret_cast<const uint32_t *>(&As[pp][r][kk + 8 + 2 * t]);
-                    a[pp][mi][3] = *reinterpret_cast<const uint32_t *>(&As[pp][r + 8][kk + 8 + 2 * t]);
-                }
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) {
-                    const int n = wn + ni * 8 + g;
-                    b[pp][ni][0] = *reinterpret_cast<const uint32_t *>(&Bs[pp][n][kk + 2 * t]);
-                    b[pp][ni][1] = *reinterpret_cast<const uint32_t *>(&Bs[pp][n][kk + 8 + 2 * t]);
-                }
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) {
-                    if (SPLIT) {
-                        mma_bf16(acc[mi][ni], a[NP - 1][mi], b[0][ni]);
-                        mma_bf16(acc[mi][ni], a[0][mi], b[NP - 1][ni]);
-                    }
-                    mma_bf16(acc[mi][ni], a[0][mi], b[0][ni]);
-                }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int m = m0 + wm + mi * 16 + g + (q >= 2 ? 8 : 0);
-                const int n = n0 + wn + ni * 8 + 2 * t + (q & 1);
-                if (m < M && n < N) ep(m, n, z, acc[mi][ni][q]);
-            }
+    return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+           (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (static_cast<uint64_t>(1) << 46);
 }
 
-// im2col of the stride-2 pad-1 3x3 convolution: row m = (b, oy, ox), column
-// k = (c, ky, kx) (the order of the weight tensor [Cout][Cin][3][3]).
-// With sc/sh set, the input is the InstanceNorm output sc[b][c] * r + sh[b][c]
-// of the raw activation r (zero padding is applied after the map).
-struct Im2col {
-    const float *in;
-    int C, S, So;
-    const float *sc = nullptr, *sh = nullptr;
-    __device__ float operator()(int m, int k, int /*z*/) const
-    {
-        const int b = m / (So * So), r = m - b * So * So, oy = r / So, ox = r - oy * So;
-        const int c = k / 9, tt = k - c * 9, ky = tt / 3, kx = tt - ky * 3;
-        const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
-        if (iy < 0 || iy >= S || ix < 0 || ix >= S) return 0.f;
-        const float v = __ldg(in + (static_cast<size_t>(b * C + c) * S + iy) * S + ix);
-        return sc ? fmaf(v, __ldg(sc + b * C + c), __ldg(sh + b * C + c)) : v;
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N and M
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t taddr, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+// waits until the mbarrier's phase of the given parity completes; false if
+// the bounded wait expired
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    uint32_t done = 0;
+    for (long it = 0; it < (1L << 26) && !done; ++it)
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(parity)
+                     : "memory");
+    return done != 0;
+}
+
+// 8 FP32 values as BF16 hi and lo = bf16(v - hi): one 16-byte store each
+__device__ __forceinline__ void split_store(char *hi, char *lo, const float (&v)[8])
+{
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(v[2 * q] - __low2float(hh), v[2 * q + 1] - __high2float(hh));
+        h[q] = *reinterpret_cast<const uint32_t *>(&hh);
+        l[q] = *reinterpret_cast<const uint32_t *>(&ll);
     }
+    *reinterpret_cast<uint4 *>(hi) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(lo) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+struct WgradArgs {
+    const float *in;       // [B][Cin][S][S] layer input (the raw activation when sc is set)
+    const float *sc, *sh;  // [B][Cin] InstanceNorm affine applied on load (zero padding after it), or null
+    const float *dz;       // [B][Cout][So][So] gradient of the conv output
+    float *part;           // [chunks][Cout][Kd + 1] partial sums
+    int Cin, Cout, S, So, npix, chunk;
 };
-// weight gradient: rows i = output channel, columns j = (c, ky, kx), the
-// reduction over pixels is chunked by blockIdx.z (partials summed later)
-struct DzRows {  // A(i, kk) = dz[b][i][p] for pixel kk of chunk z
-    const float *dz;
-    int N, So, pix, chunk;
-    __device__ float operator()(int i, int kk, int z) const
-    {
-        const int m = z * chunk + kk;
-        if (m >= pix) return 0.f;
-        const int b = m / (So * So), rr = m - b * So * So;
-        return __ldg(dz + (static_cast<size_t>(b) * N + i) * So * So + rr);
+
+// bytes of one stage: hi and lo parts of the 128-row A and the NP-row B operand
+__host__ __device__ constexpr int wgrad_stage_bytes(int NP) { return 2 * (128 + NP) * kWK * 2; }
+// CTAs per SM that the two stages allow in 227 KB of shared memory
+constexpr int wgrad_ctas_per_sm(int NP) { return (227 * 1024) / (2 * wgrad_stage_bytes(NP) + 1024); }
+
+template <int NP>
+__global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const WgradArgs p)
+{
+    static_assert(NP % 16 == 0 && NP >= 16 && NP <= 64, "N of an M = 128 MMA: 16 .. 64, multiple of 16");
+    constexpr uint32_t kCols = NP < 32 ? 32 : NP;  // TMEM columns (power of 2 >= 32)
+    constexpr int kA = 128 * kWK * 2, kB = NP * kWK * 2, kStage = wgrad_stage_bytes(NP);
+    constexpr uint32_t idesc = umma_idesc_bf16(128, NP);
+    extern __shared__ __align__(128) char wsm[];  // stage s % 2: [A hi][A lo][B hi][B lo]
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t taddr_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = blockIdx.x, z = blockIdx.y;
+    const int Kd = 9 * p.Cin, P = p.So * p.So;
+    const int ng = max(0, min(kWRows / 3, 3 * p.Cin - (kWRows / 3) * tile));  // live (c, ky) groups
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&taddr_s)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-};
-struct Im2colChunk {  // B(kk, j) = im2col(m = z * chunk + kk, j); column Kd is all ones (bias)
-    Im2col ic;
-    int pix, chunk, Kd;
-    __device__ float operator()(int kk, int j, int z) const
-    {
-        const int m = z * chunk + kk;
-        if (m >= pix) return 0.f;
-        return j == Kd ? 1.f : ic(m, j, 0);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
     }
-};
-struct PartOut {
-    float *part;
-    int N, Kd;
-    __device__ void operator()(int i, int j, int z, float v) const
-    {
-        part[(static_cast<size_t>(z) * N + i) * Kd + j] = v;
+    // rows that never change: everything zero, then the bias row (hi = 1)
+    for (int i = tid; i < 2 * kStage / 16; i += kWT) reinterpret_cast<uint4 *>(wsm)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    const int rb = Kd - kWRows * tile;
+    if (rb >= 0 && rb < kWRows && tid < 16)
+        *reinterpret_cast<uint4 *>(wsm + (tid >> 3) * kStage + (tid & 7) * 16 * 128 + 16 * rb) =
+            make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t taddr = taddr_s;
+    const int m_beg = z * p.chunk;
+    const int nst = (min(p.chunk, p.npix - m_beg) + kWK - 1) / kWK;
+    const int na = ng * 8, nt = na + p.Cout * 8;
+    bool ok = true;
+    for (int s = 0; s < nst; ++s) {
+        const int buf = s & 1;
+        char *stg = wsm + buf * kStage;
+        if (s >= 2) ok = mbar_wait(smem_addr(&mbar[buf]), ((s - 2) >> 1) & 1) && ok;  // stage s - 2 read
+        const int m0 = m_beg + s * kWK;
+        for (int t = tid; t < nt; t += kWT) {
+            if (t < na) {
+                const int q = t / ng, g = t - q * ng;
+                const int cg = (kWRows / 3) * tile + g, c = cg / 3, ky = cg - 3 * c;
+                const int m = m0 + 8 * q;
+                float v[16], left = 0.f;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) v[u] = 0.f;
+                if (m < p.npix) {
+                    const int b = m / P, rr = m - b * P, oy = rr / p.So, ox0 = rr - oy * p.So;
+                    const int iy = 2 * oy + ky - 1;
+                    if (iy >= 0 && iy < p.S) {
+                        const float *row =
+                            p.in + (static_cast<size_t>(b * p.Cin + c) * p.S + iy) * p.S + 2 * ox0;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float4 f = __ldg(reinterpret_cast<const float4 *>(row) + u);
+                            v[4 * u] = f.x;
+                            v[4 * u + 1] = f.y;
+                            v[4 * u + 2] = f.z;
+                            v[4 * u + 3] = f.w;
+                        }
+                        if (ox0 > 0) left = __ldg(row - 1);
+                        if (p.sc) {
+                            const float a = __ldg(p.sc + b * p.Cin + c), h = __ldg(p.sh + b * p.Cin + c);
+#pragma unroll
+                            for (int u = 0; u < 16; ++u) v[u] = fmaf(v[u], a, h);
+                            if (ox0 > 0) left = fmaf(left, a, h);
+                        }
+                    }
+                }
+                // input column 2 ox + kx - 1 of the octet's pixels ox0 + u
+                float r0[8], r1[8], r2[8];
+                r0[0] = left;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (u > 0) r0[u] = v[2 * u - 1];
+                    r1[u] = v[2 * u];
+                    r2[u] = v[2 * u + 1];
+                }
+                char *dst = stg + q * 16 * 128 + 16 * (3 * g);
+                split_store(dst, dst + kA, r0);
+                split_store(dst + 16, dst + kA + 16, r1);
+                split_store(dst + 32, dst + kA + 32, r2);
+            } else {
+                const int tb = t - na, q = tb / p.Cout, o = tb - q * p.Cout;
+                const int m = m0 + 8 * q;
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = 0.f;
+                if (m < p.npix) {
+                    const int b = m / P, rr = m - b * P;
+                    const float4 *src =
+                        reinterpret_cast<const float4 *>(p.dz + (static_cast<size_t>(b) * p.Cout + o) * P + rr);
+                    const float4 f0 = __ldg(src), f1 = __ldg(src + 1);
+                    v[0] = f0.x, v[1] = f0.y, v[2] = f0.z, v[3] = f0.w;
+                    v[4] = f1.x, v[5] = f1.y, v[6] = f1.z, v[7] = f1.w;
+                }
+                char *dst = stg + 2 * kA + q * 16 * NP + 16 * o;
+                split_store(dst, dst + kB, v);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic stores -> tensor core
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t a0 = smem_addr(stg), b0 = a0 + 2 * kA;
+#pragma unroll
+            for (int kk = 0; kk < kWK / 16; ++kk) {
+                const uint64_t ahi = umma_sdesc(a0 + kk * 2 * 16 * 128, 16 * 128, 128);
+                const uint64_t alo = umma_sdesc(a0 + kA + kk * 2 * 16 * 128, 16 * 128, 128);
+                const uint64_t bhi = umma_sdesc(b0 + kk * 2 * 16 * NP, 16 * NP, 128);
+                const uint64_t blo = umma_sdesc(b0 + kB + kk * 2 * 16 * NP, 16 * NP, 128);
+                umma_bf16(taddr, alo, bhi, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                umma_bf16(taddr, ahi, blo, idesc, 1u);
+                umma_bf16(taddr, ahi, bhi, idesc, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_addr(&mbar[buf]))
+                         : "memory");
+        }
     }
-};
+    if (nst > 0) ok = mbar_wait(smem_addr(&mbar[(nst - 1) & 1]), ((nst - 1) >> 1) & 1) && ok;  // all MMAs
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (!ok && lane == 0) atomicAdd(&g_umma_timeouts, 1u);
+    // epilogue: warp w holds rows 32 (w % 4) + lane of D, columns of half w / 4
+    const int r = 32 * (warp & 3) + lane, j = kWRows * tile + r;
+    constexpr int kHalf = NP / 2;
+    const int cb = (warp >> 2) * kHalf;
+#pragma unroll
+    for (int c0 = 0; c0 < kHalf; c0 += 8) {
+        uint32_t v[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                     : "r"(taddr + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + cb + c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int o = cb + c0 + q;
+            if (r < kWRows && j <= Kd && o < p.Cout)
+                p.part[(static_cast<size_t>(z) * p.Cout + o) * (Kd + 1) + j] =
+                    ok ? __uint_as_float(v[q]) : __int_as_float(0x7fc00000);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(kCols));
+    }
+}
+
 // ---- forward convolution (implicit GEMM, split over K) ----
 // Rows m = output pixel (b, oy, ox), columns n = output channel, reduction
 // k = (c, ky, kx) in the order of the weight tensor [N][C][3][3].  CTA z of a
@@ -676,11 +768,21 @@ __global__ void __launch_bounds__(512) conv_finish_kernel(const float *__restric
     }
 }
 
-template <bool SPLIT, bool ROWS, class AL, class BL, class EP>
-static svdlut_status gemm(int M, int N, int Kd, int Z, AL al, BL bl, EP ep, cudaStream_t s)
+// Launch of wgrad_kernel<NP> (opted into its dynamic shared memory once per
+// device).
+template <int NP>
+static svdlut_status launch_wgrad(const WgradArgs &a, int tiles, int chunks, cudaStream_t s)
 {
-    dim3 grid((M + 63) / 64, (N + 63) / 64, Z);
-    mma_gemm_kernel<SPLIT, ROWS><<<grid, kGT, 0, s>>>(M, N, Kd, al, bl, ep);
+    constexpr int smem = 2 * wgrad_stage_bytes(NP);
+    static std::atomic<unsigned long long> opted{0};
+    int dev = 0;
+    SVDLUT_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(opted.load() & bit)) {
+        SVDLUT_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        opted.fetch_or(bit);
+    }
+    wgrad_kernel<NP><<<dim3(tiles, chunks), kWT, smem, s>>>(a);
     SVDLUT_CUDA_TRY(cudaGetLastError());
     return SVDLUT_OK;
 }
@@ -1012,6 +1114,19 @@ inline HeadW head_weights(const float *w, const Layout &L, int K)
 }  // namespace gen
 }  // namespace svdlut
 
+extern "C" svdlut_status svdlut_tensor_core_timeouts(uint32_t *count)
+{
+    svdlut::clear_error();
+    if (!count) return svdlut::fail(SVDLUT_ERR_INVALID_ARG, "count is NULL");
+    unsigned int h = 0;
+    const unsigned int zero = 0;
+    SVDLUT_CUDA_TRY(cudaDeviceSynchronize());
+    SVDLUT_CUDA_TRY(cudaMemcpyFromSymbol(&h, svdlut::gen::g_umma_timeouts, sizeof h));
+    SVDLUT_CUDA_TRY(cudaMemcpyToSymbol(svdlut::gen::g_umma_timeouts, &zero, sizeof zero));
+    *count = h;
+    return SVDLUT_OK;
+}
+
 using namespace svdlut;
 using namespace svdlut::gen;
 
@@ -1130,12 +1245,13 @@ extern "C" svdlut_status svdlut_generator_backward(int K, const float *weights, 
     for (int i = 4; i >= 0; --i) {
         const int Cin = kCh[i], Cout = kCh[i + 1], S = kSz[i], So = kSz[i + 1];
         const int pix = B * So * So, Kd = Cin * 9, chunk = wgrad_chunk_px(B, i), chunks = wgrad_chunks(B, i);
-        const Im2col icol = i == 0 ? Im2col{w + wl.thumb, Cin, S, So}
-                                   : Im2col{w + wl.r[i - 1], Cin, S, So, w + wl.sc[i - 1], w + wl.sh[i - 1]};
         // weight and bias gradient: partial per pixel chunk (bias = an extra
         // all-ones im2col column), then an ordered sum
-        st = gemm<true, false>(Cout, Kd + 1, chunk, chunks, DzRows{dz, Cout, So, pix, chunk},
-                        Im2colChunk{icol, pix, chunk, Kd}, PartOut{w + wl.wpart, Cout, Kd + 1}, s);
+        const WgradArgs wa{i == 0 ? w + wl.thumb : w + wl.r[i - 1], i == 0 ? nullptr : w + wl.sc[i - 1],
+                           i == 0 ? nullptr : w + wl.sh[i - 1], dz, w + wl.wpart, Cin, Cout, S, So, pix, chunk};
+        const int np = wgrad_np(Cout), tiles = wgrad_tiles(i);
+        st = np == 16 ? launch_wgrad<16>(wa, tiles, chunks, s)
+                      : np == 32 ? launch_wgrad<32>(wa, tiles, chunks, s) : launch_wgrad<64>(wa, tiles, chunks, s);
         if (st != SVDLUT_OK) return st;
         wgrad_reduce_kernel<<<(Cout * (Kd + 1) * 32 + 255) / 256, 256, 0, s>>>(
             w + wl.wpart, chunks, Cout, Kd, dweights + L.conv_w[i], dweights + L.conv_b[i]);

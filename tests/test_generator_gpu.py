@@ -163,3 +163,23 @@ def test_forward_on_4k_frames_matches_oracle(sv):
     ref, _ = G.forward(blob, x, K)
     for k in ref:
         assert rel(out[k].cpu().numpy().astype(np.float64), ref[k]) <= 2e-2, k
+
+
+def test_tensor_core_tiles_complete(sv):
+    """The weight gradients run on tcgen05 tensor cores with bounded waits:
+    after a backward pass no tile reported an expired wait."""
+    import ctypes
+    import torch
+    from paper_2508_16121_gb300 import _lib
+    lib = _lib.load()
+    cnt = ctypes.c_uint32(0)
+    assert lib.svdlut_tensor_core_timeouts(ctypes.byref(cnt)) == 0
+    K = 6
+    blob = make_blob(K, 140)
+    x = torch.from_numpy(np.stack([si.make_image(np.random.default_rng(150 + j), 96, 128) for j in range(2)])).cuda()
+    gen = gpu_gen(sv, K, blob, B=2)
+    out = gen.forward(x, training=True, seed=5)
+    dw = gen.backward({k: torch.ones_like(v) for k, v in out.items()})
+    assert torch.isfinite(dw).all()
+    assert lib.svdlut_tensor_core_timeouts(ctypes.byref(cnt)) == 0
+    assert cnt.value == 0
