@@ -131,8 +131,10 @@ struct BwdArgs {
 // LUT gradients: G^c_p[i][j] = sum_px dy_c * bilinear weight of vertex (i, j)
 // at (x_alpha, x_beta) for pair p = (alpha, beta).
 // grid (P, B); CTA (p, b) owns the rows [p H / P, (p+1) H / P) of image b.
-// Warp (group g, pair q) takes the 128-column strips g, g + 4, ... and walks
-// down the CTA's rows of each; lane l takes columns l + 32 k (k = 0..3:
+// Its work units are (128-column strip, row slice): the rows are cut into
+// slices = max(1, 4 / strips) slices, so that narrow images keep all four
+// warp groups busy.  Warp (group g, pair q) takes the units g, g + 4, ... and
+// walks down the rows of each; lane l takes columns l + 32 k (k = 0..3:
 // coalesced loads) and keeps, per column, the four corner contributions
 // (three channels each) of its current cell in registers: while the cell
 // does not change (smooth regions, where consecutive rows fall in the same
@@ -171,7 +173,10 @@ __global__ void __launch_bounds__(kLutThreads, 1)
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc[k][q][c] = 0.f;
-    for (int strip = grp; strip < a.strips; strip += kGroups) {
+    const int slices = max(1, kGroups / a.strips), units = a.strips * slices;
+    for (int u = grp; u < units; u += kGroups) {
+        const int strip = u % a.strips, sl = u / a.strips;
+        const int ra = r0 + (r1 - r0) * sl / slices, rb = r0 + (r1 - r0) * (sl + 1) / slices;
         const int x = strip * kTileW + lane;
         const int n = x < a.W ? min(4, (a.W - x + 31) >> 5) : 0;  // this lane's columns x + 32 k, k < n
         struct Row {
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(kLutThreads, 1)
         auto load = [&](int r, Row &o) {
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             o.pa = o.pb = o.g0 = o.g1 = o.g2 = z;
-            if (r < r1 && n > 0) {
+            if (r < rb && n > 0) {
                 const size_t off = static_cast<size_t>(r) * a.W + x;
                 o.pa = PixIO<float>::load_s(xb + A * plane + off, n);
                 o.pb = PixIO<float>::load_s(xb + Bx * plane + off, n);
@@ -190,9 +195,9 @@ __global__ void __launch_bounds__(kLutThreads, 1)
             }
         };
         Row cur, nx1, nx2;
-        load(r0, cur);
-        load(r0 + 1, nx1);
-        for (int r = r0; r < r1; ++r) {
+        load(ra, cur);
+        load(ra + 1, nx1);
+        for (int r = ra; r < rb; ++r) {
             load(r + 2, nx2);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(kLutThreads, 1)
             cur = nx1;
             nx1 = nx2;
         }
-        // the strip's runs end here
+        // the unit's runs end here
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             warp_scatter<3, true>(tab, acc_key[k], D * 4, 4, acc[k]);
@@ -739,7 +744,23 @@ static svdlut_status plan_backward(const svdlut_dims *d, int B, int H, int W, in
     const int D = d->D_t, Dsc = d->Dsc;
     pl->lut_smem = sizeof(float) * (static_cast<size_t>(kLutWarps) * 4 * D * D + kLutWarps);
     if (pl->lut_smem > smem_limit) return fail(SVDLUT_ERR_UNSUPPORTED, "D_t=%d too large for the adjoint", D);
-    pl->P = std::max(1, std::min(H, (sm_count + B - 1) / B));
+    // LUT pass: P CTAs per image (one CTA per SM); estimated time = waves x
+    // (rows a warp group walks + a fixed cost of about 16 rows per CTA:
+    // clearing the tables, writing the partial)
+    {
+        const int strips = (W + kTileW - 1) / kTileW, G = kLutWarps / 3;
+        const int slices = std::max(1, G / strips), per_units = (strips * slices + G - 1) / G;
+        long long best_cost = -1;
+        for (int P = 1; P <= std::min(H, 4 * sm_count); ++P) {
+            const long long waves = (static_cast<long long>(B) * P + sm_count - 1) / sm_count;
+            const int rows = (H + P - 1) / P;
+            const long long cost = waves * (static_cast<long long>(per_units) * ((rows + slices - 1) / slices) + 16);
+            if (best_cost < 0 || cost < best_cost) {
+                best_cost = cost;
+                pl->P = P;
+            }
+        }
+    }
     // grid pass: blocks of 128 x BH; bands chosen like the forward plan
     const int strips = (W + kTileW - 1) / kTileW;
     const int max_bands = std::max(1, (H + kMinBlockH - 1) / kMinBlockH);
