@@ -9,6 +9,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <vector>
+#include <utility>
+#include <mutex>
 #include <cstdint>
 
 #include "svdlut_internal.cuh"
@@ -70,7 +73,7 @@ inline Layout make_layout(int K)
 // backward temporaries.  InstanceNorm is not materialised: the layer after it
 // reads r[i] and applies the per-(b, c) affine map sc * r + sh on load.
 struct WsLayout {
-    size_t thumb, r[5], mean[4], rstd[4], sc[4], sh[4], part, rho, hidden;
+    size_t thumb, r[5], mean[4], rstd[4], sc[4], sh[4], part, wbf[5], rho, hidden;
     size_t dz[2], dact, wpart, dhid, drho, insum;
     size_t total;
 };
@@ -100,17 +103,22 @@ inline int wgrad_chunks(int B, int i)
     return (pix + c - 1) / c;
 }
 
-// Split-K factor of forward conv i: enough (M-tile, K-slice) CTAs to cover
-// the SMs twice, at most one 32-wide K step per slice.
-inline int fwd_split(int B, int i)
+// Forward conv i (conv_umma_kernel): K = 9 Cin in stages of 64 (kWK); the
+// CTAs are (128-pixel tile, K split).  Layers with fewer than two tiles per
+// SM split K so that tiles x splits give about four CTAs per SM; ks = stages
+// per split.  (Fixed numbers, not the device's: the summation order, hence
+// the result, does not depend on the GPU.)
+inline int conv_stages(int i) { return (kCh[i] * 9 + 63) / 64; }
+inline int conv_ks(int B, int i)
 {
-    const int M = B * kSz[i + 1] * kSz[i + 1], tiles = (M + 63) / 64, ksteps = (kCh[i] * 9 + 31) / 32;
-    const int want = (2 * 152 + tiles - 1) / tiles;
-    return std::max(1, std::min(ksteps, want));
+    const int tiles = (B * kSz[i + 1] * kSz[i + 1] + 127) / 128, nst = conv_stages(i);
+    if (tiles >= 2 * 152) return nst;
+    const int want = (4 * 152 + tiles - 1) / tiles;
+    return std::max(1, (nst + want - 1) / want);
 }
-
-// K steps per slice for a split of Z
-inline int fwd_ksteps(int i, int Z) { return ((kCh[i] * 9 + 31) / 32 + Z - 1) / Z; }
+inline int conv_split(int B, int i) { return (conv_stages(i) + conv_ks(B, i) - 1) / conv_ks(B, i); }
+// BF16 elements of conv i's weights in the B layout (NP x whole stages)
+inline size_t conv_wbf_elems(int i) { return static_cast<size_t>(wgrad_np(kCh[i + 1])) * conv_stages(i) * 64; }
 
 inline WsLayout make_ws(int B)
 {
@@ -130,8 +138,9 @@ inline WsLayout make_ws(int B)
         w.sh[i] = take(static_cast<size_t>(B) * kCh[i + 1]);
     }
     size_t pp = 0;
-    for (int i = 0; i < 5; ++i) pp = std::max(pp, static_cast<size_t>(fwd_split(B, i)) * act_size(B, i));
+    for (int i = 0; i < 5; ++i) pp = std::max(pp, static_cast<size_t>(conv_split(B, i)) * act_size(B, i));
     w.part = take(pp);
+    for (int i = 0; i < 5; ++i) w.wbf[i] = take((conv_wbf_elems(i) + 1) / 2);
     w.rho = take(static_cast<size_t>(B) * kRho);
     w.hidden = take(static_cast<size_t>(B) * 4 * kHidden);
     const size_t amax = act_size(B, 0);
@@ -447,125 +456,201 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
     }
 }
 
-// ---- forward convolution (implicit GEMM, split over K) ----
-// Rows m = output pixel (b, oy, ox), columns n = output channel, reduction
-// k = (c, ky, kx) in the order of the weight tensor [N][C][3][3].  CTA z of a
-// split takes K steps [z ks, (z+1) ks) of 32 and writes its raw partial sums
-// to part[z][n][m]; conv_finish_kernel adds the partials in z order.  The
-// loader keeps one output pixel and 16 consecutive k per thread, so the
-// im2col index is stepped, not divided, per element; the input may be the
-// InstanceNorm output sc * r + sh of the previous layer's raw activation.
-struct ConvFwd {
-    const float *in;       // [B][C][S][S]
-    const float *sc, *sh;  // [B][C] affine map of the input, or null
-    const float *w;        // [N][C * 9]
-    float *part;           // [Z][N][M]
-    int C, S, So, N, M, Kd, ks;
+// ---- forward convolution on tcgen05 (implicit GEMM) ----
+// D[m][o] = sum_k im2col[m][k] W[o][k] for the output pixels m = (b, oy, ox)
+// of a 128-pixel tile (the MMA's M rows, TMEM lanes) and the output channels
+// o (N = NP >= Cout), K = 9 Cin.  Reduction order: (tap = 3 ky + kx, c) with c
+// fastest when Cin is a multiple of 8 (C8: an octet of k is 8 channels of one
+// tap, decoded once), else the weight tensor's own order (c, ky, kx).  Both
+// operands are single BF16 (the forward's precision) in the no-swizzle
+// K-major layout of wgrad_kernel: element (m, k) of a stage of kWK = 64 k at
+// byte (k / 8) * 16 * 128 + 16 m + 2 (k % 8), so a thread writes the 8 k of
+// one octet of its pixel as one 16-byte store (conflict-free across a warp's
+// consecutive pixels).  conv_wprep_kernel lays the weights out once per call
+// in exactly the stage layout of B (element (o, k) at byte (k / 8) * 16 NP +
+// 16 o + 2 (k % 8), zero for o >= Cout and k >= Kd), so a stage of B is a
+// contiguous copy.  CTA (tile, z) takes the stages [z ks, (z + 1) ks) and
+// writes its raw sums to part[z][o][m]; conv_finish_kernel adds the partials
+// in z order, the bias, LeakyReLU and the InstanceNorm statistics.  Two
+// stages in flight; every wait is bounded (NaN outputs and g_umma_timeouts
+// on expiry).
+struct ConvUmma {
+    const float *in;       // [B][Cin][S][S]
+    const float *sc, *sh;  // [B][Cin] affine map of the input (zero padding after it), or null
+    const uint4 *wb;       // BF16 weights in the stage layout (conv_wprep_kernel)
+    float *part;           // [Z][Cout][M]
+    int Cin, S, So, Cout, M, Kd, ks;  // ks: stages of 64 k per split
 };
 
-__global__ void __launch_bounds__(kGT) conv_fwd_kernel(const ConvFwd p)
+constexpr int kCT = 256;  // threads: pixel tid % 128, octets tid / 128 + 2 j of each stage
+__host__ __device__ constexpr int conv_stage_bytes(int NP) { return (128 + NP) * kWK * 2; }
+
+template <int NP, bool C8>
+__global__ void __launch_bounds__(kCT, 3) conv_umma_kernel(const ConvUmma p)
 {
-    pdl_enter();
-    __shared__ __align__(16) __nv_bfloat16 As[64][40];
-    __shared__ __align__(16) __nv_bfloat16 Bs[64][40];
-    const int m0 = blockIdx.x * 64, z = blockIdx.z;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int g = lane >> 2, t = lane & 3;
-    const int lr = tid >> 1, lk = (tid & 1) * 16;  // loader: tile row and first k
-    const int m = m0 + lr, P = p.So * p.So;
-    const bool mvalid = m < p.M, nvalid = lr < p.N;
+    static_assert(NP % 16 == 0 && NP >= 16 && NP <= 64, "N of an M = 128 MMA: 16 .. 64, multiple of 16");
+    constexpr uint32_t kCols = NP < 32 ? 32 : NP;
+    constexpr int kA = 128 * kWK * 2, kStage = conv_stage_bytes(NP);
+    constexpr uint32_t idesc = umma_idesc_bf16(128, NP);
+    extern __shared__ __align__(128) char csm[];  // stage i % 2: [A][B]
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t taddr_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = blockIdx.x, z = blockIdx.y;
+    const int P = p.So * p.So, S2 = p.S * p.S;
+    const int ml = tid & 127, m = tile * 128 + ml;
+    const bool mval = m < p.M;
     int b = 0, oy = 0, ox = 0;
-    if (mvalid) {
+    if (mval) {
         b = m / P;
         const int rr = m - b * P;
         oy = rr / p.So;
         ox = rr - oy * p.So;
     }
-    const int iy0 = 2 * oy - 1, ix0 = 2 * ox - 1;
-    const float *inb = p.in + static_cast<size_t>(b) * p.C * p.S * p.S;
-    const float *scb = p.sc ? p.sc + b * p.C : nullptr;
-    const float *shb = p.sh ? p.sh + b * p.C : nullptr;
-    const float *wrow = p.w + static_cast<size_t>(nvalid ? lr : 0) * p.Kd;
-    float acc[2][4][4];
+    const float *inb = p.in + static_cast<size_t>(b) * p.Cin * S2;
+    const float *scb = p.sc ? p.sc + b * p.Cin : nullptr;
+    const float *shb = p.sh ? p.sh + b * p.Cin : nullptr;
+    const int nko = (p.Kd + 7) / 8;
+    const int st_beg = z * p.ks, st_end = min(st_beg + p.ks, (p.Kd + kWK - 1) / kWK);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&taddr_s)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t taddr = taddr_s;
+    pdl_enter();  // the input and the prepared weights come from earlier kernels
+    bool ok = true;
+    for (int s = st_beg; s < st_end; ++s) {
+        const int i = s - st_beg, buf = i & 1;
+        char *stg = csm + buf * kStage;
+        if (i >= 2) ok = mbar_wait(smem_addr(&mbar[buf]), ((i - 2) >> 1) & 1) && ok;  // stage i - 2 read
+        const uint4 *wsrc = p.wb + static_cast<size_t>(s) * NP * 8;
+        for (int e = tid; e < NP * 8; e += kCT) reinterpret_cast<uint4 *>(stg + kA)[e] = __ldg(wsrc + e);
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 4; ++j) {
+            const int q = (tid >> 7) + 2 * j, k0 = s * kWK + 8 * q;
+            char *dst = stg + q * 16 * 128 + 16 * ml;
+            if (k0 >= p.Kd) {  // past the reduction: zeros (B is zero there too)
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+                continue;
+            }
+            float v[8];
+            if (C8) {
+                const int t = k0 / p.Cin, c0 = k0 - t * p.Cin, ky = t / 3, kx = t - 3 * ky;
+                const int iy = 2 * oy + ky - 1, ix = 2 * ox + kx - 1;
+                const bool in = mval && iy >= 0 && iy < p.S && ix >= 0 && ix < p.S;
+                const float *src = inb + static_cast<size_t>(c0) * S2 + iy * p.S + ix;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+                for (int u = 0; u < 8; ++u) v[u] = in ? __ldg(src + static_cast<size_t>(u) * S2) : 0.f;
+                if (scb && in) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    const int kbeg = z * p.ks * 32, kend = min(p.Kd, kbeg + p.ks * 32);
-    for (int k0 = kbeg; k0 < kend; k0 += 32) {
-        const int k = k0 + lk;
-        int c = k / 9, tt = k - c * 9, ky = tt / 3, kx = tt - ky * 3;
-        float va[16], vb[16];
+                    for (int u = 0; u < 8; ++u) v[u] = fmaf(v[u], __ldg(scb + c0 + u), __ldg(shb + c0 + u));
+                }
+            } else {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const bool kin = k + q < kend;
-            const int iy = iy0 + ky, ix = ix0 + kx;
-            const bool ok = mvalid && kin && static_cast<unsigned>(iy) < static_cast<unsigned>(p.S) &&
-                            static_cast<unsigned>(ix) < static_cast<unsigned>(p.S);
-            float v = ok ? __ldg(inb + (c * p.S + iy) * p.S + ix) : 0.f;
-            if (scb && ok) v = fmaf(v, __ldg(scb + c), __ldg(shb + c));
-            va[q] = v;
-            vb[q] = (nvalid && kin) ? __ldg(wrow + k + q) : 0.f;
-            if (++kx == 3) {
-                kx = 0;
-                if (++ky == 3) {
-                    ky = 0;
-                    ++c;
+                for (int u = 0; u < 8; ++u) {
+                    const int k = k0 + u, c = k / 9, tap = k - 9 * c, ky = tap / 3, kx = tap - 3 * ky;
+                    const int iy = 2 * oy + ky - 1, ix = 2 * ox + kx - 1;
+                    const bool in = mval && k < p.Kd && iy >= 0 && iy < p.S && ix >= 0 && ix < p.S;
+                    float x = in ? __ldg(inb + static_cast<size_t>(c) * S2 + iy * p.S + ix) : 0.f;
+                    if (scb && in) x = fmaf(x, __ldg(scb + c), __ldg(shb + c));
+                    v[u] = x;
                 }
             }
+            uint32_t h[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
+                h[u] = *reinterpret_cast<const uint32_t *>(&hh);
+            }
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
         }
-        uint4 pa[2], pb[2];
-        uint32_t *ua = reinterpret_cast<uint32_t *>(pa), *ub = reinterpret_cast<uint32_t *>(pb);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic stores -> tensor core
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t a0 = smem_addr(stg), b0 = a0 + kA;
+            const int nk = (min(8, nko - 8 * s) + 1) / 2;  // K steps of 16 holding live k
+            for (int kk = 0; kk < nk; ++kk)
+                umma_bf16(taddr, umma_sdesc(a0 + kk * 2 * 16 * 128, 16 * 128, 128),
+                          umma_sdesc(b0 + kk * 2 * 16 * NP, 16 * NP, 128), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_addr(&mbar[buf]))
+                         : "memory");
+        }
+    }
+    const int nst = st_end - st_beg;
+    if (nst > 0) ok = mbar_wait(smem_addr(&mbar[(nst - 1) & 1]), ((nst - 1) >> 1) & 1) && ok;  // all MMAs
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (!ok && lane == 0) atomicAdd(&g_umma_timeouts, 1u);
+    // epilogue: warp w holds pixels 32 (w % 4) + lane of the tile, channels of half w / 4
+    const int r = 32 * (warp & 3) + lane, mo = tile * 128 + r;
+    constexpr int kHalf = NP / 2;
+    const int cb = (warp >> 2) * kHalf;
+#pragma unroll
+    for (int c0 = 0; c0 < kHalf; c0 += 8) {
+        uint32_t v[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                     : "r"(taddr + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + cb + c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const __nv_bfloat162 ha = __floats2bfloat162_rn(va[2 * q], va[2 * q + 1]);
-            const __nv_bfloat162 hb = __floats2bfloat162_rn(vb[2 * q], vb[2 * q + 1]);
-            ua[q] = *reinterpret_cast<const uint32_t *>(&ha);
-            ub[q] = *reinterpret_cast<const uint32_t *>(&hb);
+            const int o = cb + c0 + q;
+            if (mo < p.M && o < p.Cout)
+                p.part[(static_cast<size_t>(z) * p.Cout + o) * p.M + mo] =
+                    ok ? __uint_as_float(v[q]) : __int_as_float(0x7fc00000);
         }
-        *reinterpret_cast<uint4 *>(&As[lr][lk]) = pa[0];
-        *reinterpret_cast<uint4 *>(&As[lr][lk + 8]) = pa[1];
-        *reinterpret_cast<uint4 *>(&Bs[lr][lk]) = pb[0];
-        *reinterpret_cast<uint4 *>(&Bs[lr][lk + 8]) = pb[1];
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 32; kk += 16) {
-            uint32_t a[2][4], bb[4][2];
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                const int r = wm + mi * 16 + g;
-                a[mi][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * t]);
-                a[mi][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * t]);
-                a[mi][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 8 + 2 * t]);
-                a[mi][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 8 + 2 * t]);
-            }
-#pragma unroll
-            for (int ni = 0; ni < 4; ++ni) {
-                const int n = wn + ni * 8 + g;
-                bb[ni][0] = *reinterpret_cast<const uint32_t *>(&Bs[n][kk + 2 * t]);
-                bb[ni][1] = *reinterpret_cast<const uint32_t *>(&Bs[n][kk + 8 + 2 * t]);
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], bb[ni]);
-        }
-        __syncthreads();
     }
-    float *pz = p.part + static_cast<size_t>(z) * p.N * p.M;
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int mm = m0 + wm + mi * 16 + g + (q >= 2 ? 8 : 0);
-                const int n = wn + ni * 8 + 2 * t + (q & 1);
-                if (mm < p.M && n < p.N) pz[static_cast<size_t>(n) * p.M + mm] = acc[mi][ni][q];
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(kCols));
+    }
+}
+
+// The five convolutions' weights as BF16 in the B stage layout of
+// conv_umma_kernel: element (o, k) of layer i at bf16 index (k / 8) * 8 NP +
+// 8 o + k % 8 for k < Kpad (whole 64-k stages), zero for o >= Cout or k >= Kd;
+// k in the kernel's reduction order ((tap, c) when Cin % 8 == 0, else (c, tap)).
+struct WPrep {
+    const float *w[5];
+    __nv_bfloat16 *out[5];
+    int start[6];  // flattened element ranges per layer
+    int cin[5], cout[5], np[5], kpad[5];
+};
+
+__global__ void conv_wprep_kernel(const WPrep p)
+{
+    pdl_enter();  // the outputs may still be read by the previous call's kernels
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.start[5]; e += gridDim.x * blockDim.x) {
+        int i = 0;
+        while (e >= p.start[i + 1]) ++i;
+        const int Cin = p.cin[i], Cout = p.cout[i], Kd = 9 * Cin, NP = p.np[i];
+        const int l = e - p.start[i], o = l / p.kpad[i], k = l - o * p.kpad[i];
+        float v = 0.f;
+        if (o < Cout && k < Kd) {
+            int c, tap;
+            if (Cin % 8 == 0) {
+                tap = k / Cin;
+                c = k - tap * Cin;
+            } else {
+                c = k / 9;
+                tap = k - 9 * c;
             }
+            v = p.w[i][(static_cast<size_t>(o) * Cin + c) * 9 + tap];
+        }
+        p.out[i][(k >> 3) * 8 * NP + 8 * o + (k & 7)] = __float2bfloat16_rn(v);
+    }
 }
 
 // ---- input gradient of the stride-2 3x3 convolution, by input parity ----
@@ -576,7 +661,7 @@ __global__ void __launch_bounds__(kGT) conv_fwd_kernel(const ConvFwd p)
 // m = (b, qy, qx), columns n = input channel and reduction k = (tap, o) over
 // its 1, 2 or 4 taps x Cout: none of the zero taps of the full 3x3 im2col is
 // loaded or multiplied.  Operands are split into BF16 hi + lo parts (three
-// MMAs, as in mma_gemm_kernel<true, ...>).
+// MMAs).
 struct DgradPar {
     const float *dz;  // [B][Cout][So][So]
     const float *w;   // [Cout][Cin][3][3]
@@ -768,23 +853,53 @@ __global__ void __launch_bounds__(512) conv_finish_kernel(const float *__restric
     }
 }
 
-// Launch of wgrad_kernel<NP> (opted into its dynamic shared memory once per
-// device).
+// Opts kernel fn into `bytes` of dynamic shared memory, once per device
+// (calls from several threads are serialised).
+static svdlut_status smem_opt_in(const void *fn, int bytes)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<int, const void *>> done;
+    int dev = 0;
+    SVDLUT_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    for (const auto &e : done)
+        if (e.first == dev && e.second == fn) return SVDLUT_OK;
+    SVDLUT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.emplace_back(dev, fn);
+    return SVDLUT_OK;
+}
+
 template <int NP>
 static svdlut_status launch_wgrad(const WgradArgs &a, int tiles, int chunks, cudaStream_t s)
 {
     constexpr int smem = 2 * wgrad_stage_bytes(NP);
-    static std::atomic<unsigned long long> opted{0};
-    int dev = 0;
-    SVDLUT_CUDA_TRY(cudaGetDevice(&dev));
-    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
-    if (!bit || !(opted.load() & bit)) {
-        SVDLUT_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        opted.fetch_or(bit);
-    }
+    const svdlut_status st = smem_opt_in(reinterpret_cast<const void *>(wgrad_kernel<NP>), smem);
+    if (st != SVDLUT_OK) return st;
     wgrad_kernel<NP><<<dim3(tiles, chunks), kWT, smem, s>>>(a);
     SVDLUT_CUDA_TRY(cudaGetLastError());
     return SVDLUT_OK;
+}
+
+// Launch of conv_umma_kernel<NP, C8> as a programmatic dependent of the
+// kernel before it.
+template <int NP, bool C8>
+static svdlut_status launch_conv_t(const ConvUmma &a, dim3 grid, cudaStream_t s)
+{
+    constexpr int smem = 2 * conv_stage_bytes(NP);
+    const svdlut_status st = smem_opt_in(reinterpret_cast<const void *>(conv_umma_kernel<NP, C8>), smem);
+    if (st != SVDLUT_OK) return st;
+    return launch_pdl(conv_umma_kernel<NP, C8>, grid, dim3(kCT), smem, s, a);
+}
+static svdlut_status launch_conv(const ConvUmma &a, int Z, cudaStream_t s)
+{
+    const dim3 grid((a.M + 127) / 128, Z);
+    const int np = wgrad_np(a.Cout);
+    if (a.Cin % 8 != 0) {
+        if (np == 16) return launch_conv_t<16, false>(a, grid, s);
+        return fail(SVDLUT_ERR_UNSUPPORTED, "convolution with %d inputs and %d outputs", a.Cin, a.Cout);
+    }
+    return np == 16 ? launch_conv_t<16, true>(a, grid, s)
+                    : np == 32 ? launch_conv_t<32, true>(a, grid, s) : launch_conv_t<64, true>(a, grid, s);
 }
 
 // Fixed-order block sum (256 threads); every thread gets the total.
@@ -1173,15 +1288,30 @@ extern "C" svdlut_status svdlut_generator_forward(int K, const float *weights, i
     if ((st = launch_pdl(downsample_kernel, dim3(static_cast<int>((static_cast<size_t>(B) * 3 * kThumb * kThumb + 255) / 256)),
                          dim3(256), 0, s, x, B, H, W, w + wl.thumb)) != SVDLUT_OK)
         return st;
+    {  // the convolutions' weights in the tensor cores' B layout
+        WPrep wp{};
+        int e = 0;
+        for (int i = 0; i < 5; ++i) {
+            wp.w[i] = weights + L.conv_w[i];
+            wp.out[i] = reinterpret_cast<__nv_bfloat16 *>(w + wl.wbf[i]);
+            wp.cin[i] = kCh[i];
+            wp.cout[i] = kCh[i + 1];
+            wp.np[i] = wgrad_np(kCh[i + 1]);
+            wp.kpad[i] = conv_stages(i) * 64;
+            wp.start[i] = e;
+            e += static_cast<int>(conv_wbf_elems(i));
+        }
+        wp.start[5] = e;
+        if ((st = launch_pdl(conv_wprep_kernel, dim3((e + 255) / 256), dim3(256), 0, s, wp)) != SVDLUT_OK) return st;
+    }
     const float *in = w + wl.thumb, *isc = nullptr, *ish = nullptr;
     for (int i = 0; i < 5; ++i) {
         const int Cin = kCh[i], Cout = kCh[i + 1], S = kSz[i], So = kSz[i + 1];
-        const int M = B * So * So, Kd = Cin * 9;
-        const int ks = fwd_ksteps(i, fwd_split(B, i)), Z = ((Kd + 31) / 32 + ks - 1) / ks;
+        const int M = B * So * So, Kd = Cin * 9, Z = conv_split(B, i);
         float *r = w + wl.r[i];
-        if ((st = launch_pdl(conv_fwd_kernel, dim3((M + 63) / 64, 1, Z), dim3(kGT), 0, s,
-                             ConvFwd{in, isc, ish, weights + L.conv_w[i], w + wl.part, Cin, S, So, Cout, M, Kd, ks})) !=
-            SVDLUT_OK)
+        if ((st = launch_conv(ConvUmma{in, isc, ish, reinterpret_cast<const uint4 *>(w + wl.wbf[i]), w + wl.part, Cin,
+                                       S, So, Cout, M, Kd, conv_ks(B, i)},
+                              Z, s)) != SVDLUT_OK)
             return st;
         const bool norm = i < 4;
         if ((st = launch_pdl(conv_finish_kernel, dim3(B * Cout), dim3(512), 0, s, static_cast<const float *>(w + wl.part),
