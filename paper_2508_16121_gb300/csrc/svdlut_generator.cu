@@ -73,7 +73,7 @@ inline Layout make_layout(int K)
 // backward temporaries.  InstanceNorm is not materialised: the layer after it
 // reads r[i] and applies the per-(b, c) affine map sc * r + sh on load.
 struct WsLayout {
-    size_t thumb, r[5], mean[4], rstd[4], sc[4], sh[4], part, wbf[5], rho, hidden;
+    size_t thumb, r[5], mean[4], rstd[4], sc[4], sh[4], part, wbf[5], tstat, rho, hidden;
     size_t dz[2], dact, wpart, dhid, drho, insum;
     size_t total;
 };
@@ -141,6 +141,10 @@ inline WsLayout make_ws(int B)
     for (int i = 0; i < 5; ++i) pp = std::max(pp, static_cast<size_t>(conv_split(B, i)) * act_size(B, i));
     w.part = take(pp);
     for (int i = 0; i < 5; ++i) w.wbf[i] = take((conv_wbf_elems(i) + 1) / 2);
+    size_t ts = 0;  // per-tile statistics of the layers with the fused finish
+    for (int i = 0; i < 4; ++i)
+        ts = std::max(ts, static_cast<size_t>((B * kSz[i + 1] * kSz[i + 1] + 127) / 128) * kCh[i + 1] * 2);
+    w.tstat = take(ts);
     w.rho = take(static_cast<size_t>(B) * kRho);
     w.hidden = take(static_cast<size_t>(B) * 4 * kHidden);
     const size_t amax = act_size(B, 0);
@@ -164,22 +168,38 @@ inline WsLayout make_ws(int B)
 // Bilinear downsample to 256x256 with half-pixel centres, no antialiasing.
 __global__ void downsample_kernel(const float *__restrict__ x, int B, int H, int W, float *__restrict__ t)
 {
+    static_assert(kThumb % 4 == 0, "four outputs of one thumbnail row per thread");
     pdl_enter();
-    const size_t n = static_cast<size_t>(B) * 3 * kThumb * kThumb;
+    const size_t n4 = static_cast<size_t>(B) * 3 * kThumb * kThumb / 4;
     const float sy_ = static_cast<float>(H) / kThumb, sx_ = static_cast<float>(W) / kThumb;
-    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
-         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int ox = static_cast<int>(e % kThumb), oy = static_cast<int>((e / kThumb) % kThumb);
+    for (size_t e4 = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e4 < n4;
+         e4 += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const size_t e = 4 * e4;
+        const int ox0 = static_cast<int>(e % kThumb), oy = static_cast<int>((e / kThumb) % kThumb);
         const size_t bc = e / (kThumb * kThumb);
-        float sy = fminf(fmaxf((oy + 0.5f) * sy_ - 0.5f, 0.f), static_cast<float>(H - 1));
-        float sx = fminf(fmaxf((ox + 0.5f) * sx_ - 0.5f, 0.f), static_cast<float>(W - 1));
-        const int y0 = static_cast<int>(sy), x0 = static_cast<int>(sx);
-        const int y1 = min(y0 + 1, H - 1), x1 = min(x0 + 1, W - 1);
-        const float fy = sy - y0, fx = sx - x0;
-        const float *p = x + bc * H * W;
-        const float top = (1.f - fx) * __ldg(p + static_cast<size_t>(y0) * W + x0) + fx * __ldg(p + static_cast<size_t>(y0) * W + x1);
-        const float bot = (1.f - fx) * __ldg(p + static_cast<size_t>(y1) * W + x0) + fx * __ldg(p + static_cast<size_t>(y1) * W + x1);
-        t[e] = (1.f - fy) * top + fy * bot;
+        const float sy = fminf(fmaxf((oy + 0.5f) * sy_ - 0.5f, 0.f), static_cast<float>(H - 1));
+        const int y0 = static_cast<int>(sy), y1 = min(y0 + 1, H - 1);
+        const float fy = sy - y0;
+        const float *r0 = x + (bc * H + y0) * W, *r1 = x + (bc * H + y1) * W;
+        float v[4][4], fx[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {  // every load of the four outputs first
+            const float sx = fminf(fmaxf((ox0 + u + 0.5f) * sx_ - 0.5f, 0.f), static_cast<float>(W - 1));
+            const int x0 = static_cast<int>(sx), x1 = min(x0 + 1, W - 1);
+            fx[u] = sx - x0;
+            v[u][0] = __ldg(r0 + x0);
+            v[u][1] = __ldg(r0 + x1);
+            v[u][2] = __ldg(r1 + x0);
+            v[u][3] = __ldg(r1 + x1);
+        }
+        float o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float top = (1.f - fx[u]) * v[u][0] + fx[u] * v[u][1];
+            const float bot = (1.f - fx[u]) * v[u][2] + fx[u] * v[u][3];
+            o[u] = (1.f - fy) * top + fy * bot;
+        }
+        *reinterpret_cast<float4 *>(t + e) = make_float4(o[0], o[1], o[2], o[3]);
     }
 }
 
@@ -460,8 +480,9 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
 // D[m][o] = sum_k im2col[m][k] W[o][k] for the output pixels m = (b, oy, ox)
 // of a 128-pixel tile (the MMA's M rows, TMEM lanes) and the output channels
 // o (N = NP >= Cout), K = 9 Cin.  Reduction order: (tap = 3 ky + kx, c) with c
-// fastest when Cin is a multiple of 8 (C8: an octet of k is 8 channels of one
-// tap, decoded once), else the weight tensor's own order (c, ky, kx).  Both
+// fastest when Cin is a power of two >= 8 (C8: an octet of k is 8 channels of
+// one tap, decoded once by shift and mask), else (the first layer, Cin = 3)
+// the weight tensor's own order (c, ky, kx), decoded at compile time.  Both
 // operands are single BF16 (the forward's precision) in the no-swizzle
 // K-major layout of wgrad_kernel: element (m, k) of a stage of kWK = 64 k at
 // byte (k / 8) * 16 * 128 + 16 m + 2 (k % 8), so a thread writes the 8 k of
@@ -474,25 +495,42 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
 // in z order, the bias, LeakyReLU and the InstanceNorm statistics.  Two
 // stages in flight; every wait is bounded (NaN outputs and g_umma_timeouts
 // on expiry).
+// sum over the 32 lanes (butterfly: every lane gets the same total)
+__device__ __forceinline__ float warp_total(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 struct ConvUmma {
     const float *in;       // [B][Cin][S][S]
     const float *sc, *sh;  // [B][Cin] affine map of the input (zero padding after it), or null
     const uint4 *wb;       // BF16 weights in the stage layout (conv_wprep_kernel)
     float *part;           // [Z][Cout][M]
     int Cin, S, So, Cout, M, Kd, ks;  // ks: stages of 64 k per split
+    // fused finish (one split, So^2 a multiple of 128, r set): the epilogue
+    // writes r = LeakyReLU(D + bias) and the tile's per-channel sum and M2
+    const float *bias;  // [Cout]
+    float *r;           // [B][Cout][So][So], or null: raw sums to part
+    float *tstat;       // [tiles][Cout][2]
 };
 
-constexpr int kCT = 256;  // threads: pixel tid % 128, octets tid / 128 + 2 j of each stage
+// NT threads (128 or 256): thread t keeps pixel t % 128 of the tile and the
+// octets t / 128 + (NT / 128) j of each stage; NBUF stage buffers (1 or 2).
+// The narrow layers take 128 threads, so that more CTAs (tiles in flight)
+// fit on an SM.
 __host__ __device__ constexpr int conv_stage_bytes(int NP) { return (128 + NP) * kWK * 2; }
 
-template <int NP, bool C8>
-__global__ void __launch_bounds__(kCT, 3) conv_umma_kernel(const ConvUmma p)
+template <int NP, bool C8, int NT, int NBUF>
+__global__ void __launch_bounds__(NT, NT == 128 ? 8 : (NP == 64 ? 2 : 3)) conv_umma_kernel(const ConvUmma p)
 {
     static_assert(NP % 16 == 0 && NP >= 16 && NP <= 64, "N of an M = 128 MMA: 16 .. 64, multiple of 16");
+    static_assert((NT == 128 || NT == 256) && (NBUF == 1 || NBUF == 2), "128 or 256 threads, 1 or 2 stages");
     constexpr uint32_t kCols = NP < 32 ? 32 : NP;
     constexpr int kA = 128 * kWK * 2, kStage = conv_stage_bytes(NP);
     constexpr uint32_t idesc = umma_idesc_bf16(128, NP);
-    extern __shared__ __align__(128) char csm[];  // stage i % 2: [A][B]
+    extern __shared__ __align__(128) char csm[];  // stage i % NBUF: [A][B]
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t taddr_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -510,6 +548,18 @@ __global__ void __launch_bounds__(kCT, 3) conv_umma_kernel(const ConvUmma p)
     const float *inb = p.in + static_cast<size_t>(b) * p.Cin * S2;
     const float *scb = p.sc ? p.sc + b * p.Cin : nullptr;
     const float *shb = p.sh ? p.sh + b * p.Cin : nullptr;
+    static_assert(C8 || NT == 128, "the first layer's element decode needs q = j (128 threads)");
+    const int cin_lg = 31 - __clz(p.Cin);
+    int roff[3], xoff[3];  // first layer: input row offset and column of tap ky / kx, and whether inside
+    bool vy[3], vx[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const int iy = 2 * oy + t - 1, ix = 2 * ox + t - 1;
+        vy[t] = iy >= 0 && iy < p.S;
+        vx[t] = ix >= 0 && ix < p.S;
+        roff[t] = iy * p.S;
+        xoff[t] = ix;
+    }
     const int nko = (p.Kd + 7) / 8;
     const int st_beg = z * p.ks, st_end = min(st_beg + p.ks, (p.Kd + kWK - 1) / kWK);
     if (warp == 0) {
@@ -529,38 +579,46 @@ __global__ void __launch_bounds__(kCT, 3) conv_umma_kernel(const ConvUmma p)
     pdl_enter();  // the input and the prepared weights come from earlier kernels
     bool ok = true;
     for (int s = st_beg; s < st_end; ++s) {
-        const int i = s - st_beg, buf = i & 1;
+        const int i = s - st_beg, buf = i % NBUF;
         char *stg = csm + buf * kStage;
-        if (i >= 2) ok = mbar_wait(smem_addr(&mbar[buf]), ((i - 2) >> 1) & 1) && ok;  // stage i - 2 read
+        if (i >= NBUF) ok = mbar_wait(smem_addr(&mbar[buf]), ((i - NBUF) / NBUF) & 1) && ok;  // stage i - NBUF read
         const uint4 *wsrc = p.wb + static_cast<size_t>(s) * NP * 8;
-        for (int e = tid; e < NP * 8; e += kCT) reinterpret_cast<uint4 *>(stg + kA)[e] = __ldg(wsrc + e);
+        for (int e = tid; e < NP * 8; e += NT) reinterpret_cast<uint4 *>(stg + kA)[e] = __ldg(wsrc + e);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int q = (tid >> 7) + 2 * j, k0 = s * kWK + 8 * q;
+        for (int j = 0; j < 8 * 128 / NT; ++j) {
+            const int q = (tid >> 7) + (NT / 128) * j, k0 = s * kWK + 8 * q;
             char *dst = stg + q * 16 * 128 + 16 * ml;
             if (k0 >= p.Kd) {  // past the reduction: zeros (B is zero there too)
                 *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
                 continue;
             }
             float v[8];
-            if (C8) {
-                const int t = k0 / p.Cin, c0 = k0 - t * p.Cin, ky = t / 3, kx = t - 3 * ky;
+            if constexpr (C8) {
+                // Cin a power of two: tap and first channel by shift and mask
+                const int t = k0 >> cin_lg, c0 = k0 & (p.Cin - 1), ky = t / 3, kx = t - 3 * ky;
                 const int iy = 2 * oy + ky - 1, ix = 2 * ox + kx - 1;
                 const bool in = mval && iy >= 0 && iy < p.S && ix >= 0 && ix < p.S;
                 const float *src = inb + static_cast<size_t>(c0) * S2 + iy * p.S + ix;
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[u] = in ? __ldg(src + static_cast<size_t>(u) * S2) : 0.f;
                 if (scb && in) {
+                    const float4 a0 = __ldg(reinterpret_cast<const float4 *>(scb + c0)),
+                                 a1 = __ldg(reinterpret_cast<const float4 *>(scb + c0) + 1);
+                    const float4 h0 = __ldg(reinterpret_cast<const float4 *>(shb + c0)),
+                                 h1 = __ldg(reinterpret_cast<const float4 *>(shb + c0) + 1);
+                    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float h[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = fmaf(v[u], __ldg(scb + c0 + u), __ldg(shb + c0 + u));
+                    for (int u = 0; u < 8; ++u) v[u] = fmaf(v[u], a[u], h[u]);
                 }
             } else {
+                // the first layer (Cin = 3, one stage, q = j): k = 9 c + 3 ky + kx
+                // is a constant per unrolled element
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const int k = k0 + u, c = k / 9, tap = k - 9 * c, ky = tap / 3, kx = tap - 3 * ky;
-                    const int iy = 2 * oy + ky - 1, ix = 2 * ox + kx - 1;
-                    const bool in = mval && k < p.Kd && iy >= 0 && iy < p.S && ix >= 0 && ix < p.S;
-                    float x = in ? __ldg(inb + static_cast<size_t>(c) * S2 + iy * p.S + ix) : 0.f;
+                    const int k = 8 * j + u, c = k / 9, ky = (k % 9) / 3, kx = k % 3;
+                    const bool in = k < 27 && mval && vy[ky] && vx[kx];
+                    float x = in ? __ldg(inb + c * S2 + roff[ky] + xoff[kx]) : 0.f;
                     if (scb && in) x = fmaf(x, __ldg(scb + c), __ldg(shb + c));
                     v[u] = x;
                 }
@@ -588,13 +646,64 @@ __global__ void __launch_bounds__(kCT, 3) conv_umma_kernel(const ConvUmma p)
         }
     }
     const int nst = st_end - st_beg;
-    if (nst > 0) ok = mbar_wait(smem_addr(&mbar[(nst - 1) & 1]), ((nst - 1) >> 1) & 1) && ok;  // all MMAs
+    if (nst > 0) ok = mbar_wait(smem_addr(&mbar[(nst - 1) % NBUF]), ((nst - 1) / NBUF) & 1) && ok;  // all MMAs
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     if (!ok && lane == 0) atomicAdd(&g_umma_timeouts, 1u);
-    // epilogue: warp w holds pixels 32 (w % 4) + lane of the tile, channels of half w / 4
+    // epilogue: warp w holds pixels 32 (w % 4) + lane of the tile and, of
+    // the NP channels, the kHalf from (w / 4) kHalf (kHalf = NP with 128 threads)
     const int r = 32 * (warp & 3) + lane, mo = tile * 128 + r;
-    constexpr int kHalf = NP / 2;
+    constexpr int kHalf = NP * 128 / NT;
     const int cb = (warp >> 2) * kHalf;
+    if (p.r) {
+        // fused finish: the tile lies in one image b; per channel the tile's
+        // sum (fixed order: warps, then the four warps of a half) and its M2
+        // about the tile mean (conv_stats_kernel combines the tiles)
+        __shared__ float red[2][4][NP];
+        const int bimg = (tile * 128) / P, rr = mo - bimg * P;
+        float x[kHalf];
+#pragma unroll
+        for (int c0 = 0; c0 < kHalf; c0 += 8) {
+            uint32_t v[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7])
+                         : "r"(taddr + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + cb + c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int o = cb + c0 + q;
+                float y = 0.f;
+                if (o < p.Cout) {
+                    y = __uint_as_float(v[q]) + __ldg(p.bias + o);
+                    y = y > 0.f ? y : kSlope * y;
+                    if (!ok) y = __int_as_float(0x7fc00000);
+                    p.r[(static_cast<size_t>(bimg) * p.Cout + o) * P + rr] = y;
+                }
+                x[c0 + q] = y;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kHalf; ++c) {
+            if (cb + c >= p.Cout) break;  // padding channels (uniform per warp)
+            const float t = warp_total(x[c]);
+            if (lane == 0) red[0][warp & 3][cb + c] = t;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < kHalf; ++c) {
+            const int o = cb + c;
+            if (o >= p.Cout) break;
+            const float mt = (((red[0][0][o] + red[0][1][o]) + red[0][2][o]) + red[0][3][o]) * (1.f / 128.f);
+            const float d = x[c] - mt, t = warp_total(d * d);
+            if (lane == 0) red[1][warp & 3][o] = t;
+        }
+        __syncthreads();
+        if (tid < p.Cout) {
+            float *e = p.tstat + (static_cast<size_t>(tile) * p.Cout + tid) * 2;
+            e[0] = ((red[0][0][tid] + red[0][1][tid]) + red[0][2][tid]) + red[0][3][tid];
+            e[1] = ((red[1][0][tid] + red[1][1][tid]) + red[1][2][tid]) + red[1][3][tid];
+        }
+    } else {
 #pragma unroll
     for (int c0 = 0; c0 < kHalf; c0 += 8) {
         uint32_t v[8];
@@ -610,6 +719,7 @@ __global__ void __launch_bounds__(kCT, 3) conv_umma_kernel(const ConvUmma p)
                     ok ? __uint_as_float(v[q]) : __int_as_float(0x7fc00000);
         }
     }
+    }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
     if (warp == 0) {
@@ -621,7 +731,8 @@ __global__ void __launch_bounds__(kCT, 3) conv_umma_kernel(const ConvUmma p)
 // The five convolutions' weights as BF16 in the B stage layout of
 // conv_umma_kernel: element (o, k) of layer i at bf16 index (k / 8) * 8 NP +
 // 8 o + k % 8 for k < Kpad (whole 64-k stages), zero for o >= Cout or k >= Kd;
-// k in the kernel's reduction order ((tap, c) when Cin % 8 == 0, else (c, tap)).
+// k in the kernel's reduction order ((tap, c) when Cin is a power of two >= 8,
+// else (c, tap)).
 struct WPrep {
     const float *w[5];
     __nv_bfloat16 *out[5];
@@ -640,7 +751,7 @@ __global__ void conv_wprep_kernel(const WPrep p)
         float v = 0.f;
         if (o < Cout && k < Kd) {
             int c, tap;
-            if (Cin % 8 == 0) {
+            if (Cin >= 8 && (Cin & (Cin - 1)) == 0) {
                 tap = k / Cin;
                 c = k - tap * Cin;
             } else {
@@ -794,23 +905,25 @@ __device__ __forceinline__ float block_sum(float v, float *red)
     return s;
 }
 
-// One CTA per (b, n) plane of conv i: r = LeakyReLU(sum_z part + bias); with
+// One CTA of NT threads per (b, n) plane of conv i (the layers whose K is
+// split): r = LeakyReLU(sum_z part + bias); with
 // gam set, also the InstanceNorm statistics of the plane (two passes, biased
 // variance) and its affine map sc = gamma rstd, sh = beta - mean sc.
-__global__ void __launch_bounds__(512) conv_finish_kernel(const float *__restrict__ part, int Z, int N, int M, int P,
-                                                          const float *__restrict__ bias, float *__restrict__ r,
-                                                          const float *gam, const float *bet, float *mean, float *rstd,
-                                                          float *sc, float *sh)
+template <int NT>
+__global__ void __launch_bounds__(NT) conv_finish_kernel(const float *__restrict__ part, int Z, int N, int M, int P,
+                                                         const float *__restrict__ bias, float *__restrict__ r,
+                                                         const float *gam, const float *bet, float *mean, float *rstd,
+                                                         float *sc, float *sh)
 {
     pdl_enter();
-    __shared__ float red[16];
+    __shared__ float red[NT / 32];
     const int bn = blockIdx.x, b = bn / N, n = bn - b * N;
     const float *src = part + static_cast<size_t>(n) * M + static_cast<size_t>(b) * P;
     const size_t zs = static_cast<size_t>(N) * M;
     float *dst = r + static_cast<size_t>(bn) * P;
     const float bi = __ldg(bias + n);
     float s = 0.f;
-    for (int i0 = threadIdx.x; i0 < P; i0 += 4 * 512) {
+    for (int i0 = threadIdx.x; i0 < P; i0 += 4 * NT) {
         // four pixels, partials taken 8 slices at a time with every load
         // issued before the (in-order) sums
         float v[4] = {0.f, 0.f, 0.f, 0.f};
@@ -820,7 +933,7 @@ __global__ void __launch_bounds__(512) conv_finish_kernel(const float *__restric
             for (int zz = 0; zz < 8; ++zz)
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    t[zz][u] = z0 + zz < Z && i0 + u * 512 < P ? src[(z0 + zz) * zs + i0 + u * 512] : 0.f;
+                    t[zz][u] = z0 + zz < Z && i0 + u * NT < P ? src[(z0 + zz) * zs + i0 + u * NT] : 0.f;
 #pragma unroll
             for (int zz = 0; zz < 8; ++zz)
 #pragma unroll
@@ -828,28 +941,70 @@ __global__ void __launch_bounds__(512) conv_finish_kernel(const float *__restric
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            if (i0 + u * 512 >= P) break;
+            if (i0 + u * NT >= P) break;
             float x = v[u] + bi;
             x = x > 0.f ? x : kSlope * x;
-            dst[i0 + u * 512] = x;
+            dst[i0 + u * NT] = x;
             s += x;
         }
     }
     if (!gam) return;
-    const float mu = block_sum<16>(s, red) / P;
+    const float mu = block_sum<NT / 32>(s, red) / P;
     float q = 0.f;
 #pragma unroll 4
-    for (int i = threadIdx.x; i < P; i += 512) {
+    for (int i = threadIdx.x; i < P; i += NT) {
         const float d = dst[i] - mu;
         q = fmaf(d, d, q);
     }
-    const float var = block_sum<16>(q, red) / P;
+    const float var = block_sum<NT / 32>(q, red) / P;
     if (threadIdx.x == 0) {
         const float rs = rsqrtf(var + kEps), gs = rs * gam[n];
         mean[bn] = mu;
         rstd[bn] = rs;
         sc[bn] = gs;
         sh[bn] = bet[n] - mu * gs;
+    }
+}
+
+// InstanceNorm statistics of a convolution with the fused finish: one warp
+// per (b, o) plane merges the per-tile (count 128, sum, M2) of image b in a
+// fixed order (lane l takes tiles [l T / 32, (l + 1) T / 32) in order, then a
+// pairwise tree over the lanes; Chan, Golub and LeVeque's update for a
+// union: mean += d nB / n, M2 += M2B + d^2 nA nB / n), then writes mean,
+// rstd (biased variance) and the affine map sc = gamma rstd, sh = beta - mean sc.
+__global__ void conv_stats_kernel(const float *__restrict__ tstat, int B, int Cout, int tpi, int P,
+                                  const float *__restrict__ gam, const float *__restrict__ bet, float *mean,
+                                  float *rstd, float *sc, float *sh)
+{
+    pdl_enter();
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (wid >= B * Cout) return;
+    const int b = wid / Cout, o = wid - b * Cout;
+    float n = 0.f, mu = 0.f, m2 = 0.f;
+    auto merge = [&](float nb, float mb, float m2b) {
+        if (nb == 0.f) return;
+        const float nn = n + nb, d = mb - mu, f = nb / nn;
+        m2 = m2 + m2b + d * d * n * f;
+        mu = fmaf(d, f, mu);
+        n = nn;
+    };
+    for (int t = lane * tpi / 32; t < (lane + 1) * tpi / 32; ++t) {
+        const float *e = tstat + (static_cast<size_t>(b) * tpi + t) * Cout * 2 + 2 * o;
+        merge(128.f, e[0] * (1.f / 128.f), e[1]);
+    }
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const float nb = __shfl_down_sync(0xffffffffu, n, s), mb = __shfl_down_sync(0xffffffffu, mu, s),
+                    m2b = __shfl_down_sync(0xffffffffu, m2, s);
+        if ((lane & (2 * s - 1)) == 0) merge(nb, mb, m2b);
+    }
+    if (lane == 0) {
+        const float var = m2 / static_cast<float>(P);
+        const float rs = rsqrtf(var + kEps), gs = rs * gam[o];
+        mean[wid] = mu;
+        rstd[wid] = rs;
+        sc[wid] = gs;
+        sh[wid] = bet[o] - mu * gs;
     }
 }
 
@@ -882,24 +1037,25 @@ static svdlut_status launch_wgrad(const WgradArgs &a, int tiles, int chunks, cud
 
 // Launch of conv_umma_kernel<NP, C8> as a programmatic dependent of the
 // kernel before it.
-template <int NP, bool C8>
+template <int NP, bool C8, int NT, int NBUF>
 static svdlut_status launch_conv_t(const ConvUmma &a, dim3 grid, cudaStream_t s)
 {
-    constexpr int smem = 2 * conv_stage_bytes(NP);
-    const svdlut_status st = smem_opt_in(reinterpret_cast<const void *>(conv_umma_kernel<NP, C8>), smem);
+    constexpr int smem = NBUF * conv_stage_bytes(NP);
+    const svdlut_status st = smem_opt_in(reinterpret_cast<const void *>(conv_umma_kernel<NP, C8, NT, NBUF>), smem);
     if (st != SVDLUT_OK) return st;
-    return launch_pdl(conv_umma_kernel<NP, C8>, grid, dim3(kCT), smem, s, a);
+    return launch_pdl(conv_umma_kernel<NP, C8, NT, NBUF>, grid, dim3(NT), smem, s, a);
 }
 static svdlut_status launch_conv(const ConvUmma &a, int Z, cudaStream_t s)
 {
     const dim3 grid((a.M + 127) / 128, Z);
     const int np = wgrad_np(a.Cout);
-    if (a.Cin % 8 != 0) {
-        if (np == 16) return launch_conv_t<16, false>(a, grid, s);
+    if ((a.Cin & (a.Cin - 1)) != 0 || a.Cin < 8) {
+        // the first layer: 27 k, one stage, one buffer
+        if (np == 16 && a.Cin == 3) return launch_conv_t<16, false, 128, 1>(a, grid, s);
         return fail(SVDLUT_ERR_UNSUPPORTED, "convolution with %d inputs and %d outputs", a.Cin, a.Cout);
     }
-    return np == 16 ? launch_conv_t<16, true>(a, grid, s)
-                    : np == 32 ? launch_conv_t<32, true>(a, grid, s) : launch_conv_t<64, true>(a, grid, s);
+    return np == 16 ? launch_conv_t<16, true, 128, 2>(a, grid, s)
+                    : np == 32 ? launch_conv_t<32, true, 256, 2>(a, grid, s) : launch_conv_t<64, true, 256, 2>(a, grid, s);
 }
 
 // Fixed-order block sum (256 threads); every thread gets the total.
@@ -1285,7 +1441,7 @@ extern "C" svdlut_status svdlut_generator_forward(int K, const float *weights, i
     const WsLayout wl = make_ws(B);
     float *w = static_cast<float *>(ws);
     // a chain of small kernels, each a programmatic dependent launch of the one before
-    if ((st = launch_pdl(downsample_kernel, dim3(static_cast<int>((static_cast<size_t>(B) * 3 * kThumb * kThumb + 255) / 256)),
+    if ((st = launch_pdl(downsample_kernel, dim3(static_cast<int>((static_cast<size_t>(B) * 3 * kThumb * kThumb / 4 + 255) / 256)),
                          dim3(256), 0, s, x, B, H, W, w + wl.thumb)) != SVDLUT_OK)
         return st;
     {  // the convolutions' weights in the tensor cores' B layout
@@ -1307,19 +1463,30 @@ extern "C" svdlut_status svdlut_generator_forward(int K, const float *weights, i
     const float *in = w + wl.thumb, *isc = nullptr, *ish = nullptr;
     for (int i = 0; i < 5; ++i) {
         const int Cin = kCh[i], Cout = kCh[i + 1], S = kSz[i], So = kSz[i + 1];
-        const int M = B * So * So, Kd = Cin * 9, Z = conv_split(B, i);
+        const int M = B * So * So, Kd = Cin * 9, Z = conv_split(B, i), P = So * So;
         float *r = w + wl.r[i];
+        const bool norm = i < 4, fuse = norm && Z == 1 && P % 128 == 0;
+        const float *gam = norm ? weights + L.in_g[i] : nullptr, *bet = norm ? weights + L.in_b[i] : nullptr;
+        float *mean = norm ? w + wl.mean[i] : nullptr, *rstd = norm ? w + wl.rstd[i] : nullptr;
+        float *scn = norm ? w + wl.sc[i] : nullptr, *shn = norm ? w + wl.sh[i] : nullptr;
         if ((st = launch_conv(ConvUmma{in, isc, ish, reinterpret_cast<const uint4 *>(w + wl.wbf[i]), w + wl.part, Cin,
-                                       S, So, Cout, M, Kd, conv_ks(B, i)},
+                                       S, So, Cout, M, Kd, conv_ks(B, i), weights + L.conv_b[i], fuse ? r : nullptr,
+                                       w + wl.tstat},
                               Z, s)) != SVDLUT_OK)
             return st;
-        const bool norm = i < 4;
-        if ((st = launch_pdl(conv_finish_kernel, dim3(B * Cout), dim3(512), 0, s, static_cast<const float *>(w + wl.part),
-                             Z, Cout, M, So * So, weights + L.conv_b[i], r,
-                             norm ? weights + L.in_g[i] : nullptr, norm ? weights + L.in_b[i] : nullptr,
-                             norm ? w + wl.mean[i] : nullptr, norm ? w + wl.rstd[i] : nullptr,
-                             norm ? w + wl.sc[i] : nullptr, norm ? w + wl.sh[i] : nullptr)) != SVDLUT_OK)
-            return st;
+        if (fuse) {
+            st = launch_pdl(conv_stats_kernel, dim3((B * Cout * 32 + 255) / 256), dim3(256), 0, s,
+                            static_cast<const float *>(w + wl.tstat), B, Cout, P / 128, P, gam, bet, mean, rstd, scn, shn);
+        } else {
+            const float *part = w + wl.part, *bias = weights + L.conv_b[i];
+            st = P >= 4096 ? launch_pdl(conv_finish_kernel<512>, dim3(B * Cout), dim3(512), 0, s, part, Z, Cout, M, P,
+                                        bias, r, gam, bet, mean, rstd, scn, shn)
+               : P >= 1024 ? launch_pdl(conv_finish_kernel<256>, dim3(B * Cout), dim3(256), 0, s, part, Z, Cout, M, P,
+                                        bias, r, gam, bet, mean, rstd, scn, shn)
+                           : launch_pdl(conv_finish_kernel<64>, dim3(B * Cout), dim3(64), 0, s, part, Z, Cout, M, P,
+                                        bias, r, gam, bet, mean, rstd, scn, shn);
+        }
+        if (st != SVDLUT_OK) return st;
         in = r;
         if (norm) {
             isc = w + wl.sc[i];
