@@ -73,7 +73,7 @@ inline Layout make_layout(int K)
 // backward temporaries.  InstanceNorm is not materialised: the layer after it
 // reads r[i] and applies the per-(b, c) affine map sc * r + sh on load.
 struct WsLayout {
-    size_t thumb, r[5], mean[4], rstd[4], sc[4], sh[4], part, wbf[5], tstat, rho, hidden;
+    size_t thumb, r[5], mean[4], rstd[4], sc[4], sh[4], part, wbf[5], tstat, dgw[5], rho, hidden;
     size_t dz[2], dact, wpart, dhid, drho, insum;
     size_t total;
 };
@@ -119,6 +119,16 @@ inline int conv_ks(int B, int i)
 inline int conv_split(int B, int i) { return (conv_stages(i) + conv_ks(B, i) - 1) / conv_ks(B, i); }
 // BF16 elements of conv i's weights in the B layout (NP x whole stages)
 inline size_t conv_wbf_elems(int i) { return static_cast<size_t>(wgrad_np(kCh[i + 1])) * conv_stages(i) * 64; }
+// Input gradient of conv i >= 1 (dgrad_umma_kernel): per parity class cls =
+// 2 py + px, K = (1 + py)(1 + px) Cout, padded to whole 64-k stages; the
+// class's split weights take 2 NP Kpad BF16 elements (hi, then lo).
+inline int dgrad_kpad(int i, int cls) { return ((1 + (cls >> 1)) * (1 + (cls & 1)) * kCh[i + 1] + 63) / 64 * 64; }
+inline size_t dgrad_w_elems(int i)
+{
+    size_t n = 0;
+    for (int c = 0; c < 4; ++c) n += static_cast<size_t>(2) * wgrad_np(kCh[i]) * dgrad_kpad(i, c);
+    return n;
+}
 
 inline WsLayout make_ws(int B)
 {
@@ -145,6 +155,7 @@ inline WsLayout make_ws(int B)
     for (int i = 0; i < 4; ++i)
         ts = std::max(ts, static_cast<size_t>((B * kSz[i + 1] * kSz[i + 1] + 127) / 128) * kCh[i + 1] * 2);
     w.tstat = take(ts);
+    for (int i = 1; i < 5; ++i) w.dgw[i] = take(dgrad_w_elems(i) / 2);
     w.rho = take(static_cast<size_t>(B) * kRho);
     w.hidden = take(static_cast<size_t>(B) * 4 * kHidden);
     const size_t amax = act_size(B, 0);
@@ -251,6 +262,9 @@ static_assert(kSz[0] % 16 == 0 && kSz[1] % 16 == 0 && kSz[2] % 16 == 0 && kSz[3]
 static_assert(kSz[5] % 8 == 0, "an output row holds whole pixel octets, an image whole stages");
 static_assert(kCh[1] <= 64 && kCh[2] <= 64 && kCh[3] <= 64 && kCh[4] <= 64 && kCh[5] <= 64,
               "output channels of a weight gradient: at most the MMA's N = 64");
+static_assert((kCh[2] & (kCh[2] - 1)) == 0 && (kCh[3] & (kCh[3] - 1)) == 0 && (kCh[4] & (kCh[4] - 1)) == 0 &&
+                  (kCh[5] & (kCh[5] - 1)) == 0 && kCh[2] >= 8,
+              "input gradient: output channels a power of two >= 8 (an octet of k is one tap)");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -764,130 +778,181 @@ __global__ void conv_wprep_kernel(const WPrep p)
     }
 }
 
-// ---- input gradient of the stride-2 3x3 convolution, by input parity ----
+// ---- input gradient of the stride-2 3x3 convolution on tcgen05, by input parity ----
 // Input pixel (iy, ix) = (2 qy + py, 2 qx + px) only receives the taps with
-// iy + 1 - ky and ix + 1 - kx even: ky = 1 (output row qy) when py = 0, and
-// ky = 0 (row qy + 1) or ky = 2 (row qy) when py = 1; likewise along x.  Each
-// parity class (blockIdx.z = 2 py + px) is then a dense GEMM with rows
-// m = (b, qy, qx), columns n = input channel and reduction k = (tap, o) over
-// its 1, 2 or 4 taps x Cout: none of the zero taps of the full 3x3 im2col is
-// loaded or multiplied.  Operands are split into BF16 hi + lo parts (three
-// MMAs).
-struct DgradPar {
-    const float *dz;  // [B][Cout][So][So]
-    const float *w;   // [Cout][Cin][3][3]
-    float *dact;      // [B][Cin][2 So][2 So]
-    int Cout, Cin, So, M;  // M = B So So rows per class
+// iy + 1 - ky and ix + 1 - kx even: ky = 1 (output row qy) when py = 0, ky = 0
+// (row qy + 1) or ky = 2 (row qy) when py = 1; likewise along x.  Each parity
+// class (blockIdx.y = 2 py + px) is then a dense GEMM: M = the class's input
+// pixels m = (b, qy, qx), 128 per CTA (TMEM lanes), N = NP >= Cin input
+// channels, K = (tap, o) over its 1, 2 or 4 live taps x Cout (o fastest;
+// Cout is a power of two >= 8, so an octet of k is 8 output channels of one
+// tap).  No zero tap of the full 3x3 im2col is loaded or multiplied.  Both
+// operands are split into BF16 hi and lo parts (lo*hi + hi*lo + hi*hi, the
+// weight gradient's precision), staged K-major in the no-swizzle layout
+// (element (m, k) at byte (k / 8) 16 * 128 + 16 m + 2 (k % 8)); the weights are
+// laid out once per call by dgrad_wprep_kernel in the stage layout of B
+// (per layer and class: NP x Kpad hi, then lo).  One stage buffer; every
+// wait is bounded (NaN outputs and g_umma_timeouts on expiry).
+struct DgradUmma {
+    const float *dz;   // [B][Cout][So][So]
+    const uint4 *wb;   // this layer's prepared weights; class c at wb + cls_off[c] (uint4 units)
+    float *dact;       // [B][Cin][2 So][2 So]
+    int Cout, Cin, So, M, cout_lg;  // M = B So^2 pixels per class
+    int cls_off[4], kpad[4];        // per class: offset of its hi part, K padded to whole stages
 };
 
-__global__ void __launch_bounds__(kGT) dgrad_kernel(const DgradPar p)
+constexpr int kDGT = 128;  // threads: pixel tid of the tile, all eight octets of a stage
+__host__ __device__ constexpr int dgrad_stage_bytes(int NP) { return 2 * (128 + NP) * kWK * 2; }
+
+template <int NP>
+__global__ void __launch_bounds__(kDGT, NP == 64 ? 4 : 6) dgrad_umma_kernel(const DgradUmma p)
 {
-    __shared__ __align__(16) __nv_bfloat16 As[2][64][40];
-    __shared__ __align__(16) __nv_bfloat16 Bs[2][64][40];
-    const int cls = blockIdx.z, py = cls >> 1, px = cls & 1, ntx = px ? 2 : 1;
-    const int Kd = (py ? 2 : 1) * ntx * p.Cout;
-    const int m0 = blockIdx.x * 64;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int g = lane >> 2, t = lane & 3;
-    const int lr = tid >> 1, lk = (tid & 1) * 16;  // loader: tile row and first k
-    const int m = m0 + lr, P = p.So * p.So;
-    const bool mvalid = m < p.M, nvalid = lr < p.Cin;
+    static_assert(NP % 16 == 0 && NP >= 16 && NP <= 64, "N of an M = 128 MMA: 16 .. 64, multiple of 16");
+    constexpr uint32_t kCols = NP < 32 ? 32 : NP;
+    constexpr int kA = 128 * kWK * 2, kB = NP * kWK * 2;  // one part (hi or lo) of A / B
+    constexpr uint32_t idesc = umma_idesc_bf16(128, NP);
+    extern __shared__ __align__(128) char dsm[];  // [A hi][A lo][B hi][B lo]
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t taddr_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = blockIdx.x, cls = blockIdx.y, py = cls >> 1, px = cls & 1, ntx = px ? 2 : 1;
+    const int Kd = (py ? 2 : 1) * ntx * p.Cout, nst = (Kd + kWK - 1) / kWK, P = p.So * p.So;
+    const int m = tile * 128 + tid;
+    const bool mval = m < p.M;
     int b = 0, qy = 0, qx = 0;
-    if (mvalid) {
+    if (mval) {
         b = m / P;
         const int rr = m - b * P;
         qy = rr / p.So;
         qx = rr - qy * p.So;
     }
     const float *dzb = p.dz + static_cast<size_t>(b) * p.Cout * P;
-    const float *wn_ = p.w + static_cast<size_t>(nvalid ? lr : 0) * 9;
-    float acc[2][4][4];
+    // (selected, not indexed: a runtime index would copy the arrays to local memory)
+    const int cls_off = cls == 0 ? p.cls_off[0] : cls == 1 ? p.cls_off[1] : cls == 2 ? p.cls_off[2] : p.cls_off[3];
+    const int kpad = cls == 0 ? p.kpad[0] : cls == 1 ? p.kpad[1] : cls == 2 ? p.kpad[2] : p.kpad[3];
+    const uint4 *wcls = p.wb + cls_off;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&taddr_s)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t taddr = taddr_s;
+    bool ok = true;
+    for (int s = 0; s < nst; ++s) {
+        if (s >= 1) ok = mbar_wait(smem_addr(&mbar), (s - 1) & 1) && ok;  // stage s - 1 read
+        // B: hi and lo parts of this stage, contiguous in the prepared layout
+        const uint4 *whi = wcls + static_cast<size_t>(s) * NP * 8, *wlo = whi + static_cast<size_t>(kpad) * NP / 8;
+        for (int e = tid; e < NP * 8; e += kDGT) {
+            reinterpret_cast<uint4 *>(dsm + 2 * kA)[e] = __ldg(whi + e);
+            reinterpret_cast<uint4 *>(dsm + 2 * kA + kB)[e] = __ldg(wlo + e);
+        }
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+        for (int q = 0; q < 8; ++q) {
+            const int k0 = s * kWK + 8 * q;
+            char *dst = dsm + q * 16 * 128 + 16 * tid;
+            float v[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+            for (int u = 0; u < 8; ++u) v[u] = 0.f;
+            if (k0 < Kd && mval) {
+                const int tap = k0 >> p.cout_lg, o0 = k0 & (p.Cout - 1);
+                const int ty = ntx == 2 ? tap >> 1 : tap, tx = ntx == 2 ? tap & 1 : 0;
+                const int oy = qy + (py && ty == 0 ? 1 : 0), ox = qx + (px && tx == 0 ? 1 : 0);
+                if (oy < p.So && ox < p.So) {
+                    const float *src = dzb + static_cast<size_t>(o0) * P + oy * p.So + ox;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    for (int k0 = 0; k0 < Kd; k0 += 32) {
-        const int k = k0 + lk;
-        int tap = k / p.Cout, o = k - tap * p.Cout;
-        float va[16], vb[16];
+                    for (int u = 0; u < 8; ++u) v[u] = __ldg(src + static_cast<size_t>(u) * P);
+                }
+            }
+            split_store(dst, dst + kA, v);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic stores -> tensor core
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t a0 = smem_addr(dsm), b0 = a0 + 2 * kA;
+            const int nk = (min(kWK, Kd - s * kWK) + 15) / 16;  // K steps of 16 holding live k
+            for (int kk = 0; kk < nk; ++kk) {
+                const uint64_t ahi = umma_sdesc(a0 + kk * 2 * 16 * 128, 16 * 128, 128);
+                const uint64_t alo = umma_sdesc(a0 + kA + kk * 2 * 16 * 128, 16 * 128, 128);
+                const uint64_t bhi = umma_sdesc(b0 + kk * 2 * 16 * NP, 16 * NP, 128);
+                const uint64_t blo = umma_sdesc(b0 + kB + kk * 2 * 16 * NP, 16 * NP, 128);
+                umma_bf16(taddr, alo, bhi, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                umma_bf16(taddr, ahi, blo, idesc, 1u);
+                umma_bf16(taddr, ahi, bhi, idesc, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_addr(&mbar))
+                         : "memory");
+        }
+    }
+    if (nst > 0) ok = mbar_wait(smem_addr(&mbar), (nst - 1) & 1) && ok;  // all MMAs
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (!ok && lane == 0) atomicAdd(&g_umma_timeouts, 1u);
+    // epilogue: thread tid holds pixel tid of the tile (TMEM lane), all NP channels
+    const int S = 2 * p.So;
+    float *out = p.dact + static_cast<size_t>(b) * p.Cin * S * S + static_cast<size_t>(2 * qy + py) * S + 2 * qx + px;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const bool kin = k + q < Kd;
+    for (int c0 = 0; c0 < NP; c0 += 8) {
+        uint32_t v[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                     : "r"(taddr + (static_cast<uint32_t>(32 * warp) << 16) + c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = c0 + q;
+            if (mval && c < p.Cin)
+                out[static_cast<size_t>(c) * S * S] = ok ? __uint_as_float(v[q]) : __int_as_float(0x7fc00000);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(kCols));
+    }
+}
+
+// The input-gradient weights of conv layers 1..4 as split BF16 in the B
+// stage layout of dgrad_umma_kernel: per layer and parity class, the hi part
+// then the lo part, each with element (c, k = tap * Cout + o) at bf16 index
+// (k / 8) * 8 NP + 8 c + k % 8 for k < Kpad (whole 64-k stages); zero for
+// c >= Cin or k beyond the class's taps.  Segment g = 4 (layer - 1) + class.
+struct DPrep {
+    const float *w[4];       // [Cout][Cin][3][3] of layers 1..4
+    __nv_bfloat16 *seg[16];  // hi part of each segment (lo follows at + NP Kpad)
+    int cin[4], cout[4], np[4], kpad[16];
+    int start[17];           // flattened element ranges (NP x Kpad each)
+};
+
+__global__ void dgrad_wprep_kernel(const DPrep p)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.start[16]; e += gridDim.x * blockDim.x) {
+        int g = 0;
+        while (e >= p.start[g + 1]) ++g;
+        const int l = g >> 2, cls = g & 3, py = cls >> 1, px = cls & 1, ntx = px ? 2 : 1;
+        const int Cin = p.cin[l], Cout = p.cout[l], NP = p.np[l], kpad = p.kpad[g];
+        const int i = e - p.start[g], c = i / kpad, k = i - c * kpad;
+        const int Kd = (py ? 2 : 1) * ntx * Cout;
+        float v = 0.f;
+        if (c < Cin && k < Kd) {
+            const int tap = k / Cout, o = k - tap * Cout;
             const int ty = ntx == 2 ? tap >> 1 : tap, tx = ntx == 2 ? tap & 1 : 0;
             const int ky = py ? (ty == 0 ? 0 : 2) : 1, kx = px ? (tx == 0 ? 0 : 2) : 1;
-            const int oy = qy + (py && ty == 0 ? 1 : 0), ox = qx + (px && tx == 0 ? 1 : 0);
-            const bool ok = mvalid && kin && oy < p.So && ox < p.So;
-            va[q] = ok ? __ldg(dzb + static_cast<size_t>(o) * P + oy * p.So + ox) : 0.f;
-            vb[q] = nvalid && kin ? __ldg(wn_ + static_cast<size_t>(o) * p.Cin * 9 + ky * 3 + kx) : 0.f;
-            if (++o == p.Cout) {
-                o = 0;
-                ++tap;
-            }
+            v = p.w[l][((static_cast<size_t>(o) * Cin + c) * 3 + ky) * 3 + kx];
         }
-#pragma unroll
-        for (int q = 0; q < 16; q += 2) {
-            const __nv_bfloat162 ha = __floats2bfloat162_rn(va[q], va[q + 1]);
-            const __nv_bfloat162 hb = __floats2bfloat162_rn(vb[q], vb[q + 1]);
-            *reinterpret_cast<__nv_bfloat162 *>(&As[0][lr][lk + q]) = ha;
-            *reinterpret_cast<__nv_bfloat162 *>(&Bs[0][lr][lk + q]) = hb;
-            *reinterpret_cast<__nv_bfloat162 *>(&As[1][lr][lk + q]) =
-                __floats2bfloat162_rn(va[q] - __low2float(ha), va[q + 1] - __high2float(ha));
-            *reinterpret_cast<__nv_bfloat162 *>(&Bs[1][lr][lk + q]) =
-                __floats2bfloat162_rn(vb[q] - __low2float(hb), vb[q + 1] - __high2float(hb));
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 32; kk += 16) {
-            uint32_t a[2][2][4], bb[2][4][2];
-#pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-#pragma unroll
-                for (int mi = 0; mi < 2; ++mi) {
-                    const int r = wm + mi * 16 + g;
-                    a[pp][mi][0] = *reinterpret_cast<const uint32_t *>(&As[pp][r][kk + 2 * t]);
-                    a[pp][mi][1] = *reinterpret_cast<const uint32_t *>(&As[pp][r + 8][kk + 2 * t]);
-                    a[pp][mi][2] = *reinterpret_cast<const uint32_t *>(&As[pp][r][kk + 8 + 2 * t]);
-                    a[pp][mi][3] = *reinterpret_cast<const uint32_t *>(&As[pp][r + 8][kk + 8 + 2 * t]);
-                }
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) {
-                    const int n = wn + ni * 8 + g;
-                    bb[pp][ni][0] = *reinterpret_cast<const uint32_t *>(&Bs[pp][n][kk + 2 * t]);
-                    bb[pp][ni][1] = *reinterpret_cast<const uint32_t *>(&Bs[pp][n][kk + 8 + 2 * t]);
-                }
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) {
-                    mma_bf16(acc[mi][ni], a[1][mi], bb[0][ni]);
-                    mma_bf16(acc[mi][ni], a[0][mi], bb[1][ni]);
-                    mma_bf16(acc[mi][ni], a[0][mi], bb[0][ni]);
-                }
-        }
-        __syncthreads();
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const size_t at = static_cast<size_t>(k >> 3) * 8 * NP + 8 * c + (k & 7);
+        p.seg[g][at] = h;
+        p.seg[g][static_cast<size_t>(NP) * kpad + at] = __float2bfloat16_rn(v - __bfloat162float(h));
     }
-    const int S = 2 * p.So;
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int q2 = 0; q2 < 2; ++q2) {
-            const int mm = m0 + wm + mi * 16 + g + 8 * q2;
-            if (mm >= p.M) continue;
-            const int bo = mm / P, rr = mm - bo * P, oy = rr / p.So, ox = rr - oy * p.So;
-            const size_t pix = static_cast<size_t>(2 * oy + py) * S + 2 * ox + px;
-#pragma unroll
-            for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-                for (int q1 = 0; q1 < 2; ++q1) {
-                    const int n = wn + ni * 8 + 2 * t + q1;
-                    if (n < p.Cin)
-                        p.dact[(static_cast<size_t>(bo) * p.Cin + n) * S * S + pix] = acc[mi][ni][2 * q2 + q1];
-                }
-        }
 }
 
 // Fixed-order sum over the NW warps of a block; every thread gets the total.
@@ -1044,6 +1109,16 @@ static svdlut_status launch_conv_t(const ConvUmma &a, dim3 grid, cudaStream_t s)
     const svdlut_status st = smem_opt_in(reinterpret_cast<const void *>(conv_umma_kernel<NP, C8, NT, NBUF>), smem);
     if (st != SVDLUT_OK) return st;
     return launch_pdl(conv_umma_kernel<NP, C8, NT, NBUF>, grid, dim3(NT), smem, s, a);
+}
+template <int NP>
+static svdlut_status launch_dgrad_t(const DgradUmma &a, cudaStream_t s)
+{
+    constexpr int smem = dgrad_stage_bytes(NP);
+    const svdlut_status st = smem_opt_in(reinterpret_cast<const void *>(dgrad_umma_kernel<NP>), smem);
+    if (st != SVDLUT_OK) return st;
+    dgrad_umma_kernel<NP><<<dim3((a.M + 127) / 128, 4), kDGT, smem, s>>>(a);
+    SVDLUT_CUDA_TRY(cudaGetLastError());
+    return SVDLUT_OK;
 }
 static svdlut_status launch_conv(const ConvUmma &a, int Z, cudaStream_t s)
 {
@@ -1536,6 +1611,28 @@ extern "C" svdlut_status svdlut_generator_backward(int K, const float *weights, 
     fc2_dgrad_kernel<<<dim3(B, 4), 256, 0, s>>>(pin, hw, w + wl.dhid);
     fc1_bwd_kernel<<<(std::max(4 * kHidden * kRho, B * kRho) + 255) / 256, 256, 0, s>>>(
         w + wl.rho, w + wl.dhid, hw, B, hg, w + wl.drho);
+    {  // the input-gradient weights of layers 1..4 in the tensor cores' B layout
+        DPrep dp{};
+        int e = 0;
+        for (int l = 0; l < 4; ++l) {
+            const int i = l + 1;
+            dp.w[l] = weights + L.conv_w[i];
+            dp.cin[l] = kCh[i];
+            dp.cout[l] = kCh[i + 1];
+            dp.np[l] = wgrad_np(kCh[i]);
+            __nv_bfloat16 *base = reinterpret_cast<__nv_bfloat16 *>(w + wl.dgw[i]);
+            for (int c = 0; c < 4; ++c) {
+                const int g = 4 * l + c;
+                dp.kpad[g] = dgrad_kpad(i, c);
+                dp.seg[g] = base;
+                base += static_cast<size_t>(2) * dp.np[l] * dp.kpad[g];
+                dp.start[g] = e;
+                e += dp.np[l] * dp.kpad[g];
+            }
+        }
+        dp.start[16] = e;
+        dgrad_wprep_kernel<<<(e + 255) / 256, 256, 0, s>>>(dp);
+    }
     float *dz = w + wl.dz[0];
     pool_bwd_kernel<<<(B * 4096 + 255) / 256, 256, 0, s>>>(w + wl.drho, w + wl.r[4], B, training, seed, dz);
     SVDLUT_CUDA_TRY(cudaGetLastError());
@@ -1556,9 +1653,19 @@ extern "C" svdlut_status svdlut_generator_backward(int K, const float *weights, 
         if (i == 0) break;
         // input gradient, then InstanceNorm + LeakyReLU backward of layer i-1
         float *dact = w + wl.dact;
-        dgrad_kernel<<<dim3((B * So * So + 63) / 64, 1, 4), kGT, 0, s>>>(
-            DgradPar{dz, weights + L.conv_w[i], dact, Cout, Cin, So, B * So * So});
-        SVDLUT_CUDA_TRY(cudaGetLastError());
+        {
+            DgradUmma da{dz, reinterpret_cast<const uint4 *>(w + wl.dgw[i]), dact, Cout, Cin, So, B * So * So,
+                         31 - __builtin_clz(static_cast<unsigned>(Cout)), {}, {}};
+            size_t off = 0;
+            for (int c = 0; c < 4; ++c) {
+                da.cls_off[c] = static_cast<int>(off / 8);  // uint4 units
+                da.kpad[c] = dgrad_kpad(i, c);
+                off += static_cast<size_t>(2) * wgrad_np(Cin) * da.kpad[c];
+            }
+            const int np = wgrad_np(Cin);
+            st = np == 16 ? launch_dgrad_t<16>(da, s) : np == 32 ? launch_dgrad_t<32>(da, s) : launch_dgrad_t<64>(da, s);
+            if (st != SVDLUT_OK) return st;
+        }
         const int j = i - 1;
         float *dz_next = dz == w + wl.dz[0] ? w + wl.dz[1] : w + wl.dz[0];
         in_bwd_sums_kernel<<<B * Cin, 256, 0, s>>>(dact, w + wl.r[j], w + wl.mean[j], w + wl.rstd[j], S * S,
