@@ -10,9 +10,17 @@ of the gradient within its bound of the FP64 oracle (GRAD_GROUP_BOUNDS:
 early layers).  Those bounds are about twice what the FP64 oracle itself
 moves when only its convolution operands are rounded to BF16 (LeakyReLU
 decisions near zero, amplified by InstanceNorm's backward); the CPU test
-test_oracle_generator.py pins that margin.  The gradient of the oracle with
-BF16-rounded operands is printed beside it as a diagnostic only.  Dropout
-masks, Adam and MSE are compared exactly / to FP32 rounding.
+test_oracle_generator.py pins that margin.
+
+A second, tighter gate compares with the oracle run with BF16-rounded
+convolution operands (conv_operands="bf16"): the tensor-core kernels round
+exactly those operands, so what remains is FP32 accumulation and FP32
+normalisation statistics.  Forward parameters: within 1.5e-3 (observed
+<= 4e-4 over the cases here); gradient groups: the heads within 5e-3
+(observed <= 7e-4), the convolution and norm layers within 0.1 (observed
+<= 0.04: LeakyReLU decisions of values within FP32 rounding of zero still
+differ).  Dropout masks, Adam and MSE are compared exactly / to FP32
+rounding.
 """
 import numpy as np
 import pytest
@@ -65,8 +73,11 @@ def test_forward_matches_oracle(sv, K, HW):
     out = gen.forward(torch.from_numpy(x).cuda())
     torch.cuda.synchronize()
     ref, _ = G.forward(blob, x, K)
+    ref_b, _ = G.forward(blob, x, K, conv_operands="bf16")
     for k in ref:
-        assert rel(out[k].cpu().numpy().astype(np.float64), ref[k]) <= 2e-2, k
+        got = out[k].cpu().numpy().astype(np.float64)
+        assert rel(got, ref[k]) <= 2e-2, k
+        assert rel(got, ref_b[k]) <= 1.5e-3, (k, rel(got, ref_b[k]))
 
 
 def test_training_dropout_mask_matches_counter_generator(sv):
@@ -108,12 +119,15 @@ def test_backward_matches_oracle(sv, training):
     pg, p64 = G.unpack(got, K), G.unpack(ref64, K)
     errs = {n: rel(pg[n], p64[n]) for n in p64}
     bad = {n: (e, grad_group_bound(n)) for n, e in errs.items() if e > grad_group_bound(n)}
-    # diagnostic: the same groups against the oracle with BF16-rounded conv operands
+    # the tighter gate: the oracle with BF16-rounded convolution operands
     _, cache_b = G.forward(blob, x, K, drop_mask=mask, conv_operands="bf16")
     pb = G.unpack(G.backward(blob, K, cache_b, d64), K)
+    errs_b = {n: rel(pg[n], pb[n]) for n in p64}
     print("per-group rel. error vs FP64 oracle / vs BF16-operand oracle:",
-          {n: (round(errs[n], 4), round(rel(pg[n], pb[n]), 4)) for n in p64})
+          {n: (round(errs[n], 4), round(errs_b[n], 4)) for n in p64})
     assert not bad, (bad, errs)
+    bad_b = {n: e for n, e in errs_b.items() if e > (5e-3 if n.startswith("h") else 0.1)}
+    assert not bad_b, bad_b
 
 
 def test_backward_is_deterministic(sv):
@@ -161,8 +175,11 @@ def test_forward_on_4k_frames_matches_oracle(sv):
     out = gen.forward(torch.from_numpy(x).cuda())
     torch.cuda.synchronize()
     ref, _ = G.forward(blob, x, K)
+    ref_b, _ = G.forward(blob, x, K, conv_operands="bf16")
     for k in ref:
-        assert rel(out[k].cpu().numpy().astype(np.float64), ref[k]) <= 2e-2, k
+        got = out[k].cpu().numpy().astype(np.float64)
+        assert rel(got, ref[k]) <= 2e-2, k
+        assert rel(got, ref_b[k]) <= 1.5e-3, (k, rel(got, ref_b[k]))
 
 
 def test_tensor_core_tiles_complete(sv):
