@@ -80,6 +80,27 @@ def test_forward_matches_oracle(sv, K, HW):
         assert rel(got, ref_b[k]) <= 1.5e-3, (k, rel(got, ref_b[k]))
 
 
+@pytest.mark.parametrize("B", [1, 40])
+def test_forward_batch_paths_match_oracle(sv, B):
+    """The convolution paths that depend on the batch: B = 1 splits K in
+    every layer but the first and leaves single partial tiles; B = 40 takes
+    the fused finish (bias, LeakyReLU and per-tile statistics in the
+    tensor-core epilogue) in layers 0-2, the 16- and 32-channel ones."""
+    import torch
+    K = 6
+    blob = make_blob(K, 60 + B)
+    x = np.stack([si.make_image(np.random.default_rng(300 + j), 48, 64) for j in range(B)])
+    gen = gpu_gen(sv, K, blob, B=B)
+    out = gen.forward(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    ref, _ = G.forward(blob, x, K)
+    ref_b, _ = G.forward(blob, x, K, conv_operands="bf16")
+    for k in ref:
+        got = out[k].cpu().numpy().astype(np.float64)
+        assert rel(got, ref[k]) <= 2e-2, k
+        assert rel(got, ref_b[k]) <= 1.5e-3, (k, rel(got, ref_b[k]))
+
+
 def test_training_dropout_mask_matches_counter_generator(sv):
     import torch
     K, seed = 4, 12345
@@ -97,12 +118,14 @@ def test_training_dropout_mask_matches_counter_generator(sv):
     assert rel(ref["U"], ref_nodrop["U"]) > 1e-3
 
 
-@pytest.mark.parametrize("training", [False, True])
-def test_backward_matches_oracle(sv, training):
+@pytest.mark.parametrize("training,B,HW", [(False, 3, (200, 240)), (True, 3, (200, 240)), (True, 40, (48, 64))])
+def test_backward_matches_oracle(sv, training, B, HW):
+    """B = 40: the weight-gradient chunks and input-gradient tiles of a large
+    batch, after a forward through the fused finish."""
     import torch
-    K, B, seed = 6, 3, 777
+    K, seed = 6, 777
     blob = make_blob(K, 50)
-    x = np.stack([si.make_image(np.random.default_rng(60 + j), 200, 240) for j in range(B)])
+    x = np.stack([si.make_image(np.random.default_rng(60 + j), *HW) for j in range(B)])
     gen = gpu_gen(sv, K, blob, B=B)
     out = gen.forward(torch.from_numpy(x).cuda(), training=training, seed=seed)
     rng = np.random.default_rng(70)
