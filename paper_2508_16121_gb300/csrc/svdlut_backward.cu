@@ -761,7 +761,9 @@ static svdlut_status plan_backward(const svdlut_dims *d, int B, int H, int W, in
             }
         }
     }
-    // grid pass: blocks of 128 x BH; bands chosen like the forward plan
+    // grid pass: blocks of 128 x BH; bands minimise waves x (rows a warp
+    // walks + a fixed cost of about 4 rows per block: clearing the tables,
+    // writing the partial); ties go to the better-filled waves
     const int strips = (W + kTileW - 1) / kTileW;
     const int max_bands = std::max(1, (H + kMinBlockH - 1) / kMinBlockH);
     int best = -1;
@@ -781,7 +783,8 @@ static svdlut_status plan_backward(const svdlut_dims *d, int B, int H, int W, in
         if (need + 256 > smem_limit) continue;  // + the kernel's static row offsets
         const long long T = static_cast<long long>(B) * strips * gp.bands;
         const double waves = std::ceil(static_cast<double>(T) / sm_count - 1e-9);
-        const double score = static_cast<double>(T) / (waves * sm_count) - 0.002 * waves;
+        const double fill = static_cast<double>(T) / (waves * sm_count);
+        const double score = -waves * (gp.rpw + 4) + 1e-3 * fill;
         if (score > best_score + 1e-12) {
             best_score = score;
             best = bands;
