@@ -47,9 +47,11 @@ size_t apply_smem_bytes(LaunchArgs<N> &a, size_t limit)
 }
 
 // Plans the block split of B same-size images: each image is cut into
-// `strips` column strips of kTileW pixels and `bands` row bands; bands is
-// chosen to maximise the share of SM time used (blocks / (waves x SMs)),
-// preferring fewer waves, while the block buffers fit in shared memory.  Fills strips/BH/block_begin, total_blocks, nvx_max, nvy_max,
+// `strips` column strips of kTileW pixels and `bands` row bands; bands
+// minimises the estimated time, waves x (rows each warp walks in a block + a
+// fixed cost of about one row per block: the block's tables), with ties
+// going to the better-filled waves, while the block buffers fit in shared
+// memory.  Fills strips/BH/block_begin, total_blocks, nvx_max, nvy_max,
 // bh_max and the shared-memory size.
 template <int N>
 svdlut_status plan_uniform(LaunchArgs<N> &a, int sm_count, size_t smem_limit, size_t *smem_out)
@@ -69,10 +71,10 @@ svdlut_status plan_uniform(LaunchArgs<N> &a, int sm_count, size_t smem_limit, si
         const int BH = (rows + bands - 1) / bands;
         const int need = fixed + std::max(pro, block_floats(nvx, span_bound(BH, H, e0.Dsy), e0.Dsc, BH, a.xcol != 0));
         if (sizeof(float) * static_cast<size_t>(need) > smem_limit) continue;
-        const long long T = static_cast<long long>(a.n) * strips * bands;
+        const long long T = static_cast<long long>(a.n) * strips * ((rows + BH - 1) / BH);
         const double waves = std::ceil(static_cast<double>(T) / sm_count - 1e-9);
-        const double eff = static_cast<double>(T) / (waves * sm_count);  // share of SM time used
-        const double score = eff - 0.002 * waves;                        // prefer fewer, larger blocks
+        const double fill = static_cast<double>(T) / (waves * sm_count);  // share of SM time used
+        const double score = -waves * ((BH + kWarps - 1) / kWarps + 1) + 1e-3 * fill;
         if (score > best_score + 1e-12) {
             best_score = score;
             best = bands;
