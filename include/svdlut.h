@@ -376,11 +376,14 @@ svdlut_status svdlut_backward_noalloc(const svdlut_dims *dims, const svdlut_para
                                       const svdlut_grads *grads, svdlut_stream_t stream);
 
 /*
- * svdlut_tensor_core_timeouts -- number of tensor-core tiles (the tcgen05
- * weight-gradient GEMM of svdlut_generator_backward) whose bounded wait for
- * their matrix multiplies expired since the last call, on the current device;
- * the counter is then reset.  Such a tile writes NaN instead of its result.
- * Synchronises the device.  Not a computation of the paper.
+ * svdlut_tensor_core_timeouts -- number of warps of the generator's tcgen05
+ * kernels (the forward convolutions of svdlut_generator_forward, the weight-
+ * and input-gradient GEMMs of svdlut_generator_backward) whose bounded wait
+ * for their matrix multiplies expired since the last call, on the current
+ * device; the counter is then reset.  A tile whose wait expired writes NaN
+ * instead of its result.  count: host pointer, required.  Synchronises the
+ * device (errors of earlier asynchronous work are returned).  Not a
+ * computation of the paper.
  */
 svdlut_status svdlut_tensor_core_timeouts(uint32_t *count);
 

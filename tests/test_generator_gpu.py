@@ -206,8 +206,9 @@ def test_forward_on_4k_frames_matches_oracle(sv):
 
 
 def test_tensor_core_tiles_complete(sv):
-    """The weight gradients run on tcgen05 tensor cores with bounded waits:
-    after a backward pass no tile reported an expired wait."""
+    """The convolutions and both gradient GEMMs run on tcgen05 tensor cores
+    with bounded waits: after a forward and a backward pass no tile reported
+    an expired wait, and every output is finite."""
     import ctypes
     import torch
     from paper_2508_16121_gb300 import _lib
@@ -219,6 +220,7 @@ def test_tensor_core_tiles_complete(sv):
     x = torch.from_numpy(np.stack([si.make_image(np.random.default_rng(150 + j), 96, 128) for j in range(2)])).cuda()
     gen = gpu_gen(sv, K, blob, B=2)
     out = gen.forward(x, training=True, seed=5)
+    assert all(bool(torch.isfinite(v).all()) for v in out.values())
     dw = gen.backward({k: torch.ones_like(v) for k, v in out.items()})
     assert torch.isfinite(dw).all()
     assert lib.svdlut_tensor_core_timeouts(ctypes.byref(cnt)) == 0
