@@ -373,12 +373,19 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
     const int nst = (min(p.chunk, p.npix - m_beg) + kWK - 1) / kWK;
     const int na = ng * 8, nt = na + p.Cout * 8;
     bool ok = true;
-    for (int s = 0; s < nst; ++s) {
-        const int buf = s & 1;
-        char *stg = wsm + buf * kStage;
-        if (s >= 2) ok = mbar_wait(smem_addr(&mbar[buf]), ((s - 2) >> 1) & 1) && ok;  // stage s - 2 read
-        const int m0 = m_beg + s * kWK;
-        for (int t = tid; t < nt; t += kWT) {
+    // Two stages per iteration (both buffers): twice the loads in flight per
+    // barrier, which the narrow layers need (their stage has fewer tasks
+    // than threads).  Buffer b holds the stages s with s % 2 == b.
+    for (int s = 0; s < nst; s += 2) {
+        const int ns = min(2, nst - s);
+        if (s >= 2) {  // the previous iteration's MMAs have read both buffers
+            ok = mbar_wait(smem_addr(&mbar[0]), ((s - 2) >> 1) & 1) && ok;
+            ok = mbar_wait(smem_addr(&mbar[1]), ((s - 1) >> 1) & 1) && ok;
+        }
+        for (int t2 = tid; t2 < ns * nt; t2 += kWT) {
+            const int si = t2 >= nt ? 1 : 0, t = t2 - si * nt;
+            char *stg = wsm + si * kStage;
+            const int m0 = m_beg + (s + si) * kWK;
             if (t < na) {
                 const int q = t / ng, g = t - q * ng;
                 const int cg = (kWRows / 3) * tile + g, c = cg / 3, ky = cg - 3 * c;
@@ -444,20 +451,22 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n");
-            const uint32_t a0 = smem_addr(stg), b0 = a0 + 2 * kA;
+            for (int si = 0; si < ns; ++si) {
+                const uint32_t a0 = smem_addr(wsm + si * kStage), b0 = a0 + 2 * kA;
 #pragma unroll
-            for (int kk = 0; kk < kWK / 16; ++kk) {
-                const uint64_t ahi = umma_sdesc(a0 + kk * 2 * 16 * 128, 16 * 128, 128);
-                const uint64_t alo = umma_sdesc(a0 + kA + kk * 2 * 16 * 128, 16 * 128, 128);
-                const uint64_t bhi = umma_sdesc(b0 + kk * 2 * 16 * NP, 16 * NP, 128);
-                const uint64_t blo = umma_sdesc(b0 + kB + kk * 2 * 16 * NP, 16 * NP, 128);
-                umma_bf16(taddr, alo, bhi, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                umma_bf16(taddr, ahi, blo, idesc, 1u);
-                umma_bf16(taddr, ahi, bhi, idesc, 1u);
+                for (int kk = 0; kk < kWK / 16; ++kk) {
+                    const uint64_t ahi = umma_sdesc(a0 + kk * 2 * 16 * 128, 16 * 128, 128);
+                    const uint64_t alo = umma_sdesc(a0 + kA + kk * 2 * 16 * 128, 16 * 128, 128);
+                    const uint64_t bhi = umma_sdesc(b0 + kk * 2 * 16 * NP, 16 * NP, 128);
+                    const uint64_t blo = umma_sdesc(b0 + kB + kk * 2 * 16 * NP, 16 * NP, 128);
+                    umma_bf16(taddr, alo, bhi, idesc, (s + si > 0 || kk > 0) ? 1u : 0u);
+                    umma_bf16(taddr, ahi, blo, idesc, 1u);
+                    umma_bf16(taddr, ahi, bhi, idesc, 1u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 smem_addr(&mbar[si]))
+                             : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             smem_addr(&mbar[buf]))
-                         : "memory");
         }
     }
     if (nst > 0) ok = mbar_wait(smem_addr(&mbar[(nst - 1) & 1]), ((nst - 1) >> 1) & 1) && ok;  // all MMAs
