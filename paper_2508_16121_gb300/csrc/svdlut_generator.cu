@@ -82,20 +82,24 @@ struct WsLayout {
 inline size_t act_size(int B, int i) { return static_cast<size_t>(B) * kCh[i + 1] * kSz[i + 1] * kSz[i + 1]; }
 
 // Weight gradient of conv i (wgrad_kernel): tiles of 126 im2col columns
-// (with the bias column) and N = output channels padded to 16, 32 or 64; the
-// batch's output pixels are cut into chunks of wgrad_chunk_px pixels (a
-// multiple of the 64-pixel stage) so that tiles x chunks fill the resident
-// CTAs of one wave on 152 SMs (a fixed split: the summation order, hence the
-// result, does not depend on the device).
+// (with the bias column) and N = output channels padded to 16, 32 or 64; a
+// layer with at most 32 columns (the first) packs four pixel subsets into one
+// MMA instead (wgrad_sets = 4, N = 4 Cout).  The batch's output pixels are cut
+// into chunks of wgrad_chunk_px pixels (whole stages of 64 x sets pixels) so
+// that tiles x chunks fill the resident CTAs of one wave on 152 SMs (a fixed
+// split: the summation order, hence the result, does not depend on the
+// device); the partials of chunk z and subset r are chunk sets z + r.
 inline int wgrad_np(int Cout) { return Cout <= 16 ? 16 : Cout <= 32 ? 32 : 64; }
-inline int wgrad_tiles(int i) { return (kCh[i] * 9 + 1 + 125) / 126; }
+inline int wgrad_sets(int i) { return kCh[i] * 9 + 1 <= 32 && 4 * kCh[i + 1] <= 64 ? 4 : 1; }
+inline int wgrad_np_layer(int i) { return wgrad_np(wgrad_sets(i) * kCh[i + 1]); }
+inline int wgrad_tiles(int i) { return wgrad_sets(i) > 1 ? 1 : (kCh[i] * 9 + 1 + 125) / 126; }
 inline int wgrad_chunk_px(int B, int i)
 {
-    const int pix = B * kSz[i + 1] * kSz[i + 1], np = wgrad_np(kCh[i + 1]);
-    const int ctas = (np <= 16 ? 3 : 2) * 152;  // wgrad_ctas_per_sm(np) x SMs
+    const int pix = B * kSz[i + 1] * kSz[i + 1], st = 64 * wgrad_sets(i);
+    const int ctas = 2 * 152;  // resident CTAs (two per SM) x SMs
     const int want = std::max(1, (ctas + wgrad_tiles(i) - 1) / wgrad_tiles(i));
     const int px = (pix + want - 1) / want;
-    return std::max(64, (px + 63) / 64 * 64);
+    return std::max(st, (px + st - 1) / st * st);
 }
 inline int wgrad_chunks(int B, int i)
 {
@@ -164,7 +168,7 @@ inline WsLayout make_ws(int B)
     w.dact = take(amax);
     size_t wp = 0;
     for (int i = 0; i < 5; ++i) {
-        wp = std::max(wp, static_cast<size_t>(wgrad_chunks(B, i)) * kCh[i + 1] * (kCh[i] * 9 + 1));
+        wp = std::max(wp, static_cast<size_t>(wgrad_chunks(B, i)) * wgrad_sets(i) * kCh[i + 1] * (kCh[i] * 9 + 1));
     }
     w.wpart = take(wp);
     w.dhid = take(static_cast<size_t>(B) * 4 * kHidden);
@@ -214,19 +218,6 @@ __global__ void downsample_kernel(const float *__restrict__ x, int B, int H, int
     }
 }
 
-// ---- BF16 mma.sync fragments of the forward and input-gradient convolutions ----
-// (64 x 64 output tile per CTA, 4 warps of 32 x 32, m16n8k16, FP32 accumulators)
-constexpr int kGT = 128;
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 // ---- weight gradients of the stride-2 pad-1 3x3 convolutions on tcgen05 ----
 // dW[o][j] = sum over the batch's output pixels p of dz[o][p] im2col[p][j],
 // j = (c, ky, kx) < Kd = 9 Cin, and the bias gradient as column j = Kd (an
@@ -252,7 +243,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 // bias row, the padding rows of the tile and of N) are written once.  Every
 // wait is bounded: on expiry the outputs are NaN and g_umma_timeouts counts
 // the warp.
-constexpr int kWT = 256;     // threads: warp w reads TMEM lanes 32 (w % 4) .. + 31
+constexpr int kWT = 512;     // threads (staging); warps w < 8 read TMEM lanes 32 (w % 4) .. + 31
 constexpr int kWK = 64;      // pixels per stage (four K steps of 16)
 constexpr int kWRows = 126;  // columns j per tile
 __device__ unsigned int g_umma_timeouts;
@@ -333,10 +324,18 @@ __host__ __device__ constexpr int wgrad_stage_bytes(int NP) { return 2 * (128 + 
 // CTAs per SM that the two stages allow in 227 KB of shared memory
 constexpr int wgrad_ctas_per_sm(int NP) { return (227 * 1024) / (2 * wgrad_stage_bytes(NP) + 1024); }
 
-template <int NP>
-__global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const WgradArgs p)
+// SETS = 4 (a layer with 9 Cin + 1 <= 32 columns, like the first): the 128
+// rows hold four disjoint pixel subsets of the stage, rows 32 r .. 32 r + 31
+// the im2col of subset r and B columns Cout r .. Cout r + Cout - 1 its dz, so
+// a stage covers 4 x 64 pixels; the diagonal blocks (r, r) of D are the
+// subsets' partial sums (the others are discarded), written as chunks
+// SETS z + r.
+template <int NP, int SETS>
+__global__ void __launch_bounds__(kWT, 2) wgrad_kernel(const WgradArgs p)
 {
     static_assert(NP % 16 == 0 && NP >= 16 && NP <= 64, "N of an M = 128 MMA: 16 .. 64, multiple of 16");
+    static_assert(SETS == 1 || SETS == 4, "one subset (126-column tiles) or four (32 rows each)");
+    constexpr int RS = SETS == 1 ? kWRows : 128 / SETS;  // rows of one subset
     constexpr uint32_t kCols = NP < 32 ? 32 : NP;  // TMEM columns (power of 2 >= 32)
     constexpr int kA = 128 * kWK * 2, kB = NP * kWK * 2, kStage = wgrad_stage_bytes(NP);
     constexpr uint32_t idesc = umma_idesc_bf16(128, NP);
@@ -346,7 +345,7 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = blockIdx.x, z = blockIdx.y;
     const int Kd = 9 * p.Cin, P = p.So * p.So;
-    const int ng = max(0, min(kWRows / 3, 3 * p.Cin - (kWRows / 3) * tile));  // live (c, ky) groups
+    const int ng = max(0, min(kWRows / 3, 3 * p.Cin - (kWRows / 3) * tile));  // live (c, ky) groups per subset
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&taddr_s)),
                      "r"(kCols));
@@ -360,9 +359,9 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
     // rows that never change: everything zero, then the bias row (hi = 1)
     for (int i = tid; i < 2 * kStage / 16; i += kWT) reinterpret_cast<uint4 *>(wsm)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
-    const int rb = Kd - kWRows * tile;
-    if (rb >= 0 && rb < kWRows && tid < 16)
-        *reinterpret_cast<uint4 *>(wsm + (tid >> 3) * kStage + (tid & 7) * 16 * 128 + 16 * rb) =
+    const int rb = Kd - kWRows * tile;  // the bias row within a subset
+    if (rb >= 0 && rb < RS && tid < 16 * SETS)
+        *reinterpret_cast<uint4 *>(wsm + ((tid >> 3) & 1) * kStage + (tid & 7) * 16 * 128 + 16 * ((tid >> 4) * RS + rb)) =
             make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -370,8 +369,8 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     const uint32_t taddr = taddr_s;
     const int m_beg = z * p.chunk;
-    const int nst = (min(p.chunk, p.npix - m_beg) + kWK - 1) / kWK;
-    const int na = ng * 8, nt = na + p.Cout * 8;
+    const int nst = (min(p.chunk, p.npix - m_beg) + SETS * kWK - 1) / (SETS * kWK);
+    const int na = SETS * ng * 8, nt = na + SETS * p.Cout * 8;
     bool ok = true;
     // Two stages per iteration (both buffers): twice the loads in flight per
     // barrier, which the narrow layers need (their stage has fewer tasks
@@ -385,11 +384,12 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
         for (int t2 = tid; t2 < ns * nt; t2 += kWT) {
             const int si = t2 >= nt ? 1 : 0, t = t2 - si * nt;
             char *stg = wsm + si * kStage;
-            const int m0 = m_beg + (s + si) * kWK;
+            const int m0 = m_beg + (s + si) * SETS * kWK;
             if (t < na) {
-                const int q = t / ng, g = t - q * ng;
+                const int set = SETS == 1 ? 0 : t / (ng * 8), ts = t - set * ng * 8;
+                const int q = ts / ng, g = ts - q * ng;
                 const int cg = (kWRows / 3) * tile + g, c = cg / 3, ky = cg - 3 * c;
-                const int m = m0 + 8 * q;
+                const int m = m0 + set * kWK + 8 * q;
                 float v[16], left = 0.f;
 #pragma unroll
                 for (int u = 0; u < 16; ++u) v[u] = 0.f;
@@ -425,13 +425,14 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
                     r1[u] = v[2 * u];
                     r2[u] = v[2 * u + 1];
                 }
-                char *dst = stg + q * 16 * 128 + 16 * (3 * g);
+                char *dst = stg + q * 16 * 128 + 16 * (set * RS + 3 * g);
                 split_store(dst, dst + kA, r0);
                 split_store(dst + 16, dst + kA + 16, r1);
                 split_store(dst + 32, dst + kA + 32, r2);
             } else {
-                const int tb = t - na, q = tb / p.Cout, o = tb - q * p.Cout;
-                const int m = m0 + 8 * q;
+                const int tb = t - na, set = SETS == 1 ? 0 : tb / (p.Cout * 8), ts = tb - set * p.Cout * 8;
+                const int q = ts / p.Cout, o = ts - q * p.Cout;
+                const int m = m0 + set * kWK + 8 * q;
                 float v[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[u] = 0.f;
@@ -443,7 +444,7 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
                     v[0] = f0.x, v[1] = f0.y, v[2] = f0.z, v[3] = f0.w;
                     v[4] = f1.x, v[5] = f1.y, v[6] = f1.z, v[7] = f1.w;
                 }
-                char *dst = stg + 2 * kA + q * 16 * NP + 16 * o;
+                char *dst = stg + 2 * kA + q * 16 * NP + 16 * (set * p.Cout + o);
                 split_store(dst, dst + kB, v);
             }
         }
@@ -472,12 +473,33 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
     if (nst > 0) ok = mbar_wait(smem_addr(&mbar[(nst - 1) & 1]), ((nst - 1) >> 1) & 1) && ok;  // all MMAs
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     if (!ok && lane == 0) atomicAdd(&g_umma_timeouts, 1u);
-    // epilogue: warp w holds rows 32 (w % 4) + lane of D, columns of half w / 4
+    if constexpr (SETS > 1) {
+        // warp w < 4 holds subset w's rows (its lanes), its block of columns
+        if (warp < 4) {
+            const int zv = SETS * z + warp;
+            for (int c0 = 0; c0 < p.Cout; c0 += 8) {
+                uint32_t v[8];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                               "=r"(v[7])
+                             : "r"(taddr + (static_cast<uint32_t>(32 * warp) << 16) + warp * p.Cout + c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int o = c0 + q;
+                    if (lane <= Kd && o < p.Cout)
+                        p.part[(static_cast<size_t>(zv) * p.Cout + o) * (Kd + 1) + lane] =
+                            ok ? __uint_as_float(v[q]) : __int_as_float(0x7fc00000);
+                }
+            }
+        }
+    } else {
+    // epilogue: warp w < 8 holds rows 32 (w % 4) + lane of D, columns of half w / 4
     const int r = 32 * (warp & 3) + lane, j = kWRows * tile + r;
     constexpr int kHalf = NP / 2;
     const int cb = (warp >> 2) * kHalf;
 #pragma unroll
-    for (int c0 = 0; c0 < kHalf; c0 += 8) {
+    for (int c0 = 0; c0 < (warp < 8 ? kHalf : 0); c0 += 8) {
         uint32_t v[8];
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
                      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
@@ -490,6 +512,7 @@ __global__ void __launch_bounds__(kWT, wgrad_ctas_per_sm(NP)) wgrad_kernel(const
                 p.part[(static_cast<size_t>(z) * p.Cout + o) * (Kd + 1) + j] =
                     ok ? __uint_as_float(v[q]) : __int_as_float(0x7fc00000);
         }
+    }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
@@ -1098,13 +1121,13 @@ static svdlut_status smem_opt_in(const void *fn, int bytes)
     return SVDLUT_OK;
 }
 
-template <int NP>
+template <int NP, int SETS>
 static svdlut_status launch_wgrad(const WgradArgs &a, int tiles, int chunks, cudaStream_t s)
 {
     constexpr int smem = 2 * wgrad_stage_bytes(NP);
-    const svdlut_status st = smem_opt_in(reinterpret_cast<const void *>(wgrad_kernel<NP>), smem);
+    const svdlut_status st = smem_opt_in(reinterpret_cast<const void *>(wgrad_kernel<NP, SETS>), smem);
     if (st != SVDLUT_OK) return st;
-    wgrad_kernel<NP><<<dim3(tiles, chunks), kWT, smem, s>>>(a);
+    wgrad_kernel<NP, SETS><<<dim3(tiles, chunks), kWT, smem, s>>>(a);
     SVDLUT_CUDA_TRY(cudaGetLastError());
     return SVDLUT_OK;
 }
@@ -1652,12 +1675,15 @@ extern "C" svdlut_status svdlut_generator_backward(int K, const float *weights, 
         // all-ones im2col column), then an ordered sum
         const WgradArgs wa{i == 0 ? w + wl.thumb : w + wl.r[i - 1], i == 0 ? nullptr : w + wl.sc[i - 1],
                            i == 0 ? nullptr : w + wl.sh[i - 1], dz, w + wl.wpart, Cin, Cout, S, So, pix, chunk};
-        const int np = wgrad_np(Cout), tiles = wgrad_tiles(i);
-        st = np == 16 ? launch_wgrad<16>(wa, tiles, chunks, s)
-                      : np == 32 ? launch_wgrad<32>(wa, tiles, chunks, s) : launch_wgrad<64>(wa, tiles, chunks, s);
+        const int np = wgrad_np_layer(i), tiles = wgrad_tiles(i), sets = wgrad_sets(i);
+        if (sets == 4)
+            st = np == 16 ? launch_wgrad<16, 4>(wa, tiles, chunks, s) : launch_wgrad<32, 4>(wa, tiles, chunks, s);
+        else
+            st = np == 16 ? launch_wgrad<16, 1>(wa, tiles, chunks, s)
+                          : np == 32 ? launch_wgrad<32, 1>(wa, tiles, chunks, s) : launch_wgrad<64, 1>(wa, tiles, chunks, s);
         if (st != SVDLUT_OK) return st;
         wgrad_reduce_kernel<<<(Cout * (Kd + 1) * 32 + 255) / 256, 256, 0, s>>>(
-            w + wl.wpart, chunks, Cout, Kd, dweights + L.conv_w[i], dweights + L.conv_b[i]);
+            w + wl.wpart, chunks * sets, Cout, Kd, dweights + L.conv_w[i], dweights + L.conv_b[i]);
         SVDLUT_CUDA_TRY(cudaGetLastError());
         if (i == 0) break;
         // input gradient, then InstanceNorm + LeakyReLU backward of layer i-1
