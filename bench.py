@@ -412,16 +412,20 @@ def time_calls(fn, steps, stream, warmup=3):
 
 
 def run_io_variant(svdlut, torch, dev, stream, args, x, p, d):
-    """svdlut_apply_io on the 4K frame: interleaved 8-bit in and out.  The
-    16-bit input kernels are kept out of the benchmark while an unexplained
-    fault recorded after their launches has no cause found."""
+    """svdlut_apply_io on the 4K frame: interleaved 8-bit in and out, and
+    16-bit inputs (decoded to FP32 by their own kernel, then the FP32-input
+    transform); GB/s counts the call's input and output bytes."""
     H, W = x.shape[-2], x.shape[-1]
     steps = max(3, args.steps // 2)
     grids = algo_bytes_apply(H, W, d, 0)  # the parameter and grid bytes alone
     xh = x.cpu().numpy().reshape(-1, 3, H, W)
     v8 = si.to_u8(xh)
     dv = lambda a: torch.from_numpy(a).to(dev)  # noqa: E731
-    cases = {"u8_hwc->u8_hwc": (dv(si.to_hwc(v8)), "u8_hwc", "u8_hwc", 6)}
+    v16 = np.rint(np.clip(xh, 0.0, 1.0) * 65535.0).astype(np.uint16)
+    cases = {"u8_hwc->u8_hwc": (dv(si.to_hwc(v8)), "u8_hwc", "u8_hwc", 6),
+             "u16->u8": (dv(v16), "u16", "u8", 9),
+             "u16->f32": (dv(v16), "u16", "f32", 18),
+             "u16_hwc->u8_hwc": (dv(si.to_hwc(v16)), "u16_hwc", "u8_hwc", 9)}
     out = {}
     for name, (xin, fi, fo, bpp) in cases.items():
         y = svdlut.apply_io(xin, p, fi, fo)
@@ -430,6 +434,7 @@ def run_io_variant(svdlut, torch, dev, stream, args, x, p, d):
                      "GB/s": round((H * W * bpp + grids) / (ms / 1e3) / 1e9, 1), "io_bytes_per_px": bpp}
         del y
     out["workload"] = f"1x{W}x{H}, D_t=33 rank 8, K=8 grids at 1/8 res; inputs = the headline frame quantised"
+    out["u16_path"] = "u16_decode_kernel to an FP32 frame (stream-ordered buffer), then the FP32-input apply"
     return out
 
 

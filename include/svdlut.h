@@ -426,14 +426,21 @@ typedef enum {
 
 /*
  * svdlut_apply_io -- svdlut_apply between pixel formats: the same transform
- * (Eq. 10, Supp. Eq. 22) with the input decoded and the output encoded inside
- * the kernel.  Supported (input -> output) pairs:
+ * (Eq. 10, Supp. Eq. 22) with the input decoded and the output encoded.
+ * Supported (input -> output) pairs:
  *   F32 -> F32, U8 -> U8 (as svdlut_apply), U16 -> U8, U16 -> F32,
  *   U8_HWC -> U8_HWC, U16_HWC -> U8_HWC.
+ * Interleaved 8-bit frames are decoded and encoded inside the transform
+ * kernel.  16-bit inputs are first decoded (float(v) * float(1 / 65535)) into
+ * an FP32 frame of up to 16 images (up to 16 * 3 * H * W floats), which this
+ * call takes from the device's stream-ordered allocator (cudaMallocAsync /
+ * cudaFreeAsync on `stream`) and returns before it ends on the stream; the
+ * results equal those of the float path on the decoded values.
  * x and y are device arrays of B images of H x W in their formats and must not
  * overlap; float arrays 4-byte aligned, 16-bit arrays 2-byte aligned.  W % 4
  * == 0 with 16-byte aligned arrays enables the vector path.  Errors: those of
- * svdlut_apply; UNSUPPORTED for any other pair of formats.
+ * svdlut_apply; CUDA when the temporary cannot be allocated; UNSUPPORTED for
+ * any other pair of formats.
  */
 svdlut_status svdlut_apply_io(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
                               svdlut_pixfmt in_fmt, const void *x, svdlut_pixfmt out_fmt, void *y,

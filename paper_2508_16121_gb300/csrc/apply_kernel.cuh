@@ -8,8 +8,8 @@
 // access covers 32 adjacent pixels, which keeps the table gathers of smooth
 // regions on few cells), or 4 adjacent pixels for integer pixel formats (one
 // 32- or 64-bit access per plane or word); warp w owns rows w, w + kWarps, ...
-// of the block.  The pixel formats (planar float, 8- and 16-bit, interleaved)
-// are template parameters (Io<In, Out> below).
+// of the block.  The pixel formats (planar float and 8-bit, interleaved
+// 8-bit) are template parameters (Io<In, Out> below).
 //  - Prologue, once per image a CTA meets: the factor rows arrive by
 //    asynchronous copies, the nine 2D LUTs are rebuilt from their SVD factors
 //    (Eq. 9) in shared memory, multiplied by their LUT weights (Eq. 5) and
@@ -285,8 +285,8 @@ struct PixIO<uint8_t> {
 
 // ---- pixel formats of the transform's input and output ----
 // A lane handles 4 adjacent pixels of a tile row (columns lane * 4 + k, k <
-// n), so a whole lane is one 128-bit access per float plane (one 32- or
-// 64-bit access per 8- or 16-bit plane or interleaved word).  `off` is the
+// n), so a whole lane is one 128-bit access per float plane (one 32-bit
+// access per 8-bit plane or interleaved word).  `off` is the
 // offset y * W + x of the lane's first pixel, at(base, off) its address,
 // `plane` = H * W.  load(at(..), plane, ..) fills Raw r[3] with the lane's
 // pixels; unpack() turns them into the channel values (r, g, b) of the 4
@@ -333,47 +333,6 @@ struct InU8 {  // planar 8-bit [3][H][W], value v / 255
     }
 };
 
-// 16-bit code in a 32-bit word (half h) placed in the mantissa of 2^23, minus
-// 2^23: the exact integer as a float (no I2F).
-__device__ __forceinline__ float half_value(unsigned int w, int h)
-{
-    return __int_as_float(__byte_perm(w, 0x4B000000u, h ? 0x7432 : 0x7410)) - 8388608.0f;
-}
-
-// 2 bytes x 4 pixels at p (scalar below 4 pixels or when unaligned)
-__device__ __forceinline__ uint2 load_u16x4(const uint16_t *p, int n, bool vec)
-{
-    if (vec && n == 4) return __ldcs(reinterpret_cast<const uint2 *>(p));
-    unsigned int h[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (k < n) h[k] = __ldcs(reinterpret_cast<const unsigned short *>(p + k));
-    return make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
-}
-
-struct InU16 {  // planar 16-bit [3][H][W], value v / 65535
-    using Raw = uint2;  // one per channel: pixels (0, 1) and (2, 3)
-    static constexpr size_t kPixelBytes = 6, kVecAlign = 8;
-    static __device__ __forceinline__ const void *at(const void *base, size_t off)
-    {
-        return static_cast<const uint16_t *>(base) + off;
-    }
-    static __device__ __forceinline__ void load(const void *q, size_t plane, int n, bool vec, Raw *r)
-    {
-        const uint16_t *p = static_cast<const uint16_t *>(q);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) r[c] = load_u16x4(p + c * plane, n, vec);
-    }
-    static __device__ __forceinline__ void unpack(const Raw *r, float4 (&v)[3])
-    {
-        const float k = 1.0f / 65535.0f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            v[c] = make_float4(half_value(r[c].x, 0) * k, half_value(r[c].x, 1) * k, half_value(r[c].y, 0) * k,
-                               half_value(r[c].y, 1) * k);
-    }
-};
-
 // byte b (0..3) of w as a float in [0, 255] (no I2F)
 __device__ __forceinline__ float byte_value(unsigned int w, int b)
 {
@@ -415,45 +374,6 @@ struct InU8Hwc {  // interleaved 8-bit [H][W][3], value v / 255
                            byte_value(r[2], 2) * k);
         v[2] = make_float4(byte_value(r[0], 2) * k, byte_value(r[1], 1) * k, byte_value(r[2], 0) * k,
                            byte_value(r[2], 3) * k);
-    }
-};
-
-struct InU16Hwc {  // interleaved 16-bit [H][W][3], value v / 65535
-    // 24 bytes of 4 pixels as 6 words: (r0 g0) (b0 r1) | (g1 b1) (r2 g2) | (b2 r3) (g3 b3)
-    using Raw = uint2;
-    static constexpr size_t kPixelBytes = 6, kVecAlign = 8;
-    static __device__ __forceinline__ const void *at(const void *base, size_t off)
-    {
-        return static_cast<const uint16_t *>(base) + 3 * off;
-    }
-    static __device__ __forceinline__ void load(const void *q, size_t, int n, bool vec, Raw *r)
-    {
-        const uint16_t *p = static_cast<const uint16_t *>(q);
-        if (vec && n == 4) {
-            const uint2 *w = reinterpret_cast<const uint2 *>(p);
-            r[0] = __ldcs(w);
-            r[1] = __ldcs(w + 1);
-            r[2] = __ldcs(w + 2);
-            return;
-        }
-        unsigned int w[6] = {0u, 0u, 0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int i = 0; i < 12; ++i)
-            if (i < 3 * n) w[i >> 1] |= static_cast<unsigned int>(__ldcs(reinterpret_cast<const unsigned short *>(p + i)))
-                                        << (16 * (i & 1));
-        r[0] = make_uint2(w[0], w[1]);
-        r[1] = make_uint2(w[2], w[3]);
-        r[2] = make_uint2(w[4], w[5]);
-    }
-    static __device__ __forceinline__ void unpack(const Raw *r, float4 (&v)[3])
-    {
-        const float k = 1.0f / 65535.0f;
-        v[0] = make_float4(half_value(r[0].x, 0) * k, half_value(r[0].y, 1) * k, half_value(r[1].y, 0) * k,
-                           half_value(r[2].x, 1) * k);
-        v[1] = make_float4(half_value(r[0].x, 1) * k, half_value(r[1].x, 0) * k, half_value(r[1].y, 1) * k,
-                           half_value(r[2].y, 0) * k);
-        v[2] = make_float4(half_value(r[0].y, 0) * k, half_value(r[1].x, 1) * k, half_value(r[2].x, 0) * k,
-                           half_value(r[2].y, 1) * k);
     }
 };
 

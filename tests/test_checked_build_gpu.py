@@ -28,15 +28,18 @@ for (B, H, W, d) in [(1, 1, 1, si.spatial_dims(1, 1)), (1, 37, 130, si.spatial_d
     dy = si.make_upstream(6 + H, x.shape)
     g = sv.backward(torch.from_numpy(x).cuda(), pd, torch.from_numpy(dy).cuda())
     torch.cuda.synchronize()
-# pixel formats: interleaved 8-bit, ragged and 4-aligned widths (the 16-bit
-# input kernels are quarantined, see test_io_gpu.py)
+# pixel formats: interleaved 8-bit and 16-bit inputs (decoded to FP32 by
+# their own kernel), ragged and 4-aligned widths
 for (H, W) in [(37, 130), (64, 128), (2160, 3840)]:
     d = si.spatial_dims(H, W)
     x, p = si.make_batch(7 + H, 1, H, W, d)
     pd = sv.to_device(p)
     h8 = torch.from_numpy(si.to_hwc(si.to_u8(x))).cuda()
+    v16 = np.stack([si.make_image_u16(np.random.default_rng(8 + H), H, W)])
     for _ in range(3):
         sv.apply_io(h8, pd, "u8_hwc", "u8_hwc")
+        sv.apply_io(torch.from_numpy(v16).cuda(), pd, "u16", "u8")
+        sv.apply_io(torch.from_numpy(si.to_hwc(v16)).cuda(), pd, "u16_hwc", "u8_hwc")
     torch.cuda.synchronize()
 items = si.make_ragged(seed=9, n=3, sizes=((640, 480), (130, 37), (1, 1)))
 ys = sv.apply_batched([torch.from_numpy(x).cuda() for x, _, _ in items], [sv.to_device(p) for _, _, p in items])
