@@ -72,6 +72,23 @@ def test_u16_to_f32_and_bitwise_equal_to_the_float_path(sv, B, H, W):
     assert np.array_equal(y, yf)
 
 
+@U16
+def test_u16_batches_above_one_decode_chunk(sv):
+    """More images than one decode chunk (16): every chunk is decoded, takes
+    its own images' parameters and writes its own outputs."""
+    B, H, W = 18, 12, 20
+    d, v, p = _case(70, B, H, W)
+    pd = sv.to_device(p)
+    y8 = sv.apply_io(_cuda(v), pd, "u16", "u8").cpu().numpy()
+    _lsb_check(y8, oracle.forward_io(d, p, v, "u16", "u8"))
+    yf = sv.apply_io(_cuda(v), pd, "u16", "f32").cpu().numpy()
+    assert np.abs(yf - oracle.forward_io(d, p, v, "u16", "f32")).max() <= TOL
+    xf = v.astype(np.float32) * (np.float32(1.0) / np.float32(65535.0))
+    assert np.array_equal(yf, sv.apply(_cuda(xf), pd).cpu().numpy())
+    yh = sv.apply_io(_cuda(si.to_hwc(v)), pd, "u16_hwc", "u8_hwc").cpu().numpy()
+    assert np.array_equal(yh, si.to_hwc(y8))
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("B,H,W", SIZES)
 def test_u8_hwc_equals_planar_u8(sv, B, H, W):
