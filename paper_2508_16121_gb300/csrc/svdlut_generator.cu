@@ -1286,22 +1286,23 @@ __device__ __forceinline__ float head_src(const ParamIn &i, int K, int h, int b,
     return *head_dst(o, K, h, b, n);
 }
 
-// dW2, db2: one thread per (h, n), sums over the batch in order.
+// dW2, db2: one thread per (h, n, j) (j = hidden unit; j = 0 also takes db2),
+// each summing over the batch in order.
 __global__ void fc2_wgrad_kernel(const float *__restrict__ hidden, ParamIn d, HeadW hw, int B, int ntot, HeadGrads hg)
 {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ntot; e += gridDim.x * blockDim.x) {
-        int n = e, h = 0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ntot * kHidden; e += gridDim.x * blockDim.x) {
+        int n = e / kHidden, h = 0;
+        const int j = e - n * kHidden;
         while (n >= hw.n[h]) n -= hw.n[h++];
-        float sw[kHidden] = {}, sb = 0.f;
-        for (int b = 0; b < B; ++b) {
+        float sw = 0.f, sb = 0.f;
+#pragma unroll 8
+        for (int b = 0; b < B; ++b) {  // unrolled: independent loads in flight, the same order of sums
             const float g = head_src(d, hw.K, h, b, n);
             sb += g;
-#pragma unroll
-            for (int j = 0; j < kHidden; ++j) sw[j] = fmaf(g, hidden[b * 32 + h * 8 + j], sw[j]);
+            sw = fmaf(g, hidden[b * 32 + h * 8 + j], sw);
         }
-        hg.db2[h][n] = sb;
-#pragma unroll
-        for (int j = 0; j < kHidden; ++j) hg.dw2[h][static_cast<size_t>(n) * kHidden + j] = sw[j];
+        if (j == 0) hg.db2[h][n] = sb;
+        hg.dw2[h][static_cast<size_t>(n) * kHidden + j] = sw;
     }
 }
 
@@ -1311,6 +1312,7 @@ __global__ void __launch_bounds__(256) fc2_dgrad_kernel(ParamIn d, HeadW hw, flo
     __shared__ float red[8];
     const int b = blockIdx.x, h = blockIdx.y;
     float s[kHidden] = {};
+#pragma unroll 4
     for (int n = threadIdx.x; n < hw.n[h]; n += 256) {
         const float g = head_src(d, hw.K, h, b, n);
 #pragma unroll
@@ -1401,18 +1403,29 @@ __global__ void __launch_bounds__(256) in_bwd_sums_kernel(const float *__restric
 }
 
 // pass 2: dz = LeakyReLU'(r) * rstd * gamma * (dA - s2/n - xh s1/n)
+// Four elements per thread (HW % 4 == 0: one plane per quad; float4 I/O).
 __global__ void in_bwd_apply_kernel(const float *__restrict__ da, const float *__restrict__ r, const float *mean,
                                     const float *rstd, const float *gam, const float *sums, int C, int HW, size_t n,
                                     float *__restrict__ dz)
 {
-    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
-         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const size_t bc = e / HW;
-        const int c = static_cast<int>(bc % C);
-        const float rs = rstd[bc], xh = (r[e] - mean[bc]) * rs;
-        const float inv = 1.f / HW;
-        const float dr = rs * gam[c] * (da[e] - sums[2 * bc + 1] * inv - xh * sums[2 * bc] * inv);
-        dz[e] = r[e] > 0.f ? dr : kSlope * dr;
+    const float inv = 1.f / HW;
+    const size_t n4 = n / 4;
+    for (size_t e4 = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e4 < n4;
+         e4 += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const unsigned int bc = static_cast<unsigned int>(4 * e4 / static_cast<unsigned int>(HW));
+        const int c = static_cast<int>(bc % static_cast<unsigned int>(C));
+        const float rs = rstd[bc], mu = mean[bc], g = rs * gam[c];
+        const float s0 = sums[2 * bc], s1 = sums[2 * bc + 1];
+        const float4 a = reinterpret_cast<const float4 *>(da)[e4], x = reinterpret_cast<const float4 *>(r)[e4];
+        const float av[4] = {a.x, a.y, a.z, a.w}, xv[4] = {x.x, x.y, x.z, x.w};
+        float o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float xh = (xv[u] - mu) * rs;
+            const float dr = g * (av[u] - s1 * inv - xh * s0 * inv);
+            o[u] = xv[u] > 0.f ? dr : kSlope * dr;
+        }
+        reinterpret_cast<float4 *>(dz)[e4] = make_float4(o[0], o[1], o[2], o[3]);
     }
 }
 
@@ -1639,7 +1652,8 @@ extern "C" svdlut_status svdlut_generator_backward(int K, const float *weights, 
     const ParamIn pin{dparams->U, dparams->S, dparams->V, dparams->lut_w, dparams->g_xy, dparams->g_xc,
                       dparams->g_yc, dparams->grid_w};
     const int ntot = L.head_n[0] + L.head_n[1] + L.head_n[2] + L.head_n[3];
-    fc2_wgrad_kernel<<<blocks_for(ntot), 256, 0, s>>>(w + wl.hidden, pin, hw, B, ntot, hg);
+    fc2_wgrad_kernel<<<blocks_for(static_cast<size_t>(ntot) * kHidden), 256, 0, s>>>(w + wl.hidden, pin, hw, B, ntot,
+                                                                                    hg);
     fc2_dgrad_kernel<<<dim3(B, 4), 256, 0, s>>>(pin, hw, w + wl.dhid);
     fc1_bwd_kernel<<<(std::max(4 * kHidden * kRho, B * kRho) + 255) / 256, 256, 0, s>>>(
         w + wl.rho, w + wl.dhid, hw, B, hg, w + wl.drho);
@@ -1706,7 +1720,7 @@ extern "C" svdlut_status svdlut_generator_backward(int K, const float *weights, 
         in_bwd_sums_kernel<<<B * Cin, 256, 0, s>>>(dact, w + wl.r[j], w + wl.mean[j], w + wl.rstd[j], S * S,
                                                    w + wl.insum);
         const size_t n = act_size(B, j);
-        in_bwd_apply_kernel<<<blocks_for(n), 256, 0, s>>>(dact, w + wl.r[j], w + wl.mean[j], w + wl.rstd[j],
+        in_bwd_apply_kernel<<<blocks_for(n / 4), 256, 0, s>>>(dact, w + wl.r[j], w + wl.mean[j], w + wl.rstd[j],
                                                           weights + L.in_g[j], w + wl.insum, Cin, S * S, n, dz_next);
         in_param_grad_kernel<<<1, 64, 0, s>>>(w + wl.insum, B, Cin, dweights + L.in_g[j], dweights + L.in_b[j]);
         SVDLUT_CUDA_TRY(cudaGetLastError());
