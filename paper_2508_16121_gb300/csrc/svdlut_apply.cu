@@ -116,6 +116,33 @@ extern "C" svdlut_status svdlut_apply_ws(const svdlut_dims *dims, const svdlut_p
     return apply_impl(dims, params, B, H, W, dtype, x, y, cfg ? cfg->ctas : 0, ws, ws_bytes, stream);
 }
 
+// The launches of a planned batch, N images each: the per-image tables first
+// (prep_kernel) when a workspace is given, then apply_kernel.
+template <int N>
+static svdlut_status apply_chunks(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
+                                  svdlut_dtype dtype, const void *x, void *y, int n_cta, void *ws, size_t per_img,
+                                  const DeviceInfo &di, cudaStream_t s)
+{
+    svdlut_status st = SVDLUT_OK;
+    for (int b0 = 0; b0 < B; b0 += N) {
+        LaunchArgs<N> a{};
+        a.n = std::min(N, B - b0);
+        for (int i = 0; i < a.n; ++i) {
+            a.img[i] = make_desc(dims, params, b0 + i, H, W, dtype, x, y);
+            if (ws) set_prep_tables(a.img[i], dims, static_cast<char *>(ws) + static_cast<size_t>(b0 + i) * per_img);
+        }
+        size_t smem = 0;
+        if ((st = plan_uniform(a, n_cta, static_cast<size_t>(di.max_smem_optin), &smem)) != SVDLUT_OK)
+            return st;
+        if (ws) {
+            if ((st = launch_prep(a, di.sm_count, s)) != SVDLUT_OK) return st;
+            a.pre = 1;
+        }
+        if ((st = launch_apply(a, smem, dtype, s, n_cta)) != SVDLUT_OK) return st;
+    }
+    return SVDLUT_OK;
+}
+
 static svdlut_status apply_impl(const svdlut_dims *dims, const svdlut_params *params, int B, int H, int W,
                                 svdlut_dtype dtype, const void *x, void *y, int ctas, void *ws, size_t ws_bytes,
                                 svdlut_stream_t stream)
@@ -149,21 +176,8 @@ static svdlut_status apply_impl(const svdlut_dims *dims, const svdlut_params *pa
     if ((st = device_info(&di)) != SVDLUT_OK) return st;
     const int n_cta = ctas > 0 ? std::min(ctas, di.sm_count) : di.sm_count;  // persistent CTAs to plan for
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    for (int b0 = 0; b0 < B; b0 += kPlainChunk) {
-        LaunchArgs<kPlainChunk> a{};
-        a.n = std::min(kPlainChunk, B - b0);
-        for (int i = 0; i < a.n; ++i) {
-            a.img[i] = make_desc(dims, params, b0 + i, H, W, dtype, x, y);
-            if (ws) set_prep_tables(a.img[i], dims, static_cast<char *>(ws) + static_cast<size_t>(b0 + i) * per_img);
-        }
-        size_t smem = 0;
-        if ((st = plan_uniform(a, n_cta, static_cast<size_t>(di.max_smem_optin), &smem)) != SVDLUT_OK)
-            return st;
-        if (ws) {
-            if ((st = launch_prep(a, di.sm_count, s)) != SVDLUT_OK) return st;
-            a.pre = 1;
-        }
-        if ((st = launch_apply(a, smem, dtype, s, n_cta)) != SVDLUT_OK) return st;
-    }
-    return SVDLUT_OK;
+    // up to 16 images per launch, or 64 when the batch is larger (fewer launches
+    // and table precomputations for batches of small images)
+    return B > kPlainChunk ? apply_chunks<kRaggedMax>(dims, params, B, H, W, dtype, x, y, n_cta, ws, per_img, di, s)
+                           : apply_chunks<kPlainChunk>(dims, params, B, H, W, dtype, x, y, n_cta, ws, per_img, di, s);
 }
