@@ -166,3 +166,20 @@ def test_header_is_plain_c():
     assert r.returncode == 0, r.stderr
     r = subprocess.run([cc, "-fsyntax-only", "-x", "c++", "-Wall", "-Werror", hdr], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_generator_workspace_size_holds_the_activations(lib):
+    """svdlut_generator_workspace_size (host-only): 0 for invalid K or B,
+    whole 256-byte units, growing with the batch, and at least the thumbnail
+    and the five convolution activations that the backward pass reads back
+    (channels 8/16/32/64/64 at 128..8 pixels square, Supp. A, Table 8)."""
+    assert lib.svdlut_generator_workspace_size(-1, 4) == 0
+    assert lib.svdlut_generator_workspace_size(8, 0) == 0
+    ch, sz = [8, 16, 32, 64, 64], [128, 64, 32, 16, 8]
+    prev = 0
+    for B in (1, 2, 3, 17, 64):
+        n = lib.svdlut_generator_workspace_size(8, B)
+        assert n % 256 == 0 and n > prev
+        floats = B * 3 * 256 * 256 + sum(B * c * s * s for c, s in zip(ch, sz))
+        assert n >= 4 * floats
+        prev = n
