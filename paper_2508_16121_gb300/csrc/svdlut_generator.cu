@@ -96,7 +96,7 @@ inline int wgrad_tiles(int i) { return wgrad_sets(i) > 1 ? 1 : (kCh[i] * 9 + 1 +
 inline int wgrad_chunk_px(int B, int i)
 {
     const int pix = B * kSz[i + 1] * kSz[i + 1], st = 64 * wgrad_sets(i);
-    const int ctas = 2 * 152;  // resident CTAs (two per SM) x SMs
+    const int ctas = (wgrad_np_layer(i) == 16 && wgrad_sets(i) == 1 ? 3 : 2) * 152;  // resident CTAs x SMs
     const int want = std::max(1, (ctas + wgrad_tiles(i) - 1) / wgrad_tiles(i));
     const int px = (pix + want - 1) / want;
     return std::max(st, (px + st - 1) / st * st);
@@ -243,7 +243,10 @@ __global__ void downsample_kernel(const float *__restrict__ x, int B, int H, int
 // bias row, the padding rows of the tile and of N) are written once.  Every
 // wait is bounded: on expiry the outputs are NaN and g_umma_timeouts counts
 // the warp.
-constexpr int kWT = 512;     // threads (staging); warps w < 8 read TMEM lanes 32 (w % 4) .. + 31
+// threads of a weight-gradient CTA (staging; warps w < 8 read TMEM lanes
+// 32 (w % 4) .. + 31): 512, two CTAs per SM; 256 (three per SM) for the
+// 16-channel layer with one subset, whose stages fit three CTAs
+__host__ __device__ constexpr int wgrad_threads(int NP, int SETS) { return NP == 16 && SETS == 1 ? 256 : 512; }
 constexpr int kWK = 64;      // pixels per stage (four K steps of 16)
 constexpr int kWRows = 126;  // columns j per tile
 __device__ unsigned int g_umma_timeouts;
@@ -331,10 +334,11 @@ constexpr int wgrad_ctas_per_sm(int NP) { return (227 * 1024) / (2 * wgrad_stage
 // subsets' partial sums (the others are discarded), written as chunks
 // SETS z + r.
 template <int NP, int SETS>
-__global__ void __launch_bounds__(kWT, 2) wgrad_kernel(const WgradArgs p)
+__global__ void __launch_bounds__(wgrad_threads(NP, SETS), wgrad_threads(NP, SETS) == 256 ? 3 : 2) wgrad_kernel(const WgradArgs p)
 {
     static_assert(NP % 16 == 0 && NP >= 16 && NP <= 64, "N of an M = 128 MMA: 16 .. 64, multiple of 16");
     static_assert(SETS == 1 || SETS == 4, "one subset (126-column tiles) or four (32 rows each)");
+    constexpr int kWT = wgrad_threads(NP, SETS);
     constexpr int RS = SETS == 1 ? kWRows : 128 / SETS;  // rows of one subset
     constexpr uint32_t kCols = NP < 32 ? 32 : NP;  // TMEM columns (power of 2 >= 32)
     constexpr int kA = 128 * kWK * 2, kB = NP * kWK * 2, kStage = wgrad_stage_bytes(NP);
@@ -1127,7 +1131,7 @@ static svdlut_status launch_wgrad(const WgradArgs &a, int tiles, int chunks, cud
     constexpr int smem = 2 * wgrad_stage_bytes(NP);
     const svdlut_status st = smem_opt_in(reinterpret_cast<const void *>(wgrad_kernel<NP, SETS>), smem);
     if (st != SVDLUT_OK) return st;
-    wgrad_kernel<NP, SETS><<<dim3(tiles, chunks), kWT, smem, s>>>(a);
+    wgrad_kernel<NP, SETS><<<dim3(tiles, chunks), wgrad_threads(NP, SETS), smem, s>>>(a);
     SVDLUT_CUDA_TRY(cudaGetLastError());
     return SVDLUT_OK;
 }
