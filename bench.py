@@ -64,18 +64,37 @@ def kernel_hash(read=None) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu counters, if they were
-    taken on the current kernel sources (else None)."""
+def profiled_counters():
+    """The committed ncu counters of the headline kernel, if they were taken
+    on the current kernel sources (else None)."""
     try:
         with open(os.path.join(ROOT, PROFILE_COUNTERS)) as f:
             j = json.load(f)
     except (OSError, ValueError):
         return None
-    if j.get("kernel_sources_sha256_16") != kernel_hash():
+    if not isinstance(j, dict) or j.get("kernel_sources_sha256_16") != kernel_hash():
         return None
-    v = j.get("dram_bytes_per_launch")
+    return j
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu counters (None unless
+    taken on the current kernel sources)."""
+    j = profiled_counters()
+    v = j.get("dram_bytes_per_launch") if j else None
     return int(v) if isinstance(v, (int, float)) else None
+
+
+def profiled_limiter():
+    """The resource that bounds the headline kernel, from the same counters:
+    shared-memory (LSU) wavefronts as a fraction of their peak."""
+    j = profiled_counters()
+    v = j.get("lsu_wavefronts_pct_of_peak") if j else None
+    if not isinstance(v, (int, float)):
+        return None
+    return {"resource": "L1 LSU data-pipe wavefronts (shared-memory gathers)", "frac": round(v / 100.0, 3),
+            "shared_wavefronts_per_pixel": j.get("shared_wavefronts_per_pixel"),
+            "source": "ncu l1tex__data_pipe_lsu_wavefronts, " + PROFILE_COUNTERS}
 
 
 def peaks():
@@ -358,6 +377,7 @@ def run_ours(args, world, rank, local):
                    "l2": f"rotating {N_SETS} input/output sets ({N_SETS * bytes_launch / 1e6:.0f} MB) > 129 MB L2"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                     "limiter": profiled_limiter(),
                      "kernel": "apply_kernel<Io<InF32, OutF32>, 16, false>",
                      "timed": "CUDA events around the K back-to-back calls of the timed region, per call "
                               "(prep_kernel + apply_kernel)",

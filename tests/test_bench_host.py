@@ -96,7 +96,13 @@ def test_spread_and_profiled_traffic(tmp_path, monkeypatch):
     monkeypatch.setattr(b, "kernel_hash", lambda read=None: "abc")
     counters.write_text(json.dumps({"kernel_sources_sha256_16": "abc", "dram_bytes_per_launch": 123}))
     assert b.profiled_traffic() == 123
-    counters.write_text(json.dumps({"kernel_sources_sha256_16": "old", "dram_bytes_per_launch": 123}))
-    assert b.profiled_traffic() is None
+    assert b.profiled_limiter() is None  # no limiter counters recorded
+    counters.write_text(json.dumps({"kernel_sources_sha256_16": "abc", "dram_bytes_per_launch": 123,
+                                    "lsu_wavefronts_pct_of_peak": 76.0, "shared_wavefronts_per_pixel": 2.86}))
+    lim = b.profiled_limiter()
+    assert lim["frac"] == 0.76 and lim["shared_wavefronts_per_pixel"] == 2.86
+    counters.write_text(json.dumps({"kernel_sources_sha256_16": "old", "dram_bytes_per_launch": 123,
+                                    "lsu_wavefronts_pct_of_peak": 76.0}))
+    assert b.profiled_traffic() is None and b.profiled_limiter() is None
     counters.write_text("not json")
     assert b.profiled_traffic() is None
