@@ -70,6 +70,19 @@ def test_batch_larger_than_one_launch_chunk(sv):
     check_f32(sv, d, x, p)
 
 
+def test_batches_of_64_image_launches_equal_16_image_launches(sv):
+    """Batches above 16 images are launched 64 at a time (70 images: two
+    launches); each image's result equals the oracle and, bit for bit, the
+    same image transformed in a batch of at most 16 (the 16-image launch)."""
+    d = si.spatial_dims(12, 40)
+    x, p = si.make_batch(12, 70, 12, 40, d)
+    y = run(sv, x, p)
+    assert np.abs(y.astype(np.float64) - oracle.forward(d, p, x)).max() <= TOL
+    for b0, b1 in ((0, 16), (60, 70)):
+        part = {k: v[b0:b1] for k, v in p.items()}
+        assert np.array_equal(run(sv, np.ascontiguousarray(x[b0:b1]), part), y[b0:b1])
+
+
 def test_identity_reproduces_input(sv):
     d = si.spatial_dims(40, 300)
     x = si.make_image(np.random.default_rng(3), 40, 300)
