@@ -274,8 +274,10 @@ size_t svdlut_backward_workspace_size(const svdlut_dims *dims, int B, int H, int
  * the 2D bilateral grids (K x 3 planes of 17x17), their weights (K x 4), the
  * SVD factors of the nine 2D LUTs (D_t = 33, rank 8: U, S, V) and the LUT
  * weights (3 x 4).  Its outputs are the svdlut_params of svdlut_apply with
- * dims {33, 8, K, 17, 17, 17}.  Convolutions run on BF16 tensor cores with
- * FP32 accumulation; all other arithmetic is FP32.
+ * dims {33, 8, K, 17, 17, 17}.  The convolutions run on the tensor cores
+ * (tcgen05) with FP32 accumulation: BF16 operands in the forward pass,
+ * split-BF16 operands (about 16 mantissa bits) for the weight and input
+ * gradients; all other arithmetic is FP32.
  *
  * Weights: one FP32 device array of svdlut_generator_param_count(K) floats,
  * in this order: for conv i = 0..4: w [Cout][Cin][3][3], b [Cout], and for
