@@ -840,15 +840,19 @@ struct DgradUmma {
 constexpr int kDGT = 128;  // threads: pixel tid of the tile, all eight octets of a stage
 __host__ __device__ constexpr int dgrad_stage_bytes(int NP) { return 2 * (128 + NP) * kWK * 2; }
 
-template <int NP>
-__global__ void __launch_bounds__(kDGT, NP == 64 ? 4 : 6) dgrad_umma_kernel(const DgradUmma p)
+// NBUF stage buffers: 2 for the widest layer (up to four K stages per class,
+// 128 CTAs), 1 for the others, whose many CTAs need the occupancy more than
+// the overlap (measured: two buffers slowed the 32-channel layer 23 -> 31 us).
+template <int NP, int NBUF>
+__global__ void __launch_bounds__(kDGT, NBUF == 2 ? 2 : (NP == 64 ? 4 : 6)) dgrad_umma_kernel(const DgradUmma p)
 {
+    static_assert(NBUF == 1 || NBUF == 2, "one or two stage buffers");
     static_assert(NP % 16 == 0 && NP >= 16 && NP <= 64, "N of an M = 128 MMA: 16 .. 64, multiple of 16");
     constexpr uint32_t kCols = NP < 32 ? 32 : NP;
     constexpr int kA = 128 * kWK * 2, kB = NP * kWK * 2;  // one part (hi or lo) of A / B
     constexpr uint32_t idesc = umma_idesc_bf16(128, NP);
-    extern __shared__ __align__(128) char dsm[];  // [A hi][A lo][B hi][B lo]
-    __shared__ __align__(8) uint64_t mbar;
+    extern __shared__ __align__(128) char dsm0[];  // stage s % NBUF: [A hi][A lo][B hi][B lo]
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t taddr_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = blockIdx.x, cls = blockIdx.y, py = cls >> 1, px = cls & 1, ntx = px ? 2 : 1;
@@ -873,7 +877,8 @@ __global__ void __launch_bounds__(kDGT, NP == 64 ? 4 : 6) dgrad_umma_kernel(cons
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;\n");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -882,7 +887,9 @@ __global__ void __launch_bounds__(kDGT, NP == 64 ? 4 : 6) dgrad_umma_kernel(cons
     const uint32_t taddr = taddr_s;
     bool ok = true;
     for (int s = 0; s < nst; ++s) {
-        if (s >= 1) ok = mbar_wait(smem_addr(&mbar), (s - 1) & 1) && ok;  // stage s - 1 read
+        const int buf = s % NBUF;
+        char *dsm = dsm0 + buf * dgrad_stage_bytes(NP);
+        if (s >= NBUF) ok = mbar_wait(smem_addr(&mbar[buf]), ((s - NBUF) / NBUF) & 1) && ok;  // stage s - NBUF read
         // B: hi and lo parts of this stage, contiguous in the prepared layout
         const uint4 *whi = wcls + static_cast<size_t>(s) * NP * 8, *wlo = whi + static_cast<size_t>(kpad) * NP / 8;
         for (int e = tid; e < NP * 8; e += kDGT) {
@@ -924,11 +931,11 @@ __global__ void __launch_bounds__(kDGT, NP == 64 ? 4 : 6) dgrad_umma_kernel(cons
                 umma_bf16(taddr, ahi, bhi, idesc, 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             smem_addr(&mbar))
+                             smem_addr(&mbar[buf]))
                          : "memory");
         }
     }
-    if (nst > 0) ok = mbar_wait(smem_addr(&mbar), (nst - 1) & 1) && ok;  // all MMAs
+    if (nst > 0) ok = mbar_wait(smem_addr(&mbar[(nst - 1) % NBUF]), ((nst - 1) / NBUF) & 1) && ok;  // all MMAs
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     if (!ok && lane == 0) atomicAdd(&g_umma_timeouts, 1u);
     // epilogue: thread tid holds pixel tid of the tile (TMEM lane), all NP channels
@@ -1146,13 +1153,13 @@ static svdlut_status launch_conv_t(const ConvUmma &a, dim3 grid, cudaStream_t s)
     if (st != SVDLUT_OK) return st;
     return launch_pdl(conv_umma_kernel<NP, C8, NT, NBUF>, grid, dim3(NT), smem, s, a);
 }
-template <int NP>
+template <int NP, int NBUF>
 static svdlut_status launch_dgrad_t(const DgradUmma &a, cudaStream_t s)
 {
-    constexpr int smem = dgrad_stage_bytes(NP);
-    const svdlut_status st = smem_opt_in(reinterpret_cast<const void *>(dgrad_umma_kernel<NP>), smem);
+    constexpr int smem = NBUF * dgrad_stage_bytes(NP);
+    const svdlut_status st = smem_opt_in(reinterpret_cast<const void *>(dgrad_umma_kernel<NP, NBUF>), smem);
     if (st != SVDLUT_OK) return st;
-    dgrad_umma_kernel<NP><<<dim3((a.M + 127) / 128, 4), kDGT, smem, s>>>(a);
+    dgrad_umma_kernel<NP, NBUF><<<dim3((a.M + 127) / 128, 4), kDGT, smem, s>>>(a);
     SVDLUT_CUDA_TRY(cudaGetLastError());
     return SVDLUT_OK;
 }
@@ -1716,7 +1723,8 @@ extern "C" svdlut_status svdlut_generator_backward(int K, const float *weights, 
                 off += static_cast<size_t>(2) * wgrad_np(Cin) * da.kpad[c];
             }
             const int np = wgrad_np(Cin);
-            st = np == 16 ? launch_dgrad_t<16>(da, s) : np == 32 ? launch_dgrad_t<32>(da, s) : launch_dgrad_t<64>(da, s);
+            st = np == 16 ? launch_dgrad_t<16, 1>(da, s)
+                          : np == 32 ? launch_dgrad_t<32, 1>(da, s) : launch_dgrad_t<64, 2>(da, s);
             if (st != SVDLUT_OK) return st;
         }
         const int j = i - 1;
