@@ -26,11 +26,12 @@ Pinned (tests/test_oracle_generator.py): the parameter count (Table 6 and its
 ablation rows) of param_layout; conv against brute force on tiny inputs;
 downsample, inorm and avgpool4 against their defining invariants;
 splitmix64 against the published SplitMix64 outputs; backward against
-central differences of forward.  "Parity unpinned", function by function,
-because every pin above still passes if the reading is changed:
-  forward          the order conv -> LeakyReLU -> InstanceNorm within a layer
-                   (LeakyReLU and InstanceNorm swapped would pass), the slope
-                   0.2, eps 1e-5, and dropout before the pool;
+central differences of forward; in forward, InstanceNorm as the last step of
+layers 0-3 (each plane leaves with mean beta_c and variance at most
+gamma_c^2) and dropout on the 8x8 features before the pool (one dropped
+element moves one pooled feature by -2a/16).  "Parity unpinned", function by
+function, because every pin above still passes if the reading is changed:
+  forward          the slope 0.2 and eps 1e-5;
   heads_to_params  the split of each head's output (U, S, V order and the
   params_to_heads  [c][pair] / [K][plane] layouts: a swapped U and V block
                    would pass);

@@ -197,3 +197,63 @@ def test_bf16_operand_sensitivity_is_within_half_the_gpu_bounds():
         for n in g64:
             den = max(np.linalg.norm(g64[n]), 1e-30)
             assert np.linalg.norm(gb[n] - g64[n]) / den <= 0.5 * grad_group_bound(n), n
+
+
+def _blob_with_random_norms(K, seed):
+    """identity-biased blob with noise, and InstanceNorm scales and shifts
+    drawn away from (1, 0), so that the invariants below are not trivial"""
+    rng = np.random.default_rng(seed)
+    blob = G.identity_blob(K, rng, scale=0.05)
+    blob = blob + rng.normal(0, 0.05, size=blob.shape)
+    o = 0
+    for name, shape in G.param_layout(K):
+        n = int(np.prod(shape))
+        if name.startswith("in") and name.endswith(".g"):
+            blob[o:o + n] = rng.uniform(0.5, 2.0, size=n)
+        elif name.startswith("in") and name.endswith(".b"):
+            blob[o:o + n] = rng.uniform(-1.0, 1.0, size=n)
+        o += n
+    return blob
+
+
+def test_instance_norm_is_the_last_step_of_each_of_the_first_four_layers():
+    """Layer order conv -> LeakyReLU -> InstanceNorm (Supp. A, Table 8): the
+    input of layers 1-4 is a normalised plane, so per (b, c) its mean is the
+    shift beta_c and its biased variance gamma_c^2 v / (v + eps), v the
+    plane's variance before the norm: at most gamma_c^2.  With the norm
+    before the LeakyReLU the planes' means would not be beta_c."""
+    import svdlut_inputs as si
+    K = 4
+    blob = _blob_with_random_norms(K, 70)
+    p = G.unpack(blob, K)
+    x = np.stack([si.make_image(np.random.default_rng(71 + j), 64, 80) for j in range(2)])
+    _, cache = G.forward(blob, x, K)
+    for i in range(4):
+        a = cache["acts"][i + 1][0]  # the input of layer i + 1 = the output of layer i
+        g, b = p[f"in{i}.g"], p[f"in{i}.b"]
+        assert np.allclose(a.mean(axis=(2, 3)), b[None, :], atol=1e-10)
+        var = a.var(axis=(2, 3))
+        assert np.all(var <= g[None, :] ** 2 * (1 + 1e-12))
+        assert np.all(var >= 0.5 * g[None, :] ** 2)  # eps is small against these planes' variance
+
+
+def test_dropout_acts_on_the_8x8_features_before_the_4x4_pool():
+    """Dropping one element (b, c, y, x) of the [B][64][8][8] mask changes one
+    pooled feature, rho[b][4 c + 2 (y // 4) + x // 4], by -2 a / 16 (a the
+    activation there, 2 the keep scale) and leaves every other feature."""
+    import svdlut_inputs as si
+    K = 4
+    blob = _blob_with_random_norms(K, 80)
+    x = np.stack([si.make_image(np.random.default_rng(81 + j), 64, 80) for j in range(2)])
+    keep = np.full((2, 64, 8, 8), 2.0)
+    _, c1 = G.forward(blob, x, K, drop_mask=keep)
+    b, c, y, xx = 1, 37, 5, 2
+    drop = keep.copy()
+    drop[b, c, y, xx] = 0.0
+    _, c2 = G.forward(blob, x, K, drop_mask=drop)
+    d = c2["rho"] - c1["rho"]
+    a = G.lrelu(c1["acts"][4][1])[b, c, y, xx]  # the last layer's activation (no norm)
+    k = 4 * c + 2 * (y // 4) + xx // 4
+    assert np.isclose(d[b, k], -2.0 * a / 16.0, rtol=0, atol=1e-12)
+    d[b, k] = 0.0
+    assert np.abs(d).max() == 0.0
