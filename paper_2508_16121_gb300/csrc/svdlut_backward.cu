@@ -131,11 +131,12 @@ struct BwdArgs {
 // LUT gradients: G^c_p[i][j] = sum_px dy_c * bilinear weight of vertex (i, j)
 // at (x_alpha, x_beta) for pair p = (alpha, beta).
 // grid (P, B); CTA (p, b) owns the rows [p H / P, (p+1) H / P) of image b.
-// Its work units are (128-column strip, row slice): the rows are cut into
-// slices = max(1, 4 / strips) slices, so that narrow images keep all four
-// warp groups busy.  Warp (group g, pair q) takes the units g, g + 4, ... and
-// walks down the rows of each; lane l takes columns l + 32 k (k = 0..3:
-// coalesced loads) and keeps, per column, the four corner contributions
+// Its work is the sequence of (128-column strip, row) pairs, strip by strip;
+// warp group g takes the g-th quarter of it (equal shares to within one row,
+// whatever the number of strips: a piece of a strip, whole strips, a piece of
+// the next).  Warp (group g, pair q) walks down the rows of each of its
+// pieces; lane l takes columns l + 32 k (k = 0..3: coalesced loads) and
+// keeps, per column, the four corner contributions
 // (three channels each) of its current cell in registers: while the cell
 // does not change (smooth regions, where consecutive rows fall in the same
 // cell) it only accumulates; when it changes, the warp scatters the finished
@@ -173,10 +174,13 @@ __global__ void __launch_bounds__(kLutThreads, 1)
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc[k][q][c] = 0.f;
-    const int slices = max(1, kGroups / a.strips), units = a.strips * slices;
-    for (int u = grp; u < units; u += kGroups) {
-        const int strip = u % a.strips, sl = u / a.strips;
-        const int ra = r0 + (r1 - r0) * sl / slices, rb = r0 + (r1 - r0) * (sl + 1) / slices;
+    const long long nrows = r1 - r0, T = static_cast<long long>(a.strips) * nrows;
+    const long long t1 = T * (grp + 1) / kGroups;
+    for (long long t = T * grp / kGroups; t < t1;) {
+        const int strip = static_cast<int>(t / nrows);
+        const long long s0 = strip * nrows;
+        const int ra = r0 + static_cast<int>(t - s0), rb = r0 + static_cast<int>(min(t1 - s0, nrows));
+        t = s0 + nrows;
         const int x = strip * kTileW + lane;
         const int n = x < a.W ? min(4, (a.W - x + 31) >> 5) : 0;  // this lane's columns x + 32 k, k < n
         struct Row {
@@ -229,7 +233,7 @@ __global__ void __launch_bounds__(kLutThreads, 1)
             cur = nx1;
             nx1 = nx2;
         }
-        // the unit's runs end here
+        // the piece's runs end here
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             warp_scatter<3, true>(tab, acc_key[k], D * 4, 4, acc[k]);
@@ -745,16 +749,15 @@ static svdlut_status plan_backward(const svdlut_dims *d, int B, int H, int W, in
     pl->lut_smem = sizeof(float) * (static_cast<size_t>(kLutWarps) * 4 * D * D + kLutWarps);
     if (pl->lut_smem > smem_limit) return fail(SVDLUT_ERR_UNSUPPORTED, "D_t=%d too large for the adjoint", D);
     // LUT pass: P CTAs per image (one CTA per SM); estimated time = waves x
-    // (rows a warp group walks + a fixed cost of about 16 rows per CTA:
-    // clearing the tables, writing the partial)
+    // (rows a warp group walks: a quarter of strips x rows, + a fixed cost of
+    // about 16 rows per CTA: clearing the tables, writing the partial)
     {
-        const int strips = (W + kTileW - 1) / kTileW, G = kLutWarps / 3;
-        const int slices = std::max(1, G / strips), per_units = (strips * slices + G - 1) / G;
+        const long long strips = (W + kTileW - 1) / kTileW, G = kLutWarps / 3;
         long long best_cost = -1;
         for (int P = 1; P <= std::min(H, 4 * sm_count); ++P) {
             const long long waves = (static_cast<long long>(B) * P + sm_count - 1) / sm_count;
-            const int rows = (H + P - 1) / P;
-            const long long cost = waves * (static_cast<long long>(per_units) * ((rows + slices - 1) / slices) + 16);
+            const long long rows = (H + P - 1) / P;
+            const long long cost = waves * ((strips * rows + G - 1) / G + 16);
             if (best_cost < 0 || cost < best_cost) {
                 best_cost = cost;
                 pl->P = P;
