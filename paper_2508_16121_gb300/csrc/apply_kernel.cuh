@@ -869,9 +869,16 @@ __device__ inline void setup_pre(const ImgDesc &d, const BlockGeom &g, const Blo
     const float *pxy = d.pfold, *pxc = pxy + 3 * static_cast<size_t>(Dsy) * Dsx,
                 *pyc = pxc + 3 * static_cast<size_t>(Dsx) * Dsc;
     if (rebuild) {
+        // Every CTA copies the same table: each starts at its own place in it
+        // (evenly spread over the CTAs), so that at any moment the copies
+        // read different lines rather than all CTAs the same ones.
         const float4 *src = reinterpret_cast<const float4 *>(d.pcell);
         const int n4 = lcell_floats(d.D) / 4;
-        for (int e = tid; e < n4; e += kThreads) cp_async16(lcell + e, src + e);
+        const int rot = static_cast<int>((static_cast<long long>(n4) * blockIdx.x) / gridDim.x);
+        for (int e = tid; e < n4; e += kThreads) {
+            const int f = e + rot < n4 ? e + rot : e + rot - n4;
+            cp_async16(lcell + f, src + f);
+        }
         if (tid < 3) misc[kMaxK * 4 + tid] = __ldg(d.pfold + pfold_floats(Dsx, Dsy, Dsc) + tid);
     }
     const int nxy = nvy * nvx, nxc = nvx * Dsc, nyc = nvy * Dsc, oxy = 3 * nxy, oxc = 3 * nxc;
