@@ -668,9 +668,11 @@ def run_learned_variant(svdlut, torch, dev, stream, args):
             "speedup_vs_plain_host_factors": round(t_h / t_l, 3),
             "serving_pipelined": {"value": round(mpix / (t_pipe / 1e3), 1), "unit": "Mpix/s",
                                   "ms_per_batch": round(t_pipe, 4),
-                                  "how": f"{T} batches per graph; generator of batch t+1 on {free_sms} SMs "
-                                         "overlapping the transform of batch t (svdlut_apply_cfg, persistent "
-                                         "CTAs on the rest)",
+                                  "how": f"{T} batches per graph; the generator of batch t+1 on its own "
+                                         "stream, overlapping the transform of batch t" +
+                                         (f" (svdlut_apply_cfg: persistent CTAs on all but {free_sms} SMs)"
+                                          if free_sms else " (the transform's CTAs on every SM: the fastest "
+                                          "of 0-24 SMs left free)"),
                                   "speedup_vs_plain_graph": round(t_p / t_pipe, 3)},
             "train_step_ms_batch64_256px": round(t_tr, 3),
             "train_loss": "MSE + 0.005 CIE94 (Eq. 11 without LPIPS)",
