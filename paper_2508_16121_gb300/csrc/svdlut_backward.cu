@@ -13,7 +13,8 @@
 //                (xy, xc, yc per output channel) over 128-px column blocks.
 //   4. reduce  : lut_finalize_kernel sums the CTA partials and contracts
 //                through T = U diag(S) V^T (Eq. 9) to dU, dS, dV, dlut_w;
-//                grid_reduce_kernel + grid_finalize_kernel give dg_* and dgrid_w.
+//                grid_reduce_kernel sums the block partials per vertex into dg_*
+//                and per-CTA partials of dgrid_w, grid_wsum_kernel sums those.
 #include <algorithm>
 #include <mutex>
 #include <utility>
@@ -566,14 +567,27 @@ __global__ void __launch_bounds__(kFinThreads)
 }
 
 // ---------------------------------------------------------------------------
-// grid reduce: dF planes per image from the block partials (fixed order over
-// the blocks covering each vertex).  dF layout per image:
-//   xy [Dsy][Dsx][3], xc [3][Dsx][Dsc], yc [3][Dsy][Dsc].
+// grid reduce and finalize, fused.  A CTA takes a slice of kGRChunk vertices
+// of one folded plane (xy, xc or yc) of one output channel c of one image.
+// Per vertex it sums the partials of the blocks whose footprint holds the
+// vertex (bands, then strips, in order), which is dF_c at that vertex; then
+// for every grid k with k mod 3 = c it writes dg^k_plane = w^k_plane dF_c
+// (Supp. Eqs. 21-22: grid k feeds channel k mod 3 with weight w^k_plane) and
+// adds dF_c g^k_plane to the CTA's partial of dgrid_w[k][plane].
+// grid_wsum_kernel sums those partials over the slices in order.
 // ---------------------------------------------------------------------------
+constexpr int kGRThreads = 256, kGRChunk = kGRThreads * 2;
+constexpr int kMaxKK = (kMaxK + 2) / 3;  // grids per output channel
+
 struct GridRed {
-    int B, H, W, Dsx, Dsy, Dsc, strips;
+    int B, H, W, K, Dsx, Dsy, Dsc, strips;
     float rW1, rH1;
     GridPlan gp;
+    int sl[3];  // slices per channel plane: xy, xc, yc
+    int smax;   // max(sl)
+    const float *gxy, *gxc, *gyc, *gw;
+    float *dgxy, *dgxc, *dgyc;  // any may be null
+    float *wpart;               // [B][3 planes][K][smax] partial sums of dgrid_w, or null
 };
 
 // block footprint along one axis: first vertex and count (as grid_grad_kernel)
@@ -595,117 +609,127 @@ __device__ __forceinline__ void cover_range(int v, int n, int Ds, int unit, int 
         u1 = nunits - 1;
         return;
     }
-    const long long lo = (static_cast<long long>(max(v - 1, 0)) * (n - 1)) / (Ds - 1);
-    const long long hi = (static_cast<long long>(min(v + 1, Ds - 1)) * (n - 1) + (Ds - 2)) / (Ds - 1);
-    u0 = max(0, static_cast<int>(lo / unit) - 1);
-    u1 = min(nunits - 1, static_cast<int>(hi / unit) + 1);
+    // a / d for 0 <= a, 1 <= d: a 32-bit division whenever a fits
+    auto div = [](long long a, int d) -> long long {
+        return a <= 0xffffffffLL ? static_cast<long long>(static_cast<unsigned int>(a) / static_cast<unsigned int>(d))
+                                 : a / d;
+    };
+    const long long lo = div(static_cast<long long>(max(v - 1, 0)) * (n - 1), Ds - 1);
+    const long long hi = div(static_cast<long long>(min(v + 1, Ds - 1)) * (n - 1) + (Ds - 2), Ds - 1);
+    u0 = max(0, static_cast<int>(div(lo, unit)) - 1);
+    u1 = min(nunits - 1, static_cast<int>(div(hi, unit)) + 1);
 }
 
-__global__ void grid_reduce_kernel(GridRed g, const float *__restrict__ grid_part, float *__restrict__ dF)
+__host__ __device__ inline int grid_plane_size(int plane, int Dsx, int Dsy, int Dsc)
 {
-    const int b = blockIdx.y;
-    const int Dsx = g.Dsx, Dsy = g.Dsy, Dsc = g.Dsc;
-    const int nxy = Dsy * Dsx * 3, nxc = 3 * Dsx * Dsc, nyc = 3 * Dsy * Dsc;
-    float *out = dF + static_cast<size_t>(b) * (nxy + nxc + nyc);
+    return plane == 0 ? Dsy * Dsx : (plane == 1 ? Dsx * Dsc : Dsy * Dsc);
+}
+
+__global__ void __launch_bounds__(kGRThreads, 4)
+    grid_reduce_kernel(GridRed g, const float *__restrict__ grid_part)
+{
+    extern __shared__ int gtab[];  // ylo[bands], nvy[bands], xlo[strips], nvx[strips]
+    __shared__ float red[kGRThreads / 32][kMaxKK];
     const GridPlan &gp = g.gp;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nxy + nxc + nyc; e += gridDim.x * blockDim.x) {
-        int iy = -1, ix = -1, j = 0, c = 0, plane;
-        if (e < nxy) {
-            plane = 0;
-            iy = e / (Dsx * 3);
-            const int r = e - iy * Dsx * 3;
-            ix = r / 3;
-            c = r - ix * 3;
-        } else if (e < nxy + nxc) {
-            plane = 1;
-            const int q = e - nxy;
-            c = q / (Dsx * Dsc);
-            const int r = q - c * Dsx * Dsc;
-            ix = r / Dsc;
-            j = r - ix * Dsc;
+    const int b = blockIdx.y;
+    int q = blockIdx.x, plane = 0;  // blockIdx.x -> (plane, channel c, slice)
+    while (plane < 2 && q >= 3 * g.sl[plane]) {
+        q -= 3 * g.sl[plane];
+        ++plane;
+    }
+    const int c = q / g.sl[plane], slice = q - c * g.sl[plane];
+    int *ylo = gtab, *nvy = gtab + gp.bands, *xlo = nvy + gp.bands, *nvx = xlo + g.strips;
+    for (int t = threadIdx.x; t < gp.bands + g.strips; t += kGRThreads) {
+        if (t < gp.bands) {
+            const int y0 = t * gp.BH, rows = min(gp.BH, g.H - y0);
+            if (rows > 0) axis_span(y0, rows, g.H, g.Dsy, g.rH1, gp.nvy, ylo[t], nvy[t]);
+            else ylo[t] = nvy[t] = 0;
         } else {
-            plane = 2;
-            const int q = e - nxy - nxc;
-            c = q / (Dsy * Dsc);
-            const int r = q - c * Dsy * Dsc;
-            iy = r / Dsc;
-            j = r - iy * Dsc;
+            const int st = t - gp.bands, x0 = st * kTileW;
+            axis_span(x0, min(kTileW, g.W - x0), g.W, g.Dsx, g.rW1, gp.nvx, xlo[st], nvx[st]);
         }
+    }
+    __syncthreads();
+    const int Dsx = g.Dsx, Dsy = g.Dsy, Dsc = g.Dsc, K = g.K;
+    const int n = grid_plane_size(plane, Dsx, Dsy, Dsc), ncol = plane == 0 ? Dsx : Dsc;
+    const float *gsrc = plane == 0 ? g.gxy : (plane == 1 ? g.gxc : g.gyc);
+    float *gdst = plane == 0 ? g.dgxy : (plane == 1 ? g.dgxc : g.dgyc);
+    const int oxc = 3 * gp.nvy * gp.nvx, oyc = oxc + 3 * gp.nvx * Dsc;  // plane offsets in a block partial
+    float acc[kMaxKK];
+#pragma unroll
+    for (int kk = 0; kk < kMaxKK; ++kk) acc[kk] = 0.f;
+    const int e1 = min(n, (slice + 1) * kGRChunk);
+    for (int e = slice * kGRChunk + threadIdx.x; e < e1; e += kGRThreads) {
+        // xy: (iy, ix); xc: (ix, j); yc: (iy, j)
+        const int r = e / ncol, col = e - r * ncol;
+        const int iy = plane == 1 ? -1 : r, ix = plane == 0 ? col : (plane == 1 ? r : -1), j = col;
         int s0 = 0, s1 = g.strips - 1, b0 = 0, b1 = gp.bands - 1;
         if (ix >= 0) cover_range(ix, g.W, Dsx, kTileW, g.strips, s0, s1);
         if (iy >= 0) cover_range(iy, g.H, Dsy, gp.BH, gp.bands, b0, b1);
         float s = 0.f;
         for (int bd = b0; bd <= b1; ++bd) {
-            const int y0 = bd * gp.BH, rows = min(gp.BH, g.H - y0);
-            if (rows <= 0) continue;
-            int ylo, nvy;
-            axis_span(y0, rows, g.H, Dsy, g.rH1, gp.nvy, ylo, nvy);
-            if (iy >= 0 && (iy < ylo || iy >= ylo + nvy)) continue;
+            const int yl = ylo[bd], ny = nvy[bd];
+            if (ny <= 0 || (iy >= 0 && (iy < yl || iy >= yl + ny))) continue;
             for (int st = s0; st <= s1; ++st) {
-                const int x0 = st * kTileW, cols = min(kTileW, g.W - x0);
-                int xlo, nvx;
-                axis_span(x0, cols, g.W, Dsx, g.rW1, gp.nvx, xlo, nvx);
-                if (ix >= 0 && (ix < xlo || ix >= xlo + nvx)) continue;
+                const int xl = xlo[st];
+                if (ix >= 0 && (ix < xl || ix >= xl + nvx[st])) continue;
                 const float *bp = grid_part + (static_cast<size_t>(b) * gp.nblk + bd * g.strips + st) * gp.blk_stride;
                 if (plane == 0)
-                    s += bp[((iy - ylo) * gp.nvx + (ix - xlo)) * 3 + c];
+                    s += bp[((iy - yl) * gp.nvx + (ix - xl)) * 3 + c];
                 else if (plane == 1)
-                    s += bp[3 * gp.nvy * gp.nvx + (c * gp.nvx + (ix - xlo)) * Dsc + j];
+                    s += bp[oxc + (c * gp.nvx + (ix - xl)) * Dsc + j];
                 else
-                    s += bp[3 * gp.nvy * gp.nvx + 3 * gp.nvx * Dsc + (c * gp.nvy + (iy - ylo)) * Dsc + j];
+                    s += bp[oyc + (c * gp.nvy + (iy - yl)) * Dsc + j];
             }
         }
-        out[e] = s;
+#pragma unroll
+        for (int kk = 0; kk < kMaxKK; ++kk) {
+            const int k = c + 3 * kk;
+            if (k >= K) break;
+            const size_t o = (static_cast<size_t>(b) * K + k) * n + e;
+            if (gdst) gdst[o] = __ldg(g.gw + (static_cast<size_t>(b) * K + k) * 4 + plane) * s;
+            acc[kk] = fmaf(s, __ldg(gsrc + o), acc[kk]);
+        }
+    }
+    if (!g.wpart) return;
+    // the CTA's partials of dgrid_w: warp butterflies, then the warps in order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int kk = 0; kk < kMaxKK; ++kk) {
+        if (c + 3 * kk >= K) break;
+        const float v = warp_sum(acc[kk]);
+        if (lane == 0) red[warp][kk] = v;
+    }
+    __syncthreads();
+    const int k = c + 3 * static_cast<int>(threadIdx.x);
+    if (static_cast<int>(threadIdx.x) < kMaxKK && k < K) {
+        float s = 0.f;
+        for (int w = 0; w < kGRThreads / 32; ++w) s += red[w][threadIdx.x];
+        g.wpart[((static_cast<size_t>(b) * 3 + plane) * K + k) * g.smax + slice] = s;
     }
 }
 
-// grid finalize: one CTA per (grid k, image):
-//   dg^k_plane = w^k_plane * dF_{k mod 3, plane};  dgrid_w[k] = <dF, g^k> per
-//   plane, bias = sum of dy_{k mod 3} (from the LUT pass partials).
-struct GridFin {
-    const float *gxy, *gxc, *gyc, *gw;
-    float *dgxy, *dgxc, *dgyc, *dgw;
-    int K, Dsx, Dsy, Dsc, P;
+// dgrid_w[b][k] = (the slice partials of each plane summed in order, the sum
+// of dy_{k mod 3} over the image from the LUT pass partials: the bias).
+struct GridWsum {
+    int B, K, P, smax;
+    int sl[3];
+    float *dgw;
 };
 
-__global__ void __launch_bounds__(kFinThreads)
-    grid_finalize_kernel(GridFin f, const float *__restrict__ dF, const float *__restrict__ sums_part)
+__global__ void grid_wsum_kernel(GridWsum f, const float *__restrict__ wpart, const float *__restrict__ sums_part)
 {
-    __shared__ float red[kFinThreads / 32];
-    const int k = blockIdx.x, b = blockIdx.y, c = k % 3;
-    const int Dsx = f.Dsx, Dsy = f.Dsy, Dsc = f.Dsc;
-    const int nxy = Dsy * Dsx * 3, nxc = 3 * Dsx * Dsc, nyc = 3 * Dsy * Dsc;
-    const float *F = dF + static_cast<size_t>(b) * (nxy + nxc + nyc);
-    const float *w = f.gw + (static_cast<size_t>(b) * f.K + k) * 4;
-    const size_t kxy = static_cast<size_t>(Dsy) * Dsx, kxc = static_cast<size_t>(Dsx) * Dsc,
-                 kyc = static_cast<size_t>(Dsy) * Dsc;
-    const size_t bk = static_cast<size_t>(b) * f.K + k;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    for (int e = threadIdx.x; e < Dsy * Dsx; e += kFinThreads) {
-        const float F0 = F[e * 3 + c];
-        a0 = fmaf(F0, f.gxy[bk * kxy + e], a0);
-        if (f.dgxy) f.dgxy[bk * kxy + e] = w[0] * F0;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (b, k, entry)
+    if (t >= f.B * f.K * 4) return;
+    const int q = t & 3, bk = t >> 2, b = bk / f.K, k = bk - b * f.K;
+    float s = 0.f;
+    if (q < 3) {
+        const float *p = wpart + ((static_cast<size_t>(b) * 3 + q) * f.K + k) * f.smax;
+        for (int i = 0; i < f.sl[q]; ++i) s += p[i];
+    } else {
+        for (int p = 0; p < f.P; ++p) s += sums_part[(static_cast<size_t>(b) * f.P + p) * 3 + k % 3];
     }
-    for (int e = threadIdx.x; e < Dsx * Dsc; e += kFinThreads) {
-        const float F1 = F[nxy + c * Dsx * Dsc + e];
-        a1 = fmaf(F1, f.gxc[bk * kxc + e], a1);
-        if (f.dgxc) f.dgxc[bk * kxc + e] = w[1] * F1;
-    }
-    for (int e = threadIdx.x; e < Dsy * Dsc; e += kFinThreads) {
-        const float F2 = F[nxy + nxc + c * Dsy * Dsc + e];
-        a2 = fmaf(F2, f.gyc[bk * kyc + e], a2);
-        if (f.dgyc) f.dgyc[bk * kyc + e] = w[2] * F2;
-    }
-    const float s0 = block_sum(a0, red), s1 = block_sum(a1, red), s2 = block_sum(a2, red);
-    if (threadIdx.x == 0 && f.dgw) {
-        float s = 0.f;
-        for (int p = 0; p < f.P; ++p) s += sums_part[(static_cast<size_t>(b) * f.P + p) * 3 + c];
-        float *o = f.dgw + bk * 4;
-        o[0] = s0;
-        o[1] = s1;
-        o[2] = s2;
-        o[3] = s;
-    }
+    f.dgw[static_cast<size_t>(bk) * 4 + q] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -718,7 +742,8 @@ struct BwdPlan {
     size_t grid_smem;  // bytes
     // workspace layout (bytes); the last part holds the per-image tables of
     // the dx pass (prep_kernel)
-    size_t off_lut, off_sums, off_grid, off_dF, off_prep, prep_img, total;
+    size_t off_lut, off_sums, off_grid, off_wpart, off_prep, prep_img, total;
+    int sl[3], smax;  // grid_reduce_kernel slices per channel plane (xy, xc, yc)
 };
 
 static size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
@@ -808,9 +833,13 @@ static svdlut_status plan_backward(const svdlut_dims *d, int B, int H, int W, in
     off = align256(off + sizeof(float) * static_cast<size_t>(B) * pl->P * 3);
     pl->off_grid = off;
     off = align256(off + sizeof(float) * static_cast<size_t>(B) * bestgp.nblk * bestgp.blk_stride);
-    pl->off_dF = off;
-    off = align256(off + sizeof(float) * static_cast<size_t>(B) *
-                             (3 * d->Dsy * d->Dsx + 3 * d->Dsx * Dsc + 3 * d->Dsy * Dsc));
+    pl->smax = 1;
+    for (int q = 0; q < 3; ++q) {
+        pl->sl[q] = (grid_plane_size(q, d->Dsx, d->Dsy, Dsc) + kGRChunk - 1) / kGRChunk;
+        pl->smax = std::max(pl->smax, pl->sl[q]);
+    }
+    pl->off_wpart = off;
+    off = align256(off + sizeof(float) * static_cast<size_t>(B) * 3 * std::max(d->K, 0) * pl->smax);
     pl->off_prep = off;
     pl->prep_img = prep_image_bytes(d);
     off += static_cast<size_t>(B) * pl->prep_img;
@@ -908,7 +937,7 @@ extern "C" svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_p
     float *lut_part = reinterpret_cast<float *>(w + pl.off_lut);
     float *sums_part = reinterpret_cast<float *>(w + pl.off_sums);
     float *grid_part = reinterpret_cast<float *>(w + pl.off_grid);
-    float *dF = reinterpret_cast<float *>(w + pl.off_dF);
+    float *wpart = reinterpret_cast<float *>(w + pl.off_wpart);
 
     BwdArgs a{};
     a.x = x;
@@ -950,14 +979,45 @@ extern "C" svdlut_status svdlut_backward(const svdlut_dims *dims, const svdlut_p
     if (want_grid) {
         grid_grad_kernel<<<dim3(pl.gp.nblk, B), kThreads, pl.grid_smem, s>>>(a, pl.gp, grid_part);
         SVDLUT_CUDA_TRY(cudaGetLastError());
-        GridRed r{B, H, W, dims->Dsx, dims->Dsy, dims->Dsc, a.strips, a.rW1, a.rH1, pl.gp};
-        const int nF = 3 * dims->Dsy * dims->Dsx + 3 * dims->Dsx * dims->Dsc + 3 * dims->Dsy * dims->Dsc;
-        grid_reduce_kernel<<<dim3(std::max(1, std::min(1024, (nF + 255) / 256)), B), 256, 0, s>>>(r, grid_part, dF);
+        GridRed r{};
+        r.B = B;
+        r.H = H;
+        r.W = W;
+        r.K = dims->K;
+        r.Dsx = dims->Dsx;
+        r.Dsy = dims->Dsy;
+        r.Dsc = dims->Dsc;
+        r.strips = a.strips;
+        r.rW1 = a.rW1;
+        r.rH1 = a.rH1;
+        r.gp = pl.gp;
+        r.smax = pl.smax;
+        for (int q = 0; q < 3; ++q) r.sl[q] = pl.sl[q];
+        r.gxy = params->g_xy;
+        r.gxc = params->g_xc;
+        r.gyc = params->g_yc;
+        r.gw = params->grid_w;
+        r.dgxy = g.dg_xy;
+        r.dgxc = g.dg_xc;
+        r.dgyc = g.dg_yc;
+        r.wpart = g.dgrid_w ? wpart : nullptr;
+        // the CTA's band and strip footprint tables
+        const size_t rsm = sizeof(int) * 2 * static_cast<size_t>(pl.gp.bands + a.strips);
+        if (rsm > 48 * 1024) {
+            if ((st = allow_dynamic_smem(reinterpret_cast<const void *>(grid_reduce_kernel), di.max_smem_optin,
+                                         di.device)) != SVDLUT_OK)
+                return st;
+            if (rsm + sizeof(float) * (kGRThreads / 32) * kMaxKK > static_cast<size_t>(di.max_smem_optin))
+                return fail(SVDLUT_ERR_UNSUPPORTED, "too many column strips and row bands for the grid reduction");
+        }
+        grid_reduce_kernel<<<dim3(3 * (pl.sl[0] + pl.sl[1] + pl.sl[2]), B), kGRThreads, rsm, s>>>(r, grid_part);
         SVDLUT_CUDA_TRY(cudaGetLastError());
-        GridFin f{params->g_xy, params->g_xc, params->g_yc, params->grid_w, g.dg_xy, g.dg_xc, g.dg_yc, g.dgrid_w,
-                  dims->K, dims->Dsx, dims->Dsy, dims->Dsc, pl.P};
-        grid_finalize_kernel<<<dim3(dims->K, B), kFinThreads, 0, s>>>(f, dF, sums_part);
-        SVDLUT_CUDA_TRY(cudaGetLastError());
+        if (g.dgrid_w) {
+            GridWsum f{B, dims->K, pl.P, pl.smax, {pl.sl[0], pl.sl[1], pl.sl[2]}, g.dgrid_w};
+            const int n = B * dims->K * 4;
+            grid_wsum_kernel<<<(n + 255) / 256, 256, 0, s>>>(f, wpart, sums_part);
+            SVDLUT_CUDA_TRY(cudaGetLastError());
+        }
     }
     return SVDLUT_OK;
 }
