@@ -100,6 +100,24 @@ def test_backward_is_bitwise_deterministic(sv):
         assert np.array_equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("want", [("dgrid_w",), ("dg_xy", "dg_yc"), ("dU", "dg_xc"), ("dx", "dlut_w", "dgrid_w")])
+def test_backward_gradient_subsets_equal_the_full_call(sv, want):
+    """Any subset of the gradients (the grid weights without the grid
+    planes, planes without the weights, LUT and grid parts apart) gives the
+    same bits as the call that asks for all of them."""
+    import torch
+    d = si.Dims(17, 8, 9, 12, 9, 17)
+    x, p = si.make_batch(330, 2, 72, 100, d)
+    dy = si.make_upstream(331, x.shape)
+    xt, pt, gt = torch.from_numpy(x).cuda(), sv.to_device(p), torch.from_numpy(dy).cuda()
+    full = sv.backward(xt, pt, gt)
+    part = sv.backward(xt, pt, gt, want=want)
+    torch.cuda.synchronize()
+    assert set(part) == set(want)
+    for k in want:
+        assert torch.equal(part[k], full[k]), k
+
+
 def test_backward_matches_fp64_central_differences(sv):
     """directional derivatives of the FP64 oracle forward on a 64x64 crop"""
     d = si.spatial_dims(64, 64)
